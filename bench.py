@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Throughput of the t-product hot path on one GB300 (or N GPUs as independent replicas).
+
+Step = one batched prox_tnn call (Algorithm 3) over the batched workload: 512 independent
+real tensors with n1, n2 uniform in {16..160}, n3 uniform in {4..64}, tubal rank r uniform
+in {2..12} (t-product of N(0,1) factors) plus N(0, 0.05^2) noise, tau = 2x the noise level
+of one Fourier slice.  Metric: prox_tnn Fourier slices per second (a slice is one of the
+ceil((n3+1)/2) directly computed frontal slices of a tensor).
+
+The JSON line also carries:
+  roofline      the slice-SVT kernels (dominant), timed live with CUDA events recorded by
+                the library at stage boundaries, against the FP32 ALU peak;
+  e2e           the same metric with pinned host inputs copied in and outputs copied back
+                inside the timed region;
+  tprod         t-product TFLOP/s on A 2048x1024x64 times B 1024x1024x64 (plain FP32);
+  cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
+
+`--impl reference` times the FP64 oracle itself (host cores) on the same workload.
+Multi-GPU (torchrun): every rank runs its own batch (seed = rank); no collective on the
+data path; value = all ranks' slices / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "prox_tnn slices/s & tprod TFLOP/s vs plain FP32 GPU path at ≤1e-4 rel err"
+UNIT = "slices/s"
+WORKLOAD = ("batched prox_tnn, FP32: 512 tensors, n1,n2~U{16..160}, n3~U{4..64}, tubal rank "
+            "r~U{2..12} t-product of N(0,1) factors + N(0,0.05^2) noise, tau = 2x noise level")
+SM_COUNT = 152
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * 2.070e9 / 1e12   # FFMA lanes x 2 flops x max SM clock
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="tp", choices=["tp", "reference"])
+    p.add_argument("--count", type=int, default=512)
+    p.add_argument("--no-tprod", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling of the SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- workload
+def svd_launch_groups(shapes):
+    """Kernel instantiations one batched prox call launches (mirrors the library's
+    slice planner: elements per lane and whether the slice fits in shared memory)."""
+    groups = set()
+    for n1, n2 in shapes:
+        m, n = max(n1, n2), min(n1, n2)
+        need = (m + 31) // 32
+        e = max(need, 1) if need <= 5 else (8 if need <= 8 else 16)
+        aux = (6 * n * 4 + 256 + (m + 1) * 4 + 20 * m + 15) & ~15
+        in_smem = n * (m | 1) * 8 + aux <= 227 * 1024 - 1024
+        groups.add((in_smem, e))
+    return len(groups)
+
+
+def make_batch(tp, synth, count, seed, device):
+    import numpy as np
+    import torch
+    specs = synth.batched_specs(512, seed)[:count]
+    Ys, taus = [], []
+    for i, s in enumerate(specs):
+        f = synth.batched_tensor(s, i, seed)
+        Y = tp.tprod(tp.to_device(f["P"], device), tp.to_device(f["Q"], device))
+        Y.add_(tp.to_device(f["E"], device))
+        Ys.append(Y)
+        taus.append(s.tau)
+    torch.cuda.synchronize()
+    slices = sum(s.n3 // 2 + 1 for s in specs)
+    nbytes = sum(4 * s.n1 * s.n2 * s.n3 for s in specs)
+    model_shapes = [(s.n1, s.n2, s.n3) for s in specs]
+    return specs, Ys, taus, slices, nbytes, model_shapes
+
+
+def jacobi_model_flops(shapes, sweeps):
+    """Model count of the one-sided Jacobi: per sweep n(n-1)/2 column pairs, 40 m real flops
+    per pair (16 m for the three dot products, 24 m for the complex rotation of two columns)."""
+    total, idx = 0.0, 0
+    for n1, n2, n3 in shapes:
+        m, n = max(n1, n2), min(n1, n2)
+        for _ in range(n3 // 2 + 1):
+            total += float(sweeps[idx]) * n * (n - 1) / 2 * 40.0 * m
+            idx += 1
+    return total
+
+
+# ----------------------------------------------------------------------------- oracle legs
+def oracle_sample(specs, seed, seconds, max_items=None):
+    """Time the FP64 oracle's prox_tnn on tensors 0, 1, ... of the batch until `seconds`
+    of CPU work (at least one tensor). Returns (slices/s, slices, tensors, seconds)."""
+    import numpy as np
+
+    from oracle import tproduct as O
+    from paper_1806_07247_gb300 import synth
+    done_slices, done, t_total = 0, 0, 0.0
+    for i, s in enumerate(specs):
+        f = synth.batched_tensor(s, i, seed)
+        X = (O.tprod_fourier(f["P"], f["Q"]) + f["E"]).astype(np.float32)
+        t0 = time.perf_counter()
+        O.prox_tnn(X, s.tau)
+        t_total += time.perf_counter() - t0
+        done_slices += s.n3 // 2 + 1
+        done += 1
+        if t_total >= seconds or (max_items and done >= max_items):
+            break
+    return done_slices / t_total, done_slices, done, t_total
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1806_07247_gb300 import synth
+    specs = synth.batched_specs(512, 0)[:args.count]
+    sample = specs[:6]
+    times, slices = [], sum(s.n3 // 2 + 1 for s in sample)
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle_sample(sample, 0, seconds=1e9, max_items=len(sample))
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = slices * args.steps / total
+    cores = os.cpu_count()
+    desc = (f"each step: FP64 oracle prox_tnn on tensors 0-5 of the 512-tensor batch "
+            f"({slices} free slices), all n3 slices SVD'd by LAPACK")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tensors": len(specs), "seed": 0},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_tp(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1806_07247_gb300 import synth, tp
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    tp.lib()
+    specs, Ys, taus, slices, nbytes, shapes = make_batch(tp, synth, args.count, rank, device)
+    Xs = [tp.empty(*Y.shape, device=device) for Y in Ys]
+    descs = tp.make_descs(Ys, Xs, taus)
+    nsl = slices
+    sweeps = torch.zeros(nsl, dtype=torch.int32, device=device)
+
+    def events(n):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        for e in evs:
+            e.record()
+        return evs
+
+    base_opts = tp.options(sync=False)
+    for _ in range(args.warmup):
+        tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=base_opts, descs=descs)
+    torch.cuda.synchronize()
+    # convergence status of the workload (one synchronous call, untimed)
+    tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=tp.options(sync=True, sweeps_out=sweeps),
+                        descs=descs)
+
+    stage = [events(4) for _ in range(args.steps)]
+    step_opts = [tp.options(sync=False, sweeps_out=sweeps, stage_events=stage[i])
+                 for i in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    t0.record()
+    for i in range(args.steps):
+        tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=step_opts[i], descs=descs)
+    t1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = slices * world * args.steps / (ms_max / 1e3)
+
+    # stage times (ms per step): DFT, slice SVT, inverse DFT
+    st = [[s[j].elapsed_time(s[j + 1]) for j in range(3)] for s in stage]
+    st_mean = [sum(x[j] for x in st) / len(st) for j in range(3)]
+    sw = sweeps.cpu().numpy()
+    flops = jacobi_model_flops(shapes, sw)
+    groups = svd_launch_groups([(a, b) for a, b, _ in shapes])
+    svt_tflops = flops / (st_mean[1] / 1e3) / 1e12
+    # DFT stages: algorithmic bytes = real tensor + half spectrum (complex FP32)
+    spec_bytes = sum(8 * a * b * (c // 2 + 1) for a, b, c in shapes)
+    dft_gbs = (nbytes + spec_bytes) / (st_mean[0] / 1e3) / 1e9
+    idft_gbs = (nbytes + spec_bytes) / (st_mean[2] / 1e3) / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tensors": len(specs), "free_slices": slices,
+                       "seed": rank, "input_bytes": nbytes,
+                       "l2": "inputs larger than L2 (%.2f GB in + out per step)" % (2 * nbytes / 1e9)},
+            "gpu_launches": (2 + groups) * args.steps,
+            "clocks": clk,
+            "roofline": {"kernel": "svd_kernel<SVD_PROX> (one-sided Jacobi + SVT), %d launches/step" % groups,
+                         "bound": "alu", "achieved": svt_tflops, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": svt_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                         "model": "sum over slices of sweeps*n(n-1)/2*40*m flops",
+                         "sweeps_mean": float(sw.mean()), "sweeps_max": int(sw.max())},
+            "stages_ms": {"rfft": st_mean[0], "svt": st_mean[1], "irfft": st_mean[2]},
+            "dft_gbs": {"rfft": dft_gbs, "irfft": idft_gbs}}
+
+    if not args.no_e2e:
+        line["e2e"] = e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device)
+    if not args.no_tprod and rank == 0:
+        line["tprod"] = tprod_leg(args, tp, synth, device)
+    if rank == 0:
+        rate, sl, nt, secs = oracle_sample(specs, rank, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"FP64 oracle prox_tnn on tensors 0-{nt - 1} of the batch "
+                                          f"({sl} free slices, {secs:.1f} s); numpy/LAPACK threads"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
+    """Pinned host input -> device, batched prox, device -> pinned host output, per step."""
+    import torch
+    hin = [torch.empty(Y.numel(), dtype=torch.float32, pin_memory=True) for Y in Ys]
+    hout = [torch.empty(Y.numel(), dtype=torch.float32, pin_memory=True) for Y in Ys]
+    for h, Y in zip(hin, Ys):
+        h.copy_(Y.permute(2, 1, 0).reshape(-1).cpu())
+    flat_in = [Y.permute(2, 1, 0).reshape(-1) for Y in Ys]     # views of the device buffers
+    flat_out = [X.permute(2, 1, 0).reshape(-1) for X in Xs]
+    opts = tp.options(sync=False)
+
+    def step():
+        for d, h in zip(flat_in, hin):
+            d.copy_(h, non_blocking=True)
+        tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=opts, descs=descs)
+        for h, d in zip(hout, flat_out):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record()
+    for _ in range(args.steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    nb = sum(4 * Y.numel() for Y in Ys)
+    return {"value": slices * world * args.steps / (float(ms_t.item()) / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+
+
+def tprod_leg(args, tp, synth, device):
+    """Plain FP32 t-product of A 2048x1024x64 and B 1024x1024x64 (one rank)."""
+    import torch
+    g = synth.gemm(0)
+    A, B = tp.to_device(g["A"], device), tp.to_device(g["B"], device)
+    del g
+    n1, n2, l, n3 = 2048, 1024, 1024, 64
+    C = tp.empty(n1, l, n3, device)
+    h = n3 // 2 + 1
+    nreal = 2 if n3 % 2 == 0 else 1
+    flops = (2.0 * nreal + 8.0 * (h - nreal)) * n1 * n2 * l
+    steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        tp.tprod(A, B, out=C, opts=tp.options(sync=False))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for s in evs:
+        for e in s:
+            e.record()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for i in range(steps):
+        tp.tprod(A, B, out=C, opts=tp.options(sync=False, stage_events=evs[i]))
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    st = [sum(s[j].elapsed_time(s[j + 1]) for s in evs) / steps for j in range(3)]
+    gemm_tflops = flops / (st[1] / 1e3) / 1e12
+    return {"workload": "A 2048x1024x64 * B 1024x1024x64, N(0,1)", "precision": "fp32",
+            "tflops": flops / (ms / 1e3) / 1e12, "ms_per_call": ms, "flops": flops,
+            "stages_ms": {"rfft": st[0], "gemm": st[1], "irfft": st[2]},
+            "gemm_roofline": {"bound": "alu", "achieved": gemm_tflops, "peak": FP32_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": gemm_tflops / FP32_PEAK_TFLOPS}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_tp(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * tp.h -- C ABI of the GB300 t-product library (libtp).
+ *
+ * The operations are those of Lu, "Tensor-Tensor Product Toolbox" (2018), on real
+ * third-order tensors, computed by the Fourier-domain method the paper describes:
+ * a real DFT along every mode-3 tube that keeps the ceil((n3+1)/2) independent
+ * frontal slices (Lemma 2.1, Eq. 8), one batched kernel over those slices (a
+ * complex GEMM, a one-sided Jacobi SVD with one of several epilogues), and the
+ * inverse DFT with the mirrored slices implied (Algorithms 1-3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout.    A tensor A of size n1 x n2 x n3 is an array of n1*n2*n3 float32 values,
+ *            column-major: entry A(i, j, k) (0-based) is at A[i + n1*j + n1*n2*k]
+ *            (the paper's Matlab indexing, section 2.1).
+ * Memory.    Every tensor or scalar pointer is a DEVICE pointer of the current CUDA
+ *            device, owned by the caller; the library never frees or keeps it.
+ *            Tensor pointers need 4-byte alignment; 16-byte alignment enables the
+ *            vectorised paths.
+ * Stream.    `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
+ *            enqueued on it and the call returns without waiting, unless
+ *            tp_options.sync is set (the default), in which case the call waits for
+ *            the stream and reports device-side non-convergence.
+ * Workspace. The library allocates its temporary buffers with the stream-ordered
+ *            allocator (cudaMallocAsync / cudaFreeAsync on `stream`) and keeps a
+ *            per-device table of DFT twiddles in static device memory, filled on the
+ *            first call on each device: make that first call before any stream
+ *            capture.
+ * Empty.     A dimension equal to 0 is a valid empty tensor: the call writes nothing
+ *            (scalar results are 0) and returns TP_OK.
+ * Errors.    Arguments are checked before anything is enqueued. A negative dimension,
+ *            a NULL pointer for a non-empty tensor, a negative or NaN tau or an
+ *            invalid option gives TP_ERR_INVALID_ARG; inconsistent shapes give
+ *            TP_ERR_SHAPE; sizes beyond the documented limits give
+ *            TP_ERR_UNSUPPORTED; a failing allocation gives TP_ERR_NO_MEMORY; a CUDA
+ *            launch error gives TP_ERR_CUDA. No call aborts, traps or prints.
+ * Aliasing.  Inputs and outputs must not overlap, except in tp_prox_tnn, where
+ *            X == Y (fully in place) is allowed.
+ * Limits.    n3 <= TP_MAX_N3. For the SVD-based calls, max(n1, n2) <= TP_MAX_SVD_DIM.
+ *            All counts fit in int64_t; a single tensor has fewer than 2^31 entries
+ *            per frontal slice.
+ */
+#ifndef TP_H
+#define TP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TP_MAX_N3 1024
+#define TP_MAX_SVD_DIM 512
+
+typedef enum tp_status {
+    TP_OK = 0,
+    TP_ERR_INVALID_ARG = 1,
+    TP_ERR_SHAPE = 2,
+    TP_ERR_NO_MEMORY = 3,
+    TP_ERR_CUDA = 4,
+    TP_ERR_NOT_CONVERGED = 5, /* a Jacobi SVD hit max_sweeps; outputs are still written */
+    TP_ERR_UNSUPPORTED = 6
+} tp_status;
+
+/* Arithmetic of the tprod slice GEMMs (Algorithm 1, step 2). */
+typedef enum tp_precision {
+    TP_PREC_FP32 = 0,   /* plain FP32 FFMA */
+    TP_PREC_3XTF32 = 1, /* tensor cores: split-TF32, three products, FP32 accumulation */
+    TP_PREC_BF16X3 = 2  /* tensor cores: split-BF16, three products, FP32 accumulation */
+} tp_precision;
+
+typedef struct tp_options {
+    int32_t precision;   /* tp_precision, used by tp_tprod (default TP_PREC_FP32) */
+    int32_t econ;        /* tp_tsvd: 0 = full shapes of Thm. 2.2, 1 = economy shapes */
+    int32_t max_sweeps;  /* Jacobi sweep cap per slice (default 30, range 1..1000; 0 = 30) */
+    int32_t sync;        /* 1 (default): wait for the stream before returning and report
+                            TP_ERR_NOT_CONVERGED; 0: fully asynchronous */
+    double jacobi_tol;   /* rotate a column pair when |a_p^H a_q| > tol*||a_p||*||a_q||;
+                            <= 0 selects max(8, sqrt(m)) * 2^-23 */
+    int32_t* sweeps_out; /* optional DEVICE array, one int per directly computed Fourier
+                            slice (tensor-major, slice-minor): Jacobi sweeps used */
+    void* const* stage_events; /* optional HOST array of 4 cudaEvent_t, recorded on `stream`
+                            before the tube DFT, after it, after the per-slice kernels and
+                            after the inverse DFT (or final reduction); for timing */
+} tp_options;
+
+/* Fill *opts with the defaults used when a NULL options pointer is passed. */
+void tp_options_default(tp_options* opts);
+
+/* Human-readable name of a status code (static string). */
+const char* tp_status_string(tp_status status);
+
+/* Name of the last CUDA error this thread's library calls met ("cudaSuccess" if none);
+   a static string, for diagnosing TP_ERR_CUDA. */
+const char* tp_last_error_string(void);
+
+/*
+ * t-product C = A * B (Def. 2.1, Eq. 9), computed as Algorithm 1: DFT of the tubes
+ * of A and B, Cbar^(k) = Abar^(k) Bbar^(k) for the ceil((n3+1)/2) independent slices,
+ * inverse DFT with the conjugate mirror implied.
+ *   A: n1 x n2 x n3 (in), B: n2 x l x n3 (in), C: n1 x l x n3 (out).
+ * opts->precision selects the slice-GEMM arithmetic.
+ */
+tp_status tp_tprod(const float* A, const float* B, float* C, int64_t n1, int64_t n2,
+                   int64_t l, int64_t n3, const tp_options* opts, void* stream);
+
+/*
+ * Conjugate tensor transpose (Def. 2.2) of a real tensor: AT(j, i, 0) = A(i, j, 0)
+ * and AT(j, i, k) = A(i, j, n3 - k) for 0 < k < n3.
+ *   A: n1 x n2 x n3 (in), AT: n2 x n1 x n3 (out).
+ */
+tp_status tp_tran(const float* A, float* AT, int64_t n1, int64_t n2, int64_t n3,
+                  void* stream);
+
+/*
+ * t-SVD A = U * S * V^* (Thm. 2.2) by Algorithm 2: one-sided Jacobi SVD of each of the
+ * ceil((n3+1)/2) independent Fourier slices (real arithmetic on the real slices 0 and
+ * n3/2, so U and V come out real), the other slices implied as conjugate mirrors.
+ *   Full (opts->econ == 0): U n1 x n1 x n3, S n1 x n2 x n3, V n2 x n2 x n3.
+ *   Economy (opts->econ == 1): U n1 x r x n3, S r x r x n3, V n2 x r x n3,
+ *   r = min(n1, n2).
+ * S is f-diagonal with S(:, :, 0) decreasing (Eq. 13). U and V are unique only up to
+ * the usual phase and repeated-singular-value freedom.
+ */
+tp_status tp_tsvd(const float* A, float* U, float* S, float* V, int64_t n1, int64_t n2,
+                  int64_t n3, const tp_options* opts, void* stream);
+
+/*
+ * Tensor nuclear norm (Def. 2.9 with Eq. 14): out[0] = (1/n3) * sum over all n3 Fourier
+ * slices of the sum of their singular values. `out` is a device double.
+ */
+tp_status tp_tnn(const float* A, double* out, int64_t n1, int64_t n2, int64_t n3,
+                 const tp_options* opts, void* stream);
+
+/*
+ * Tensor spectral norm (Def. 2.8, Eq. 17): out[0] = ||bcirc(A)|| = the largest singular
+ * value over the Fourier slices. `out` is a device double.
+ */
+tp_status tp_tsn(const float* A, double* out, int64_t n1, int64_t n2, int64_t n3,
+                 const tp_options* opts, void* stream);
+
+/*
+ * Tensor tubal rank (Def. 2.7, Eq. 16): out[0] = #{i : S(i, i, 0) > tol}, with
+ * S(i, i, 0) = (1/n3) sum_k sigma_i(Abar^(k)) (Eq. 14). tol < 0 selects
+ * max(n1, n2) * 2^-23 * S(0, 0, 0). If s_out is not NULL it receives the
+ * min(n1, n2) tensor singular values S(i, i, 0) (device doubles).
+ */
+tp_status tp_tubalrank(const float* A, int64_t* out, double* s_out, int64_t n1, int64_t n2,
+                       int64_t n3, double tol, const tp_options* opts, void* stream);
+
+/*
+ * Proximal operator of the tensor nuclear norm (Eq. 19), X = U * S_tau * V^* (Thm. 2.3),
+ * computed by Algorithm 3: singular value thresholding at tau of each independent
+ * Fourier slice, the mirrored slices implied, inverse DFT.
+ *   Y, X: n1 x n2 x n3. tau >= 0 (tau = 0 returns Y up to rounding). X == Y allowed.
+ */
+tp_status tp_prox_tnn(const float* Y, float* X, int64_t n1, int64_t n2, int64_t n3,
+                      double tau, const tp_options* opts, void* stream);
+
+/* One tensor of a batched call. */
+typedef struct tp_tensor_desc {
+    const float* in; /* device, n1 x n2 x n3 */
+    float* out;      /* device, n1 x n2 x n3; may equal `in` */
+    int64_t n1, n2, n3;
+    double tau;
+} tp_tensor_desc;
+
+/*
+ * tp_prox_tnn on `count` independent tensors of any sizes, as three launches over all
+ * of them (one DFT launch, slice SVT launches grouped by slice size, one inverse-DFT
+ * launch) on one stream. `descs` is a HOST array. Each tensor obeys tp_prox_tnn's rules;
+ * tensors must not overlap one another. sweeps_out (if set) is indexed by the
+ * concatenation, in descriptor order, of each tensor's ceil((n3+1)/2) slices.
+ */
+tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count,
+                              const tp_options* opts, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TP_H */

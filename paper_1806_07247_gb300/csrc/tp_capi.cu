@@ -1,0 +1,600 @@
+// extern "C" entry points of libtp: argument checks, workspace planning and the launch
+// sequence of each operation (DFT of the tubes -> per-slice kernel -> inverse DFT).
+#include <math.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "tp_internal.cuh"
+
+using namespace tp;
+
+namespace {
+
+thread_local cudaError_t t_last_error = cudaSuccess;
+
+tp_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return TP_OK;
+    t_last_error = e;
+    if (e == cudaErrorMemoryAllocation) return TP_ERR_NO_MEMORY;
+    return TP_ERR_CUDA;
+}
+
+#define TP_TRY(expr)                              \
+    do {                                          \
+        tp_status _st = (expr);                   \
+        if (_st != TP_OK) return _st;             \
+    } while (0)
+#define TP_CUDA(expr) TP_TRY(from_cuda(expr))
+
+std::mutex g_pool_mutex;
+bool g_pool_ready[128] = {};
+
+// Keep freed stream-ordered allocations in this process's default pool for reuse.
+cudaError_t ensure_pool() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (g_pool_ready[dev]) return cudaSuccess;
+    cudaMemPool_t pool;
+    e = cudaDeviceGetDefaultMemPool(&pool, dev);
+    if (e != cudaSuccess) return e;
+    uint64_t thr = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (e != cudaSuccess) return e;
+    g_pool_ready[dev] = true;
+    return cudaSuccess;
+}
+
+tp_status prepare() {
+    TP_CUDA(ensure_pool());
+    TP_CUDA(ensure_twiddles());
+    return TP_OK;
+}
+
+// One stream-ordered workspace per call, carved into 256-byte aligned pieces.
+struct Workspace {
+    cudaStream_t s;
+    char* base = nullptr;
+    size_t size = 0, used = 0;
+    explicit Workspace(cudaStream_t st) : s(st) {}
+    ~Workspace() {
+        if (base) cudaFreeAsync(base, s);
+    }
+    static size_t round(size_t b) { return (b + 255) & ~(size_t)255; }
+    tp_status reserve(size_t bytes) {
+        size = bytes;
+        if (bytes == 0) return TP_OK;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, s);
+        if (e != cudaSuccess) {
+            base = nullptr;
+            cudaGetLastError();
+            return from_cuda(e);
+        }
+        return TP_OK;
+    }
+    // Carve `count` elements; an over-run (a sizing bug) is recorded, not written through.
+    template <class T>
+    T* take(size_t count) {
+        size_t b = round(count * sizeof(T));
+        if (used + b > size) {
+            overflow = true;
+            return nullptr;
+        }
+        T* p = reinterpret_cast<T*>(base + used);
+        used += b;
+        return p;
+    }
+    bool overflow = false;
+    tp_status check() const { return overflow ? TP_ERR_CUDA : TP_OK; }
+};
+
+struct Opts {
+    int precision = TP_PREC_FP32, econ = 0, max_sweeps = 30, sync = 1;
+    double jacobi_tol = 0.0;
+    int32_t* sweeps_out = nullptr;
+    void* const* events = nullptr;
+    // Record stage boundary i (0..3) on the stream when the caller asked for it.
+    tp_status mark(int i, cudaStream_t s) const {
+        if (!events || !events[i]) return TP_OK;
+        return from_cuda(cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s));
+    }
+};
+
+tp_status resolve(const tp_options* o, Opts* r) {
+    *r = Opts();
+    if (!o) return TP_OK;
+    if (o->precision < TP_PREC_FP32 || o->precision > TP_PREC_BF16X3) return TP_ERR_INVALID_ARG;
+    if (o->econ != 0 && o->econ != 1) return TP_ERR_INVALID_ARG;
+    if (o->max_sweeps < 0 || o->max_sweeps > 1000) return TP_ERR_INVALID_ARG;
+    if (o->sync != 0 && o->sync != 1) return TP_ERR_INVALID_ARG;
+    if (isnan(o->jacobi_tol) || o->jacobi_tol >= 1.0) return TP_ERR_INVALID_ARG;
+    r->precision = o->precision;
+    r->econ = o->econ;
+    r->max_sweeps = o->max_sweeps == 0 ? 30 : o->max_sweeps;
+    r->sync = o->sync;
+    r->jacobi_tol = o->jacobi_tol;
+    r->sweeps_out = o->sweeps_out;
+    r->events = o->stage_events;
+    return TP_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+tp_status check_dims(int64_t n1, int64_t n2, int64_t n3) {
+    if (n1 < 0 || n2 < 0 || n3 < 0) return TP_ERR_INVALID_ARG;
+    if (n3 > TP_MAX_N3) return TP_ERR_UNSUPPORTED;
+    if (n1 * n2 >= ((int64_t)1 << 31)) return TP_ERR_UNSUPPORTED;
+    return TP_OK;
+}
+
+// Upload a host array into the workspace (pageable copy; the source may be freed on return).
+template <class T>
+tp_status upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
+    if (src.empty()) return TP_OK;
+    return from_cuda(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(),
+                                     cudaMemcpyHostToDevice, s));
+}
+
+tp_status finish(uint32_t* d_status, const Opts& o, cudaStream_t s) {
+    TP_CUDA(cudaGetLastError());
+    if (!o.sync) return TP_OK;
+    uint32_t h = 0;
+    if (d_status) TP_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    TP_CUDA(cudaStreamSynchronize(s));
+    return (h & 1u) ? TP_ERR_NOT_CONVERGED : TP_OK;
+}
+
+// Group per-slice SVD jobs by kernel instantiation and launch each group.
+struct SvdBatch {
+    struct Item {
+        SvdJob job;
+        int maxe, smem, threads;
+        bool in_smem;
+        int64_t cost;
+    };
+    std::vector<Item> items;
+
+    tp_status launch(Workspace& ws, int mode, const Opts& o, uint32_t* d_status, cudaStream_t s) {
+        if (items.empty()) return TP_OK;
+        std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
+            if (a.in_smem != b.in_smem) return a.in_smem > b.in_smem;
+            if (a.maxe != b.maxe) return a.maxe < b.maxe;
+            return a.cost > b.cost;
+        });
+        std::vector<SvdJob> jobs(items.size());
+        for (size_t i = 0; i < items.size(); ++i) jobs[i] = items[i].job;
+        SvdJob* d_jobs = ws.take<SvdJob>(jobs.size());
+        TP_TRY(ws.check());
+        TP_TRY(upload(d_jobs, jobs, s));
+        SvdParams p;
+        p.mode = mode;
+        p.max_sweeps = o.max_sweeps;
+        p.tol = (float)o.jacobi_tol;
+        p.sweeps_out = o.sweeps_out;
+        p.status = d_status;
+        size_t i = 0;
+        while (i < items.size()) {
+            size_t j = i;
+            int smem = 0, threads = 0;
+            while (j < items.size() && items[j].in_smem == items[i].in_smem &&
+                   items[j].maxe == items[i].maxe) {
+                smem = std::max(smem, items[j].smem);
+                threads = std::max(threads, items[j].threads);
+                ++j;
+            }
+            SvdLaunch L;
+            L.jobs = d_jobs + i;
+            L.njobs = (int)(j - i);
+            L.maxe = items[i].maxe;
+            L.in_smem = items[i].in_smem;
+            L.smem_bytes = smem;
+            L.threads = threads;
+            TP_CUDA(launch_svd(L, p, s));
+            i = j;
+        }
+        return TP_OK;
+    }
+};
+
+struct FftBatch {
+    std::vector<FftJob> jobs;
+    int max_n3 = 1;
+    bool vec = true;
+    void add(const float* x, float2* X, int64_t P, int n3) {
+        if (P <= 0 || n3 <= 0) return;
+        FftJob j;
+        j.x = x;
+        j.X = X;
+        j.P = P;
+        j.n3 = n3;
+        j.tile_begin = 0;
+        jobs.push_back(j);
+        max_n3 = std::max(max_n3, n3);
+        vec = vec && (P % 4 == 0) && aligned16(x) && aligned16(X);
+    }
+    tp_status launch(Workspace& ws, bool inverse, cudaStream_t s) {
+        if (jobs.empty()) return TP_OK;
+        int64_t tiles = 0;
+        for (auto& j : jobs) {
+            j.tile_begin = (int32_t)tiles;
+            tiles += fft_tiles(j.P, max_n3);
+        }
+        if (tiles > 0x7fffffffLL) return TP_ERR_UNSUPPORTED;
+        FftJob* d = ws.take<FftJob>(jobs.size());
+        TP_TRY(ws.check());
+        TP_TRY(upload(d, jobs, s));
+        cudaError_t e = inverse ? launch_irfft(d, (int)jobs.size(), (int)tiles, max_n3, vec, s)
+                                : launch_rfft(d, (int)jobs.size(), (int)tiles, max_n3, vec, s);
+        return from_cuda(e);
+    }
+};
+
+size_t cbytes(int64_t count) { return Workspace::round((size_t)count * sizeof(float2)); }
+
+// Batched prox over validated descriptors.
+tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cudaStream_t s) {
+    // sizes first
+    size_t bytes = Workspace::round(sizeof(uint32_t));
+    int64_t slices = 0;
+    std::vector<int> maxe(count), smem(count), thr(count);
+    std::vector<char> insm(count);
+    std::vector<int64_t> work(count);
+    int64_t nfft = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        const int64_t n1 = d[t].n1, n2 = d[t].n2, n3 = d[t].n3;
+        if (n1 == 0 || n2 == 0 || n3 == 0) continue;
+        const int h = free_slices((int)n3);
+        bool sm = false;
+        if (!svd_plan((int)n1, (int)n2, SVD_PROX, &maxe[t], &sm, &smem[t], &thr[t], &work[t]))
+            return TP_ERR_UNSUPPORTED;
+        insm[t] = sm;
+        bytes += cbytes(n1 * n2 * h);
+        if (work[t] > 0) bytes += cbytes(work[t] * h);
+        slices += h;
+        ++nfft;
+    }
+    if (nfft == 0) return TP_OK;
+    bytes += 2 * Workspace::round(sizeof(FftJob) * (nfft + 1));
+    bytes += Workspace::round(sizeof(SvdJob) * (slices + 1));
+    Workspace ws(s);
+    TP_TRY(ws.reserve(bytes));
+    uint32_t* d_status = ws.take<uint32_t>(1);
+    TP_TRY(ws.check());
+    TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+    FftBatch fwd, inv;
+    SvdBatch svd;
+    int64_t sidx = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        const int64_t n1 = d[t].n1, n2 = d[t].n2, n3 = d[t].n3;
+        if (n1 == 0 || n2 == 0 || n3 == 0) continue;
+        const int h = free_slices((int)n3);
+        const int64_t P = n1 * n2;
+        float2* spec = ws.take<float2>(P * h);
+        float2* wk = work[t] > 0 ? ws.take<float2>(work[t] * h) : nullptr;
+        fwd.add(d[t].in, spec, P, (int)n3);
+        inv.add(d[t].out, spec, P, (int)n3);
+        for (int k = 0; k < h; ++k) {
+            SvdBatch::Item it;
+            SvdJob& j = it.job;
+            j.A = spec + P * k;
+            j.W = spec + P * k;
+            j.Vout = nullptr;
+            j.work = wk ? wk + work[t] * k : nullptr;
+            j.sigma = nullptr;
+            j.n1 = (int)n1;
+            j.n2 = (int)n2;
+            j.real_slice = is_real_slice(k, (int)n3) ? 1 : 0;
+            j.ucols = j.vcols = 0;
+            j.sweeps_index = (int32_t)(sidx++);
+            j.tau = d[t].tau;
+            it.maxe = maxe[t];
+            it.smem = smem[t];
+            it.threads = thr[t];
+            it.in_smem = insm[t] != 0;
+            const int64_t m = std::max(n1, n2), n = std::min(n1, n2);
+            it.cost = m * n * n;
+            svd.items.push_back(it);
+        }
+    }
+    TP_TRY(o.mark(0, s));
+    TP_TRY(fwd.launch(ws, false, s));
+    TP_TRY(o.mark(1, s));
+    TP_TRY(svd.launch(ws, SVD_PROX, o, d_status, s));
+    TP_TRY(o.mark(2, s));
+    TP_TRY(inv.launch(ws, true, s));
+    TP_TRY(o.mark(3, s));
+    return finish(d_status, o, s);
+}
+
+// Singular values of all free slices of one tensor, sorted decreasing, then one reduction.
+tp_status sigma_op(const float* A, int64_t n1, int64_t n2, int64_t n3, int kind, double tol,
+                   double* out_d, int64_t* out_i, double* s_out, const Opts& o, cudaStream_t s) {
+    const int h = free_slices((int)n3);
+    const int64_t r = std::min(n1, n2), P = n1 * n2;
+    int maxe, smem, thr;
+    bool sm;
+    int64_t work;
+    if (!svd_plan((int)n1, (int)n2, SVD_SIGMA, &maxe, &sm, &smem, &thr, &work))
+        return TP_ERR_UNSUPPORTED;
+    size_t bytes = Workspace::round(4) + cbytes(P * h) + (work ? cbytes(work * h) : 0) +
+                   Workspace::round(sizeof(float) * r * h) + 2 * Workspace::round(sizeof(FftJob)) +
+                   Workspace::round(sizeof(SvdJob) * h);
+    Workspace ws(s);
+    TP_TRY(ws.reserve(bytes));
+    uint32_t* d_status = ws.take<uint32_t>(1);
+    TP_TRY(ws.check());
+    TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+    float2* spec = ws.take<float2>(P * h);
+    float2* wk = work ? ws.take<float2>(work * h) : nullptr;
+    float* sig = ws.take<float>(r * h);
+    FftBatch fwd;
+    fwd.add(A, spec, P, (int)n3);
+    SvdBatch svd;
+    for (int k = 0; k < h; ++k) {
+        SvdBatch::Item it;
+        SvdJob& j = it.job;
+        j.A = spec + P * k;
+        j.W = nullptr;
+        j.Vout = nullptr;
+        j.work = wk ? wk + work * k : nullptr;
+        j.sigma = sig + r * k;
+        j.n1 = (int)n1;
+        j.n2 = (int)n2;
+        j.real_slice = is_real_slice(k, (int)n3) ? 1 : 0;
+        j.ucols = j.vcols = 0;
+        j.sweeps_index = k;
+        j.tau = 0.0;
+        it.maxe = maxe;
+        it.smem = smem;
+        it.threads = thr;
+        it.in_smem = sm;
+        it.cost = 0;
+        svd.items.push_back(it);
+    }
+    TP_TRY(o.mark(0, s));
+    TP_TRY(fwd.launch(ws, false, s));
+    TP_TRY(o.mark(1, s));
+    TP_TRY(svd.launch(ws, SVD_SIGMA, o, d_status, s));
+    TP_TRY(o.mark(2, s));
+    TP_TRY(ws.check());
+    TP_CUDA(launch_sigma_reduce(sig, h, (int)r, (int)n3, kind, tol, std::max(n1, n2), out_d, out_i,
+                                s_out, s));
+    TP_TRY(o.mark(3, s));
+    return finish(d_status, o, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+void tp_options_default(tp_options* opts) {
+    if (!opts) return;
+    opts->precision = TP_PREC_FP32;
+    opts->econ = 0;
+    opts->max_sweeps = 30;
+    opts->sync = 1;
+    opts->jacobi_tol = 0.0;
+    opts->sweeps_out = nullptr;
+    opts->stage_events = nullptr;
+}
+
+const char* tp_last_error_string(void) {
+    return t_last_error == cudaSuccess ? "cudaSuccess" : cudaGetErrorName(t_last_error);
+}
+
+const char* tp_status_string(tp_status status) {
+    switch (status) {
+        case TP_OK: return "TP_OK";
+        case TP_ERR_INVALID_ARG: return "TP_ERR_INVALID_ARG";
+        case TP_ERR_SHAPE: return "TP_ERR_SHAPE";
+        case TP_ERR_NO_MEMORY: return "TP_ERR_NO_MEMORY";
+        case TP_ERR_CUDA: return "TP_ERR_CUDA";
+        case TP_ERR_NOT_CONVERGED: return "TP_ERR_NOT_CONVERGED";
+        case TP_ERR_UNSUPPORTED: return "TP_ERR_UNSUPPORTED";
+        default: return "TP_ERR_UNKNOWN";
+    }
+}
+
+tp_status tp_tprod(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t l,
+                   int64_t n3, const tp_options* opts, void* stream) {
+    Opts o;
+    TP_TRY(resolve(opts, &o));
+    TP_TRY(check_dims(n1, n2, n3));
+    TP_TRY(check_dims(n2, l, n3));
+    TP_TRY(check_dims(n1, l, n3));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n1 == 0 || l == 0 || n3 == 0) return TP_OK;
+    if (!C) return TP_ERR_INVALID_ARG;
+    if (n2 > 0 && (!A || !B)) return TP_ERR_INVALID_ARG;
+    if (o.precision != TP_PREC_FP32) return TP_ERR_UNSUPPORTED;
+    TP_TRY(prepare());
+    if (n2 == 0) {
+        TP_CUDA(cudaMemsetAsync(C, 0, sizeof(float) * n1 * l * n3, s));
+        return finish(nullptr, o, s);
+    }
+    const int h = free_slices((int)n3);
+    const int64_t PA = n1 * n2, PB = n2 * l, PC = n1 * l;
+    Workspace ws(s);
+    TP_TRY(ws.reserve(cbytes(PA * h) + cbytes(PB * h) + cbytes(PC * h) +
+                      2 * Workspace::round(sizeof(FftJob) * 3)));
+    float2* Ab = ws.take<float2>(PA * h);
+    float2* Bb = ws.take<float2>(PB * h);
+    float2* Cb = ws.take<float2>(PC * h);
+    FftBatch fwd, inv;
+    fwd.add(A, Ab, PA, (int)n3);
+    fwd.add(B, Bb, PB, (int)n3);
+    TP_TRY(o.mark(0, s));
+    TP_TRY(fwd.launch(ws, false, s));
+    TP_TRY(o.mark(1, s));
+    TP_TRY(ws.check());
+    TP_CUDA(launch_cgemm_fp32(Ab, Bb, Cb, (int)n1, (int)l, (int)n2, PA, PB, PC, h, s));
+    TP_TRY(o.mark(2, s));
+    inv.add(C, Cb, PC, (int)n3);
+    TP_TRY(inv.launch(ws, true, s));
+    TP_TRY(o.mark(3, s));
+    return finish(nullptr, o, s);
+}
+
+tp_status tp_tran(const float* A, float* AT, int64_t n1, int64_t n2, int64_t n3, void* stream) {
+    TP_TRY(check_dims(n1, n2, n3));
+    if (n1 == 0 || n2 == 0 || n3 == 0) return TP_OK;
+    if (!A || !AT) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TP_CUDA(launch_tran(A, AT, n1, n2, n3, s));
+    return TP_OK;
+}
+
+tp_status tp_tsvd(const float* A, float* U, float* S, float* V, int64_t n1, int64_t n2,
+                  int64_t n3, const tp_options* opts, void* stream) {
+    Opts o;
+    TP_TRY(resolve(opts, &o));
+    TP_TRY(check_dims(n1, n2, n3));
+    if (n1 == 0 || n2 == 0 || n3 == 0) return TP_OK;
+    if (!A || !U || !S || !V) return TP_ERR_INVALID_ARG;
+    const int64_t r = std::min(n1, n2);
+    const int64_t ucols = o.econ ? r : n1, vcols = o.econ ? r : n2;
+    const int64_t sS1 = o.econ ? r : n1, sS2 = o.econ ? r : n2;
+    if (n1 * ucols >= ((int64_t)1 << 31) || n2 * vcols >= ((int64_t)1 << 31))
+        return TP_ERR_UNSUPPORTED;
+    int maxe, smem, thr;
+    bool sm;
+    int64_t work;
+    if (!svd_plan((int)n1, (int)n2, SVD_FULL, &maxe, &sm, &smem, &thr, &work))
+        return TP_ERR_UNSUPPORTED;
+    TP_TRY(prepare());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int h = free_slices((int)n3);
+    const int64_t P = n1 * n2, PU = n1 * ucols, PV = n2 * vcols;
+    Workspace ws(s);
+    TP_TRY(ws.reserve(Workspace::round(4) + cbytes(P * h) + cbytes(work * h) + cbytes(PU * h) +
+                      cbytes(PV * h) + cbytes(r * h) + Workspace::round(sizeof(float) * r * h) +
+                      Workspace::round(sizeof(float) * r * n3) +
+                      2 * Workspace::round(sizeof(FftJob) * 4) +
+                      Workspace::round(sizeof(SvdJob) * h)));
+    uint32_t* d_status = ws.take<uint32_t>(1);
+    TP_TRY(ws.check());
+    TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+    float2* spec = ws.take<float2>(P * h);
+    float2* wk = ws.take<float2>(work * h);
+    float2* Ub = ws.take<float2>(PU * h);
+    float2* Vb = ws.take<float2>(PV * h);
+    float2* Sb = ws.take<float2>(r * h);
+    float* sig = ws.take<float>(r * h);
+    float* tubes = ws.take<float>(r * n3);
+    FftBatch fwd;
+    fwd.add(A, spec, P, (int)n3);
+    TP_TRY(fwd.launch(ws, false, s));
+    SvdBatch svd;
+    for (int k = 0; k < h; ++k) {
+        SvdBatch::Item it;
+        SvdJob& j = it.job;
+        j.A = spec + P * k;
+        j.W = Ub + PU * k;
+        j.Vout = Vb + PV * k;
+        j.work = wk + work * k;
+        j.sigma = sig + r * k;
+        j.n1 = (int)n1;
+        j.n2 = (int)n2;
+        j.real_slice = is_real_slice(k, (int)n3) ? 1 : 0;
+        j.ucols = (int)ucols;
+        j.vcols = (int)vcols;
+        j.sweeps_index = k;
+        j.tau = 0.0;
+        it.maxe = maxe;
+        it.smem = smem;
+        it.threads = thr;
+        it.in_smem = sm;
+        it.cost = 0;
+        svd.items.push_back(it);
+    }
+    TP_TRY(svd.launch(ws, SVD_FULL, o, d_status, s));
+    TP_TRY(ws.check());
+    TP_CUDA(launch_diag_spectrum(sig, h, (int)r, Sb, s));
+    TP_CUDA(cudaMemsetAsync(S, 0, sizeof(float) * sS1 * sS2 * n3, s));
+    FftBatch inv;
+    inv.add(U, Ub, PU, (int)n3);
+    inv.add(V, Vb, PV, (int)n3);
+    inv.add(tubes, Sb, r, (int)n3);
+    TP_TRY(inv.launch(ws, true, s));
+    TP_CUDA(launch_diag_scatter(tubes, (int)r, (int)n3, S, sS1, sS2, s));
+    return finish(d_status, o, s);
+}
+
+static tp_status scalar_op(const float* A, double* out, int64_t n1, int64_t n2, int64_t n3,
+                           const tp_options* opts, void* stream, int kind) {
+    Opts o;
+    TP_TRY(resolve(opts, &o));
+    TP_TRY(check_dims(n1, n2, n3));
+    if (!out) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n1 == 0 || n2 == 0 || n3 == 0) {
+        TP_TRY(prepare());
+        TP_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
+        return finish(nullptr, o, s);
+    }
+    if (!A) return TP_ERR_INVALID_ARG;
+    TP_TRY(prepare());
+    return sigma_op(A, n1, n2, n3, kind, 0.0, out, nullptr, nullptr, o, s);
+}
+
+tp_status tp_tnn(const float* A, double* out, int64_t n1, int64_t n2, int64_t n3,
+                 const tp_options* opts, void* stream) {
+    return scalar_op(A, out, n1, n2, n3, opts, stream, 0);
+}
+
+tp_status tp_tsn(const float* A, double* out, int64_t n1, int64_t n2, int64_t n3,
+                 const tp_options* opts, void* stream) {
+    return scalar_op(A, out, n1, n2, n3, opts, stream, 1);
+}
+
+tp_status tp_tubalrank(const float* A, int64_t* out, double* s_out, int64_t n1, int64_t n2,
+                       int64_t n3, double tol, const tp_options* opts, void* stream) {
+    Opts o;
+    TP_TRY(resolve(opts, &o));
+    TP_TRY(check_dims(n1, n2, n3));
+    if (!out || isnan(tol)) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TP_TRY(prepare());
+    if (n1 == 0 || n2 == 0 || n3 == 0) {
+        TP_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+        return finish(nullptr, o, s);
+    }
+    if (!A) return TP_ERR_INVALID_ARG;
+    return sigma_op(A, n1, n2, n3, 2, tol, nullptr, out, s_out, o, s);
+}
+
+tp_status tp_prox_tnn(const float* Y, float* X, int64_t n1, int64_t n2, int64_t n3, double tau,
+                      const tp_options* opts, void* stream) {
+    tp_tensor_desc d;
+    d.in = Y;
+    d.out = X;
+    d.n1 = n1;
+    d.n2 = n2;
+    d.n3 = n3;
+    d.tau = tau;
+    return tp_prox_tnn_batched(&d, 1, opts, stream);
+}
+
+tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count, const tp_options* opts,
+                              void* stream) {
+    Opts o;
+    TP_TRY(resolve(opts, &o));
+    if (count < 0 || (count > 0 && !descs)) return TP_ERR_INVALID_ARG;
+    for (int64_t t = 0; t < count; ++t) {
+        const tp_tensor_desc& d = descs[t];
+        TP_TRY(check_dims(d.n1, d.n2, d.n3));
+        if (isnan(d.tau) || d.tau < 0.0) return TP_ERR_INVALID_ARG;
+        if (d.n1 == 0 || d.n2 == 0 || d.n3 == 0) continue;
+        if (!d.in || !d.out) return TP_ERR_INVALID_ARG;
+        if (std::max(d.n1, d.n2) > TP_MAX_SVD_DIM) return TP_ERR_UNSUPPORTED;
+    }
+    if (count == 0) return TP_OK;
+    TP_TRY(prepare());
+    return prox_batched(descs, count, o, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,309 @@
+// Mode-3 tube DFTs (section 2.2): the forward real DFT that keeps the ceil((n3+1)/2)
+// independent frequencies (Lemma 2.1, Eq. 8) and the inverse DFT that implies the
+// conjugate mirror of the remaining frequencies and scales by 1/n3 (F^-1 = F^*/n, Eq. 1).
+//
+// Data layout.  A tensor of n1*n2 = P tubes and n3 samples is column-major, so sample t
+// of tube p is at x[p + P*t]: consecutive tubes are consecutive in memory.  A CTA takes
+// TP consecutive tubes, stages all their samples in shared memory with coalesced (float4
+// where the alignment allows) loads, and each thread then produces 4 consecutive tubes
+// x 4 frequencies per pass, reading the samples as float4 and the twiddles as warp
+// broadcasts.  Outputs are written back coalesced, frequency-major (X[p + P*k]).
+//
+// Twiddles.  w(n, m) = exp(2*pi*i*m/n) for 0 <= m < n and every n <= TP_MAX_N3 are
+// computed once per device on the host in FP64 (quarter points exact) and kept in a
+// static device table; the exponent (k*t) mod n3 is advanced by integer addition.
+#include <math.h>
+
+#include <mutex>
+#include <vector>
+
+#include "tp_internal.cuh"
+
+namespace tp {
+
+namespace {
+
+constexpr int kFftThreads = 256;
+constexpr int64_t kTwiddleCount = (int64_t)TP_MAX_N3 * (TP_MAX_N3 + 1) / 2;
+
+// Table for length n starts at n*(n-1)/2.
+__device__ float2 g_twiddle[kTwiddleCount];
+
+__host__ __device__ inline int64_t tw_offset(int n) { return (int64_t)n * (n - 1) / 2; }
+
+int tubes_per_cta(int max_n3) {
+    if (max_n3 <= 128) return 128;
+    if (max_n3 <= 256) return 64;
+    return 32;
+}
+
+size_t fft_smem_bytes(int max_n3, bool inverse) {
+    int tp = tubes_per_cta(max_n3);
+    int rows = inverse ? free_slices(max_n3) : max_n3;
+    size_t elem = inverse ? sizeof(float2) : sizeof(float);
+    return (size_t)rows * tp * elem + (size_t)max_n3 * sizeof(float2);
+}
+
+__device__ inline int find_job(const FftJob* jobs, int njobs, int b) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile_begin <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Forward: X[p, k] = sum_t x[p, t] * exp(-2 pi i k t / n3), k < h.
+template <bool VEC>
+__global__ void __launch_bounds__(kFftThreads) rfft_kernel(const FftJob* __restrict__ jobs,
+                                                           int njobs, int TP) {
+    extern __shared__ float4 smem4[];
+    const FftJob J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int n3 = J.n3, h = free_slices(n3);
+    const int64_t P = J.P;
+    const int64_t p0 = (int64_t)(blockIdx.x - J.tile_begin) * TP;
+    const int G = TP / 4;  // groups of 4 tubes
+    float* xs = reinterpret_cast<float*>(smem4);
+    float2* tw = reinterpret_cast<float2*>(xs + (size_t)n3 * TP);
+    const float2* gtw = g_twiddle + tw_offset(n3);
+    const int tid = threadIdx.x;
+
+    for (int i = tid; i < n3; i += kFftThreads) tw[i] = gtw[i];
+    if (VEC) {
+        float4* xs4 = reinterpret_cast<float4*>(xs);
+        for (int idx = tid; idx < n3 * G; idx += kFftThreads) {
+            int t = idx / G, g = idx - t * G;
+            int64_t p = p0 + 4 * g;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (p < P) v = __ldg(reinterpret_cast<const float4*>(J.x + p + P * t));
+            xs4[idx] = v;
+        }
+    } else {
+        for (int idx = tid; idx < n3 * TP; idx += kFftThreads) {
+            int t = idx / TP, j = idx - t * TP;
+            int64_t p = p0 + j;
+            xs[idx] = (p < P) ? __ldg(J.x + p + P * t) : 0.f;
+        }
+    }
+    __syncthreads();
+
+    const int g = tid % G, f = tid / G, F = kFftThreads / G;
+    const float4* xs4 = reinterpret_cast<const float4*>(xs);
+    const int64_t pg = p0 + 4 * g;
+    for (int base = f; base < h; base += 4 * F) {
+        int k[4], e[4];
+        float ar[4][4], ai[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int kq = base + q * F;
+            k[q] = (kq < h) ? kq : 0;
+            e[q] = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ar[q][i] = ai[q][i] = 0.f;
+        }
+        for (int t = 0; t < n3; ++t) {
+            float4 xv = xs4[t * G + g];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 w = tw[e[q]];
+                e[q] += k[q];
+                if (e[q] >= n3) e[q] -= n3;
+                ar[q][0] = fmaf(xv.x, w.x, ar[q][0]); ai[q][0] = fmaf(-xv.x, w.y, ai[q][0]);
+                ar[q][1] = fmaf(xv.y, w.x, ar[q][1]); ai[q][1] = fmaf(-xv.y, w.y, ai[q][1]);
+                ar[q][2] = fmaf(xv.z, w.x, ar[q][2]); ai[q][2] = fmaf(-xv.z, w.y, ai[q][2]);
+                ar[q][3] = fmaf(xv.w, w.x, ar[q][3]); ai[q][3] = fmaf(-xv.w, w.y, ai[q][3]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int kq = base + q * F;
+            if (kq >= h) continue;
+            if (is_real_slice(kq, n3)) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ai[q][i] = 0.f;
+            }
+            float2* dst = J.X + pg + P * kq;
+            if (VEC) {
+                if (pg < P) {
+                    reinterpret_cast<float4*>(dst)[0] = make_float4(ar[q][0], ai[q][0], ar[q][1], ai[q][1]);
+                    reinterpret_cast<float4*>(dst)[1] = make_float4(ar[q][2], ai[q][2], ar[q][3], ai[q][3]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (pg + i < P) dst[i] = make_float2(ar[q][i], ai[q][i]);
+            }
+        }
+    }
+}
+
+// Inverse: x[p, t] = (1/n3) sum_{k<n3} X[p, k] exp(2 pi i k t / n3) with X[n3-k] = conj(X[k]),
+// i.e. (1/n3) [Re X0 + 2 sum_{0<k<n3/2} Re(X_k e^{i theta}) + (even n3) Re X_{n3/2} (-1)^t].
+template <bool VEC>
+__global__ void __launch_bounds__(kFftThreads) irfft_kernel(const FftJob* __restrict__ jobs,
+                                                            int njobs, int TP) {
+    extern __shared__ float4 smem4[];
+    const FftJob J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int n3 = J.n3, h = free_slices(n3);
+    const int64_t P = J.P;
+    const int64_t p0 = (int64_t)(blockIdx.x - J.tile_begin) * TP;
+    const int G = TP / 4;
+    float2* Xs = reinterpret_cast<float2*>(smem4);
+    float2* tw = Xs + (size_t)h * TP;
+    const float2* gtw = g_twiddle + tw_offset(n3);
+    const int tid = threadIdx.x;
+    const float inv_n = 1.0f / (float)n3;
+
+    for (int i = tid; i < n3; i += kFftThreads) tw[i] = gtw[i];
+    // Stage the half spectrum, pre-scaled by its weight (1 or 2) / n3; the imaginary
+    // parts of the real slices are dropped.
+    for (int idx = tid; idx < h * G; idx += kFftThreads) {
+        int k = idx / G, gg = idx - k * G;
+        int64_t p = p0 + 4 * gg;
+        float wk = is_real_slice(k, n3) ? inv_n : 2.f * inv_n;
+        float wi = is_real_slice(k, n3) ? 0.f : wk;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        const float2* src = J.X + p + P * k;
+        if (VEC) {
+            if (p < P) {
+                a = __ldg(reinterpret_cast<const float4*>(src));
+                b = __ldg(reinterpret_cast<const float4*>(src) + 1);
+            }
+        } else {
+            float2 v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                v[i] = (p + i < P) ? __ldg(src + i) : make_float2(0.f, 0.f);
+            a = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+            b = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+        }
+        a.x *= wk; a.y *= wi; a.z *= wk; a.w *= wi;
+        b.x *= wk; b.y *= wi; b.z *= wk; b.w *= wi;
+        float4* d = reinterpret_cast<float4*>(Xs + (size_t)k * TP + 4 * gg);
+        d[0] = a;
+        d[1] = b;
+    }
+    __syncthreads();
+
+    const int g = tid % G, f = tid / G, F = kFftThreads / G;
+    const int64_t pg = p0 + 4 * g;
+    float* xout = const_cast<float*>(J.x);
+    for (int base = f; base < n3; base += 4 * F) {
+        int tt[4], e[4];
+        float acc[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int tq = base + q * F;
+            tt[q] = (tq < n3) ? tq : 0;
+            e[q] = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[q][i] = 0.f;
+        }
+        for (int k = 0; k < h; ++k) {
+            const float4* row = reinterpret_cast<const float4*>(Xs + (size_t)k * TP + 4 * g);
+            float4 a = row[0], b = row[1];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 w = tw[e[q]];
+                e[q] += tt[q];
+                if (e[q] >= n3) e[q] -= n3;
+                acc[q][0] = fmaf(a.x, w.x, fmaf(-a.y, w.y, acc[q][0]));
+                acc[q][1] = fmaf(a.z, w.x, fmaf(-a.w, w.y, acc[q][1]));
+                acc[q][2] = fmaf(b.x, w.x, fmaf(-b.y, w.y, acc[q][2]));
+                acc[q][3] = fmaf(b.z, w.x, fmaf(-b.w, w.y, acc[q][3]));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int tq = base + q * F;
+            if (tq >= n3) continue;
+            float* dst = xout + pg + P * tq;
+            if (VEC) {
+                if (pg < P)
+                    *reinterpret_cast<float4*>(dst) = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (pg + i < P) dst[i] = acc[q][i];
+            }
+        }
+    }
+}
+
+std::mutex g_tw_mutex;
+bool g_tw_ready[128] = {};
+
+}  // namespace
+
+cudaError_t ensure_twiddles() {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_tw_mutex);
+    if (g_tw_ready[dev]) return cudaSuccess;
+    static std::vector<float2> host;
+    if (host.empty()) {
+        host.resize((size_t)kTwiddleCount);
+        for (int n = 1; n <= TP_MAX_N3; ++n) {
+            float2* row = host.data() + tw_offset(n);
+            for (int m = 0; m < n; ++m) {
+                double c, s;
+                if (m == 0) { c = 1.0; s = 0.0; }
+                else if (2 * m == n) { c = -1.0; s = 0.0; }
+                else if (4 * m == n) { c = 0.0; s = 1.0; }
+                else if (4 * m == 3 * n) { c = 0.0; s = -1.0; }
+                else {
+                    double a = 2.0 * M_PI * (double)m / (double)n;
+                    c = cos(a);
+                    s = sin(a);
+                }
+                row[m] = make_float2((float)c, (float)s);
+            }
+        }
+    }
+    err = cudaMemcpyToSymbol(g_twiddle, host.data(), sizeof(float2) * host.size());
+    if (err != cudaSuccess) return err;
+    // the largest dynamic shared memory any launch of these kernels asks for
+    const int fwd = (int)fft_smem_bytes(TP_MAX_N3, false), inv = (int)fft_smem_bytes(TP_MAX_N3, true);
+    int mf = fwd, mi = inv;
+    for (int n = 1; n <= TP_MAX_N3; ++n) {
+        mf = mf > (int)fft_smem_bytes(n, false) ? mf : (int)fft_smem_bytes(n, false);
+        mi = mi > (int)fft_smem_bytes(n, true) ? mi : (int)fft_smem_bytes(n, true);
+    }
+    cudaError_t e1 = cudaFuncSetAttribute(rfft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
+    cudaError_t e2 = cudaFuncSetAttribute(rfft_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
+    cudaError_t e3 = cudaFuncSetAttribute(irfft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mi);
+    cudaError_t e4 = cudaFuncSetAttribute(irfft_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mi);
+    for (cudaError_t e : {e1, e2, e3, e4})
+        if (e != cudaSuccess) return e;
+    g_tw_ready[dev] = true;
+    return cudaSuccess;
+}
+
+int fft_tiles(int64_t P, int max_n3) {
+    int tp = tubes_per_cta(max_n3);
+    return (int)((P + tp - 1) / tp);
+}
+
+cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3, bool vec_ok,
+                        cudaStream_t s) {
+    if (total_tiles <= 0) return cudaSuccess;
+    int tp = tubes_per_cta(max_n3);
+    size_t smem = fft_smem_bytes(max_n3, false);
+    if (vec_ok) rfft_kernel<true><<<total_tiles, kFftThreads, smem, s>>>(d_jobs, njobs, tp);
+    else rfft_kernel<false><<<total_tiles, kFftThreads, smem, s>>>(d_jobs, njobs, tp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_irfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3, bool vec_ok,
+                         cudaStream_t s) {
+    if (total_tiles <= 0) return cudaSuccess;
+    int tp = tubes_per_cta(max_n3);
+    size_t smem = fft_smem_bytes(max_n3, true);
+    if (vec_ok) irfft_kernel<true><<<total_tiles, kFftThreads, smem, s>>>(d_jobs, njobs, tp);
+    else irfft_kernel<false><<<total_tiles, kFftThreads, smem, s>>>(d_jobs, njobs, tp);
+    return cudaGetLastError();
+}
+
+}  // namespace tp

@@ -1,0 +1,107 @@
+// Internal declarations shared by the translation units of libtp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tp.h"
+
+namespace tp {
+
+// Number of Fourier slices computed directly: ceil((n3+1)/2) = floor(n3/2)+1
+// (Algorithms 1-3); slices k >= h are conjugate mirrors of slice n3-k (Eq. 8).
+inline __host__ __device__ int free_slices(int n3) { return n3 / 2 + 1; }
+
+// Slice 0 and, for even n3, slice n3/2 are real matrices (Eq. 8).
+inline __host__ __device__ bool is_real_slice(int k, int n3) {
+    return k == 0 || (2 * k == n3);
+}
+
+// ---------------------------------------------------------------------------
+// Tube DFTs (tp_fft.cu)
+// ---------------------------------------------------------------------------
+// One tensor's tubes: x is P tubes x n3 samples (tube p, sample t at x[p + P*t]),
+// X is P tubes x h complex frequencies (X[p + P*k]).
+struct FftJob {
+    const float* x;      // rfft: input; irfft: output (written)
+    float2* X;           // rfft: output; irfft: input
+    int64_t P;           // tubes (n1*n2)
+    int32_t n3;
+    int32_t tile_begin;  // first CTA of this job in the launch
+};
+
+// Fills the per-device twiddle table on first use; returns cudaSuccess or the error.
+cudaError_t ensure_twiddles();
+
+// Forward real DFT of every tube, frequencies 0..h-1 (unnormalised, Eq. 2).
+cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
+                        bool vec_ok, cudaStream_t s);
+// Inverse DFT from the half spectrum with the conjugate mirror implied, scaled by 1/n3.
+cudaError_t launch_irfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
+                         bool vec_ok, cudaStream_t s);
+// CTAs one job needs (tubes per CTA depend on the launch's largest n3).
+int fft_tiles(int64_t P, int max_n3);
+
+// ---------------------------------------------------------------------------
+// Slice GEMMs (tp_gemm.cu): C_k = A_k B_k for k < nslices, complex, column-major.
+// ---------------------------------------------------------------------------
+cudaError_t launch_cgemm_fp32(const float2* A, const float2* B, float2* C, int M, int N, int K,
+                              int64_t sA, int64_t sB, int64_t sC, int nslices, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Slice SVDs (tp_svd.cu)
+// ---------------------------------------------------------------------------
+enum SvdMode : int32_t { SVD_SIGMA = 0, SVD_PROX = 1, SVD_FULL = 2 };
+
+struct SvdJob {
+    const float2* A;     // Fourier slice, n1 x n2, column-major, ld n1
+    float2* W;           // PROX: output slice (may equal A); FULL: Ubar slice (n1 x ucols)
+    float2* Vout;        // FULL: Vbar slice (n2 x vcols)
+    float2* work;        // global scratch: FULL needs n*n (V_G); large slices need m*n (G)
+    float* sigma;        // min(n1,n2) singular values, decreasing (SIGMA, FULL)
+    int32_t n1, n2;
+    int32_t real_slice;  // 1 for the real slices of Eq. 8
+    int32_t ucols, vcols;  // FULL: columns of U and V to produce
+    int32_t sweeps_index;  // index into sweeps_out, or -1
+    double tau;          // PROX threshold
+};
+
+struct SvdLaunch {
+    const SvdJob* jobs;  // device array
+    int njobs;
+    int maxe;            // elements per lane: m <= 32*maxe
+    bool in_smem;        // working matrix in shared memory
+    int smem_bytes;
+    int threads;
+};
+
+struct SvdParams {
+    int mode;
+    int max_sweeps;
+    float tol;           // <= 0: default per slice
+    int32_t* sweeps_out; // device, may be null
+    uint32_t* status;    // device status word (bit 0: not converged)
+};
+
+// Which launch configuration a slice of size n1 x n2 needs.
+bool svd_plan(int n1, int n2, int mode, int* maxe, bool* in_smem, int* smem_bytes,
+              int* threads, int64_t* work_elems);
+cudaError_t launch_svd(const SvdLaunch& L, const SvdParams& p, cudaStream_t s);
+
+// Reductions over the sorted singular values of one tensor (tnn, tsn, tubal rank).
+cudaError_t launch_sigma_reduce(const float* sigma, int h, int r, int n3, int kind, double tol,
+                                int64_t rank_scale, double* out_d, int64_t* out_i, double* s_out,
+                                cudaStream_t s);
+// S(i, i, t) tubes from the singular values: S is nS1 x nS2 x n3 (zeroed by the caller).
+cudaError_t launch_diag_spectrum(const float* sigma, int h, int r, float2* Sbar_diag,
+                                 cudaStream_t s);
+cudaError_t launch_diag_scatter(const float* tubes, int r, int n3, float* S, int64_t nS1,
+                                int64_t nS2, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Transpose (tp_tran.cu)
+// ---------------------------------------------------------------------------
+cudaError_t launch_tran(const float* A, float* AT, int64_t n1, int64_t n2, int64_t n3,
+                        cudaStream_t s);
+
+}  // namespace tp

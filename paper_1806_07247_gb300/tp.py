@@ -1,0 +1,284 @@
+"""ctypes binding of libtp (include/tp.h): argument marshalling only.
+
+Every operation runs in the CUDA library; this module only checks tensor types, passes
+device pointers, sizes and the current torch CUDA stream, and turns status codes into
+exceptions.  If libtp.so is missing the import of any operation raises: there is no
+fallback.
+
+Tensors are torch float32 CUDA tensors of logical shape (n1, n2, n3) in column-major
+layout, strides (1, n1, n1*n2) -- entry (i, j, k) at offset i + n1*j + n1*n2*k.  Use
+`empty`, `to_device` and `to_numpy` to move between that layout and numpy arrays in
+Fortran order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtp.so")
+
+TP_OK, TP_ERR_INVALID_ARG, TP_ERR_SHAPE, TP_ERR_NO_MEMORY, TP_ERR_CUDA, \
+    TP_ERR_NOT_CONVERGED, TP_ERR_UNSUPPORTED = range(7)
+PRECISIONS = {"fp32": 0, "3xtf32": 1, "bf16x3": 2}
+MAX_N3 = 1024
+MAX_SVD_DIM = 512
+
+
+class TpError(RuntimeError):
+    def __init__(self, status: int, func: str):
+        self.status = status
+        extra = ""
+        if status == TP_ERR_CUDA:
+            extra = f" ({lib().tp_last_error_string().decode()})"
+        super().__init__(f"{func} failed: {status_string(status)}{extra}")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("econ", ctypes.c_int32),
+                ("max_sweeps", ctypes.c_int32), ("sync", ctypes.c_int32),
+                ("jacobi_tol", ctypes.c_double), ("sweeps_out", ctypes.c_void_p),
+                ("stage_events", ctypes.c_void_p)]
+
+
+class TensorDesc(ctypes.Structure):
+    _fields_ = [("inp", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n1", ctypes.c_int64),
+                ("n2", ctypes.c_int64), ("n3", ctypes.c_int64), ("tau", ctypes.c_double)]
+
+
+_lib = None
+
+_SIGS = {
+    "tp_options_default": (None, [ctypes.POINTER(Options)]),
+    "tp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "tp_last_error_string": (ctypes.c_char_p, []),
+    "tp_tprod": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 4 +
+                 [ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_tran": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int64] * 3 + [ctypes.c_void_p]),
+    "tp_tsvd": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int64] * 3 +
+                [ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_tnn": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int64] * 3 +
+               [ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_tsn": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int64] * 3 +
+               [ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_tubalrank": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 3 +
+                     [ctypes.c_double, ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_prox_tnn": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int64] * 3 +
+                    [ctypes.c_double, ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_prox_tnn_batched": (ctypes.c_int, [ctypes.POINTER(TensorDesc), ctypes.c_int64,
+                                           ctypes.POINTER(Options), ctypes.c_void_p]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtp.so (built in-tree by build.py); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libtp.so not found at {LIB_PATH}: run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().tp_status_string(int(status)).decode()
+
+
+def options(precision: str = "fp32", econ: bool = False, max_sweeps: int = 30, sync: bool = True,
+            jacobi_tol: float = 0.0, sweeps_out: torch.Tensor | None = None,
+            stage_events=None) -> Options:
+    """tp_options; stage_events is a list of 4 recorded torch.cuda.Event (see tp.h)."""
+    o = Options()
+    o.precision = PRECISIONS[precision]
+    o.econ = int(bool(econ))
+    o.max_sweeps = int(max_sweeps)
+    o.sync = int(bool(sync))
+    o.jacobi_tol = float(jacobi_tol)
+    if sweeps_out is not None:
+        assert sweeps_out.is_cuda and sweeps_out.dtype == torch.int32
+        o.sweeps_out = sweeps_out.data_ptr()
+    if stage_events is not None:
+        arr = (ctypes.c_void_p * 4)(*[ev.cuda_event for ev in stage_events])
+        o._events_keepalive = arr
+        o.stage_events = ctypes.cast(arr, ctypes.c_void_p).value
+    return o
+
+
+# ----------------------------------------------------------------------------- layout helpers
+def empty(n1: int, n2: int, n3: int, device="cuda") -> torch.Tensor:
+    """Uninitialised column-major float32 tensor of logical shape (n1, n2, n3)."""
+    return torch.empty((n3, n2, n1), dtype=torch.float32, device=device).permute(2, 1, 0)
+
+
+def is_colmajor(t: torch.Tensor) -> bool:
+    if t.dim() != 3 or t.dtype != torch.float32:
+        return False
+    if t.numel() == 0:
+        return True
+    n1, n2, n3 = t.shape
+    want = (1, n1, n1 * n2)
+    return all(s == w or d <= 1 for s, w, d in zip(t.stride(), want, t.shape))
+
+
+def colmajor(t: torch.Tensor) -> torch.Tensor:
+    """t itself if already column-major float32, else a column-major copy."""
+    if is_colmajor(t):
+        return t
+    return t.to(torch.float32).permute(2, 1, 0).contiguous().permute(2, 1, 0)
+
+
+def to_device(a: np.ndarray, device="cuda") -> torch.Tensor:
+    """numpy (n1, n2, n3) array -> column-major float32 CUDA tensor."""
+    a = np.asarray(a, dtype=np.float32)
+    if a.ndim == 2:
+        a = a[:, :, None]
+    host = torch.from_numpy(np.ascontiguousarray(a.transpose(2, 1, 0)))
+    return host.to(device).permute(2, 1, 0)
+
+
+def to_numpy(t: torch.Tensor) -> np.ndarray:
+    """Column-major tensor -> numpy float32 (n1, n2, n3) array (Fortran order)."""
+    return t.detach().permute(2, 1, 0).contiguous().cpu().numpy().transpose(2, 1, 0)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _check(status: int, func: str):
+    if status != TP_OK:
+        raise TpError(status, func)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _prep(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dim() != 3:
+        raise ValueError(f"{name} must be 3-way (n1, n2, n3)")
+    return colmajor(t)
+
+
+# ----------------------------------------------------------------------------- operations
+def tprod(A: torch.Tensor, B: torch.Tensor, out: torch.Tensor | None = None,
+          precision: str = "fp32", opts: Options | None = None, stream=None) -> torch.Tensor:
+    """C = A * B (Def. 2.1) via Algorithm 1."""
+    A, B = _prep(A, "A"), _prep(B, "B")
+    n1, n2, n3 = A.shape
+    l = B.shape[1]
+    if B.shape[0] != n2 or B.shape[2] != n3:
+        raise ValueError("tprod needs A: n1 x n2 x n3 and B: n2 x l x n3")
+    C = empty(n1, l, n3, A.device) if out is None else out
+    assert is_colmajor(C)
+    o = opts or options(precision=precision)
+    _check(lib().tp_tprod(_ptr(A), _ptr(B), _ptr(C), n1, n2, l, n3, ctypes.byref(o),
+                          _stream(stream)), "tp_tprod")
+    return C
+
+
+def tran(A: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Conjugate tensor transpose (Def. 2.2) of a real tensor."""
+    A = _prep(A, "A")
+    n1, n2, n3 = A.shape
+    T = empty(n2, n1, n3, A.device) if out is None else out
+    _check(lib().tp_tran(_ptr(A), _ptr(T), n1, n2, n3, _stream(stream)), "tp_tran")
+    return T
+
+
+def tsvd(A: torch.Tensor, econ: bool = False, opts: Options | None = None, stream=None):
+    """t-SVD (Thm. 2.2) via Algorithm 2; returns (U, S, V)."""
+    A = _prep(A, "A")
+    n1, n2, n3 = A.shape
+    r = min(n1, n2)
+    U = empty(n1, r if econ else n1, n3, A.device)
+    S = empty(r if econ else n1, r if econ else n2, n3, A.device)
+    V = empty(n2, r if econ else n2, n3, A.device)
+    o = opts or options(econ=econ)
+    o.econ = int(bool(econ))
+    _check(lib().tp_tsvd(_ptr(A), _ptr(U), _ptr(S), _ptr(V), n1, n2, n3, ctypes.byref(o),
+                         _stream(stream)), "tp_tsvd")
+    return U, S, V
+
+
+def _scalar(fn, name, A, opts, stream, out):
+    A = _prep(A, "A")
+    n1, n2, n3 = A.shape
+    res = torch.empty(1, dtype=torch.float64, device=A.device) if out is None else out
+    o = opts or options()
+    _check(fn(_ptr(A), _ptr(res), n1, n2, n3, ctypes.byref(o), _stream(stream)), name)
+    return res
+
+
+def tnn(A: torch.Tensor, opts: Options | None = None, stream=None, out=None) -> torch.Tensor:
+    """Tensor nuclear norm (Def. 2.9); a 1-element float64 device tensor."""
+    return _scalar(lib().tp_tnn, "tp_tnn", A, opts, stream, out)
+
+
+def tsn(A: torch.Tensor, opts: Options | None = None, stream=None, out=None) -> torch.Tensor:
+    """Tensor spectral norm (Def. 2.8); a 1-element float64 device tensor."""
+    return _scalar(lib().tp_tsn, "tp_tsn", A, opts, stream, out)
+
+
+def tubalrank(A: torch.Tensor, tol: float = -1.0, opts: Options | None = None, stream=None):
+    """(tubal rank as a 1-element int64 tensor, tensor singular values S(i,i,0) as float64)."""
+    A = _prep(A, "A")
+    n1, n2, n3 = A.shape
+    rank = torch.zeros(1, dtype=torch.int64, device=A.device)
+    svals = torch.zeros(max(min(n1, n2), 1), dtype=torch.float64, device=A.device)
+    o = opts or options()
+    _check(lib().tp_tubalrank(_ptr(A), _ptr(rank), _ptr(svals), n1, n2, n3, float(tol),
+                              ctypes.byref(o), _stream(stream)), "tp_tubalrank")
+    return rank, svals[:min(n1, n2)]
+
+
+def prox_tnn(Y: torch.Tensor, tau: float, out: torch.Tensor | None = None,
+             opts: Options | None = None, stream=None) -> torch.Tensor:
+    """Proximal operator of TNN (Thm. 2.3) via Algorithm 3."""
+    Y = _prep(Y, "Y")
+    n1, n2, n3 = Y.shape
+    X = empty(n1, n2, n3, Y.device) if out is None else out
+    o = opts or options()
+    _check(lib().tp_prox_tnn(_ptr(Y), _ptr(X), n1, n2, n3, float(tau), ctypes.byref(o),
+                             _stream(stream)), "tp_prox_tnn")
+    return X
+
+
+def make_descs(Ys, Xs, taus):
+    """ctypes array of tp_tensor_desc for prox_tnn_batched (keeps no tensor alive)."""
+    arr = (TensorDesc * len(Ys))()
+    for i, (Y, X, tau) in enumerate(zip(Ys, Xs, taus)):
+        assert is_colmajor(Y) and is_colmajor(X)
+        n1, n2, n3 = Y.shape
+        arr[i].inp, arr[i].out = Y.data_ptr(), X.data_ptr()
+        arr[i].n1, arr[i].n2, arr[i].n3, arr[i].tau = n1, n2, n3, float(tau)
+    return arr
+
+
+def prox_tnn_batched(Ys, taus, outs=None, opts: Options | None = None, stream=None, descs=None):
+    """prox_tnn over many tensors in one batched call; returns the outputs."""
+    Ys = [_prep(Y, "Y") for Y in Ys]
+    Xs = [empty(*Y.shape, device=Y.device) for Y in Ys] if outs is None else outs
+    d = make_descs(Ys, Xs, taus) if descs is None else descs
+    o = opts or options()
+    _check(lib().tp_prox_tnn_batched(d, len(Ys), ctypes.byref(o), _stream(stream)),
+           "tp_prox_tnn_batched")
+    return Xs
+
+
+def exported_symbols():
+    """Names of the C-ABI functions declared in include/tp.h."""
+    return sorted(_SIGS)

@@ -1,0 +1,85 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every function
+that include/tp.h declares; argument validation that returns before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tp.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1806_07247_gb300 import build, tp
+    if not os.path.exists(tp.LIB_PATH):
+        build.build()
+    return tp.lib()
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tp_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for need in ["tp_tprod", "tp_tran", "tp_tsvd", "tp_tnn", "tp_tsn", "tp_prox_tnn",
+                 "tp_prox_tnn_batched", "tp_tubalrank", "tp_status_string", "tp_options_default"]:
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1806_07247_gb300 import tp
+    assert sorted(tp.exported_symbols()) == _declared()
+
+
+def test_status_strings(L):
+    from paper_1806_07247_gb300 import tp
+    assert tp.status_string(0) == "TP_OK"
+    assert tp.status_string(5) == "TP_ERR_NOT_CONVERGED"
+    assert tp.status_string(99) == "TP_ERR_UNKNOWN"
+
+
+def test_options_default(L):
+    from paper_1806_07247_gb300 import tp
+    o = tp.Options()
+    L.tp_options_default(ctypes.byref(o))
+    assert (o.precision, o.econ, o.max_sweeps, o.sync, o.jacobi_tol) == (0, 0, 30, 1, 0.0)
+    assert o.sweeps_out is None
+
+
+def test_negative_dims_rejected_before_any_cuda_call(L):
+    from paper_1806_07247_gb300 import tp
+    assert L.tp_tran(None, None, -1, 2, 3, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_tprod(None, None, None, 2, -2, 2, 2, None, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_tsvd(None, None, None, None, 2, 2, -1, None, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_prox_tnn(None, None, -3, 2, 2, 0.5, None, None) == tp.TP_ERR_INVALID_ARG
+
+
+def test_limits_and_bad_options_rejected(L):
+    from paper_1806_07247_gb300 import tp
+    assert L.tp_tran(None, None, 2, 2, tp.MAX_N3 + 1, None) == tp.TP_ERR_UNSUPPORTED
+    o = tp.options()
+    o.precision = 7
+    assert L.tp_tprod(None, None, None, 2, 2, 2, 2, ctypes.byref(o), None) == tp.TP_ERR_INVALID_ARG
+    o = tp.options()
+    o.max_sweeps = -1
+    assert L.tp_prox_tnn(None, None, 2, 2, 2, 0.5, ctypes.byref(o), None) == tp.TP_ERR_INVALID_ARG
+    # tau must be >= 0 and not NaN; batched count must be >= 0
+    assert L.tp_prox_tnn(None, None, 2, 2, 2, -0.5, None, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_prox_tnn(None, None, 2, 2, 2, float("nan"), None, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_prox_tnn_batched(None, -1, None, None) == tp.TP_ERR_INVALID_ARG
+    # SVD size limit
+    d = (tp.TensorDesc * 1)()
+    d[0].inp, d[0].out, d[0].n1, d[0].n2, d[0].n3, d[0].tau = 16, 16, tp.MAX_SVD_DIM + 1, 4, 2, 0.1
+    assert L.tp_prox_tnn_batched(d, 1, None, None) == tp.TP_ERR_UNSUPPORTED
+    # null pointer for a non-empty tensor
+    assert L.tp_tran(None, None, 2, 2, 2, None) == tp.TP_ERR_INVALID_ARG
