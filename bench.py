@@ -118,15 +118,24 @@ class Clocks:
 # ----------------------------------------------------------------------------- workload
 def svd_launch_groups(shapes):
     """Kernel instantiations one batched prox call launches (mirrors the library's
-    slice planner: elements per lane and whether the slice fits in shared memory)."""
+    slice planner: lanes per column pair, float4 pairs per lane, shared or global)."""
     groups = set()
     for n1, n2 in shapes:
         m, n = max(n1, n2), min(n1, n2)
-        need = (m + 31) // 32
-        e = max(need, 1) if need <= 5 else (8 if need <= 8 else 16)
+        best, lp = 1e30, 32
+        for cand in (8, 16, 32):
+            e2 = (m + 2 * cand - 1) // (2 * cand)
+            if e2 > 8:
+                continue
+            score = (2 * cand * e2 - m) / m + 0.03 * abs(e2 - 5.0)
+            if score < best:
+                best, lp = score, cand
+        e2 = (m + 2 * lp - 1) // (2 * lp)
+        maxe2 = 2 if e2 <= 2 else (4 if e2 <= 4 else 8)
+        ld = 2 * lp * e2
         aux = (6 * n * 4 + 256 + (m + 1) * 4 + 20 * m + 15) & ~15
-        in_smem = n * (m | 1) * 8 + aux <= 227 * 1024 - 1024
-        groups.add((in_smem, e))
+        in_smem = n * ld * 8 + aux <= 227 * 1024 - 1024
+        groups.add((in_smem, lp, maxe2))
     return len(groups)
 
 

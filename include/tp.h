@@ -76,7 +76,7 @@ typedef struct tp_options {
     int32_t sync;        /* 1 (default): wait for the stream before returning and report
                             TP_ERR_NOT_CONVERGED; 0: fully asynchronous */
     double jacobi_tol;   /* rotate a column pair when |a_p^H a_q| > tol*||a_p||*||a_q||;
-                            <= 0 selects max(8, sqrt(m)) * 2^-23 */
+                            <= 0 selects 8 * 2^-23 */
     int32_t* sweeps_out; /* optional DEVICE array, one int per directly computed Fourier
                             slice (tensor-major, slice-minor): Jacobi sweeps used */
     void* const* stage_events; /* optional HOST array of 4 cudaEvent_t, recorded on `stream`

@@ -152,17 +152,18 @@ tp_status finish(uint32_t* d_status, const Opts& o, cudaStream_t s) {
 struct SvdBatch {
     struct Item {
         SvdJob job;
-        int maxe, smem, threads;
-        bool in_smem;
+        SvdConfig cfg;
         int64_t cost;
     };
     std::vector<Item> items;
 
     tp_status launch(Workspace& ws, int mode, const Opts& o, uint32_t* d_status, cudaStream_t s) {
         if (items.empty()) return TP_OK;
-        std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
-            if (a.in_smem != b.in_smem) return a.in_smem > b.in_smem;
-            if (a.maxe != b.maxe) return a.maxe < b.maxe;
+        auto key = [](const Item& a) {
+            return (a.cfg.in_smem ? 0 : 1000000) + a.cfg.lp * 100 + a.cfg.maxe;
+        };
+        std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
+            if (key(a) != key(b)) return key(a) < key(b);
             return a.cost > b.cost;
         });
         std::vector<SvdJob> jobs(items.size());
@@ -180,17 +181,17 @@ struct SvdBatch {
         while (i < items.size()) {
             size_t j = i;
             int smem = 0, threads = 0;
-            while (j < items.size() && items[j].in_smem == items[i].in_smem &&
-                   items[j].maxe == items[i].maxe) {
-                smem = std::max(smem, items[j].smem);
-                threads = std::max(threads, items[j].threads);
+            while (j < items.size() && key(items[j]) == key(items[i])) {
+                smem = std::max(smem, items[j].cfg.smem_bytes);
+                threads = std::max(threads, items[j].cfg.threads);
                 ++j;
             }
             SvdLaunch L;
             L.jobs = d_jobs + i;
             L.njobs = (int)(j - i);
-            L.maxe = items[i].maxe;
-            L.in_smem = items[i].in_smem;
+            L.lp = items[i].cfg.lp;
+            L.maxe = items[i].cfg.maxe;
+            L.in_smem = items[i].cfg.in_smem;
             L.smem_bytes = smem;
             L.threads = threads;
             TP_CUDA(launch_svd(L, p, s));
@@ -240,18 +241,15 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     // sizes first
     size_t bytes = Workspace::round(sizeof(uint32_t));
     int64_t slices = 0;
-    std::vector<int> maxe(count), smem(count), thr(count);
-    std::vector<char> insm(count);
-    std::vector<int64_t> work(count);
+    std::vector<SvdConfig> cfg(count);
+    std::vector<int64_t> work(count, 0);
     int64_t nfft = 0;
     for (int64_t t = 0; t < count; ++t) {
         const int64_t n1 = d[t].n1, n2 = d[t].n2, n3 = d[t].n3;
         if (n1 == 0 || n2 == 0 || n3 == 0) continue;
         const int h = free_slices((int)n3);
-        bool sm = false;
-        if (!svd_plan((int)n1, (int)n2, SVD_PROX, &maxe[t], &sm, &smem[t], &thr[t], &work[t]))
-            return TP_ERR_UNSUPPORTED;
-        insm[t] = sm;
+        if (!svd_plan((int)n1, (int)n2, SVD_PROX, &cfg[t])) return TP_ERR_UNSUPPORTED;
+        work[t] = cfg[t].work_elems;
         bytes += cbytes(n1 * n2 * h);
         if (work[t] > 0) bytes += cbytes(work[t] * h);
         slices += h;
@@ -291,10 +289,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             j.ucols = j.vcols = 0;
             j.sweeps_index = (int32_t)(sidx++);
             j.tau = d[t].tau;
-            it.maxe = maxe[t];
-            it.smem = smem[t];
-            it.threads = thr[t];
-            it.in_smem = insm[t] != 0;
+            it.cfg = cfg[t];
             const int64_t m = std::max(n1, n2), n = std::min(n1, n2);
             it.cost = m * n * n;
             svd.items.push_back(it);
@@ -315,11 +310,9 @@ tp_status sigma_op(const float* A, int64_t n1, int64_t n2, int64_t n3, int kind,
                    double* out_d, int64_t* out_i, double* s_out, const Opts& o, cudaStream_t s) {
     const int h = free_slices((int)n3);
     const int64_t r = std::min(n1, n2), P = n1 * n2;
-    int maxe, smem, thr;
-    bool sm;
-    int64_t work;
-    if (!svd_plan((int)n1, (int)n2, SVD_SIGMA, &maxe, &sm, &smem, &thr, &work))
-        return TP_ERR_UNSUPPORTED;
+    SvdConfig cfg;
+    if (!svd_plan((int)n1, (int)n2, SVD_SIGMA, &cfg)) return TP_ERR_UNSUPPORTED;
+    const int64_t work = cfg.work_elems;
     size_t bytes = Workspace::round(4) + cbytes(P * h) + (work ? cbytes(work * h) : 0) +
                    Workspace::round(sizeof(float) * r * h) + 2 * Workspace::round(sizeof(FftJob)) +
                    Workspace::round(sizeof(SvdJob) * h);
@@ -348,10 +341,7 @@ tp_status sigma_op(const float* A, int64_t n1, int64_t n2, int64_t n3, int kind,
         j.ucols = j.vcols = 0;
         j.sweeps_index = k;
         j.tau = 0.0;
-        it.maxe = maxe;
-        it.smem = smem;
-        it.threads = thr;
-        it.in_smem = sm;
+        it.cfg = cfg;
         it.cost = 0;
         svd.items.push_back(it);
     }
@@ -460,11 +450,9 @@ tp_status tp_tsvd(const float* A, float* U, float* S, float* V, int64_t n1, int6
     const int64_t sS1 = o.econ ? r : n1, sS2 = o.econ ? r : n2;
     if (n1 * ucols >= ((int64_t)1 << 31) || n2 * vcols >= ((int64_t)1 << 31))
         return TP_ERR_UNSUPPORTED;
-    int maxe, smem, thr;
-    bool sm;
-    int64_t work;
-    if (!svd_plan((int)n1, (int)n2, SVD_FULL, &maxe, &sm, &smem, &thr, &work))
-        return TP_ERR_UNSUPPORTED;
+    SvdConfig cfg;
+    if (!svd_plan((int)n1, (int)n2, SVD_FULL, &cfg)) return TP_ERR_UNSUPPORTED;
+    const int64_t work = cfg.work_elems;
     TP_TRY(prepare());
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int h = free_slices((int)n3);
@@ -504,10 +492,7 @@ tp_status tp_tsvd(const float* A, float* U, float* S, float* V, int64_t n1, int6
         j.vcols = (int)vcols;
         j.sweeps_index = k;
         j.tau = 0.0;
-        it.maxe = maxe;
-        it.smem = smem;
-        it.threads = thr;
-        it.in_smem = sm;
+        it.cfg = cfg;
         it.cost = 0;
         svd.items.push_back(it);
     }

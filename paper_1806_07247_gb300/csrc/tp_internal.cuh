@@ -69,10 +69,18 @@ struct SvdJob {
 struct SvdLaunch {
     const SvdJob* jobs;  // device array
     int njobs;
-    int maxe;            // elements per lane: m <= 32*maxe
+    int lp;              // lanes per column pair (8, 16, 32)
+    int maxe;            // elements per lane: m <= lp*maxe
     bool in_smem;        // working matrix in shared memory
     int smem_bytes;
     int threads;
+};
+
+// Launch configuration of one slice size (see svd_plan).
+struct SvdConfig {
+    int lp, maxe, smem_bytes, threads;
+    bool in_smem;
+    int64_t work_elems;  // global scratch elements (float2) per slice
 };
 
 struct SvdParams {
@@ -84,8 +92,7 @@ struct SvdParams {
 };
 
 // Which launch configuration a slice of size n1 x n2 needs.
-bool svd_plan(int n1, int n2, int mode, int* maxe, bool* in_smem, int* smem_bytes,
-              int* threads, int64_t* work_elems);
+bool svd_plan(int n1, int n2, int mode, SvdConfig* cfg);
 cudaError_t launch_svd(const SvdLaunch& L, const SvdParams& p, cudaStream_t s);
 
 // Reductions over the sorted singular values of one tensor (tnn, tsn, tubal rank).

@@ -21,13 +21,19 @@
 // gamma is real, e = +-1, and the arithmetic stays real.
 //
 // Parallel order.  Each sweep is the round-robin tournament over n (rounded up to even)
-// columns: n' - 1 rounds of n'/2 disjoint pairs; pairs of a round go to different warps,
-// a warp holds its two columns in registers (MAXE elements per lane) between the dot
-// products and the update.  A sweep with no rotation ends the iteration.
+// columns: n' - 1 rounds of n'/2 disjoint pairs.  A pair is handled by a group of LP
+// lanes (LP = 8, 16 or 32 by column length, so that each lane holds several elements);
+// a warp carries 32/LP pairs at once and the CTA is sized to the pairs of a round.  The
+// group holds its two columns in registers (up to 2*MAXE2 elements per lane) between the dot
+// products and the update, reduces within the group with xor shuffles, and forms the
+// rotation with refined reciprocal square roots (rotation_cs keeps c^2 + s^2 = 1 to an ulp,
+// which is what bounds the singular value error; computing c and s in FP64 is no better).  A sweep with no rotation ends the
+// iteration.
 //
-// Working storage.  G lives in shared memory (row stride m rounded up to odd, which keeps
-// the 64-bit accesses of a warp free of bank conflicts) when it fits, otherwise in a
-// global scratch area of the slice.  SVD_FULL accumulates V in global scratch.
+// Working storage.  G lives in shared memory when it fits, otherwise in a global scratch
+// area of the slice; its columns are zero-padded to 2*LP*e2 entries so that each lane owns
+// e2 float4 pairs (8 lanes of a quarter-warp read 128 contiguous bytes: no bank conflicts,
+// no bounds tests in the rotation loop).  SVD_FULL accumulates V in global scratch.
 //
 // The SVT epilogue needs no V: u_j = b_j / sigma_j and v_j^* = b_j^* A_G / sigma_j^2,
 // so W_G = sum_{sigma_j > tau} ((sigma_j - tau) / sigma_j) (1/sigma_j^2) b_j (b_j^* g_c)
@@ -79,59 +85,138 @@ __device__ __forceinline__ int block_argmax(float key, int idx, float* redf, int
     return bi;
 }
 
-// One Jacobi rotation of columns gp, gq (length m) and, for SVD_FULL, of the
-// accumulated V columns vp, vq (length nv).  Returns true if the pair was rotated.
-template <int MAXE, bool WITH_V>
-__device__ __forceinline__ bool jacobi_pair(float2* gp, float2* gq, int m, int lane, float tol,
-                                            float2* vp, float2* vq, int nv) {
-    float2 xp[MAXE], xq[MAXE];
+// Sum over the aligned group of LP lanes holding one column pair.
+template <int LP>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = LP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// 1/sqrt(x) and 1/x from the hardware approximations plus one Newton step (about 1 ulp).
+__device__ __forceinline__ float rsqrt_nr(float x) {
+    const float r = rsqrtf(x);
+    return r * fmaf(-0.5f * x * r, r, 1.5f);
+}
+__device__ __forceinline__ float rcp_nr(float x) {
+    const float r = __fdividef(1.f, x);
+    return r * fmaf(-x, r, 2.f);
+}
+
+// Cosine and sine of the Jacobi rotation with tangent t (|t| <= 1): c = 1/sqrt(1 + t^2),
+// s = c t.  c^2 + s^2 = 1 must hold to about an ulp with no bias, because every column is
+// rotated some n * sweeps times and a biased norm drift accumulates into the singular
+// values.  1 + t^2 is therefore kept exactly as qh + ql (error-free product and Fast2Sum),
+// and the hardware reciprocal square root gets one Newton step whose residual
+// 1 - (qh + ql) r^2 is evaluated with the exact product qh r = h + hl.  The _rn intrinsics
+// keep the compiler from fusing or reassociating these steps.
+__device__ __forceinline__ void rotation_cs(float t, float& c, float& s) {
+    const float hi = __fmul_rn(t, t);
+    const float lo = fmaf(t, t, -hi);
+    const float qh = __fadd_rn(1.f, hi);
+    const float ql = __fadd_rn(__fadd_rn(__fsub_rn(1.f, qh), hi), lo);
+    const float r = rsqrtf(qh);
+    const float h = __fmul_rn(qh, r);
+    const float hl = fmaf(qh, r, -h);
+    const float rho = __fsub_rn(fmaf(-h, r, 1.f), r * fmaf(ql, r, hl));
+    c = fmaf(0.5f * r, rho, r);
+    s = __fmul_rn(c, t);
+}
+
+// Sums of four values over the aligned LP-lane group (LP >= 8), returned in every lane:
+// the first two xor steps exchange halves of the set, so log2(LP) + 5 shuffles replace
+// the 4 log2(LP) of four separate reductions.
+template <int LP>
+__device__ __forceinline__ void group_sum4(float& v0, float& v1, float& v2, float& v3,
+                                           int sub, int lane) {
+    const bool h1 = (sub & (LP / 2)) != 0;
+    float k0 = h1 ? v2 : v0, k1 = h1 ? v3 : v1;
+    const float s0 = h1 ? v0 : v2, s1 = h1 ? v1 : v3;
+    k0 += __shfl_xor_sync(0xffffffffu, s0, LP / 2);
+    k1 += __shfl_xor_sync(0xffffffffu, s1, LP / 2);
+    const bool h2 = (sub & (LP / 4)) != 0;
+    float k = h2 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, h2 ? k0 : k1, LP / 4);
+#pragma unroll
+    for (int o = LP / 8; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    // lane with (h1, h2) = (a, b) now holds the total of value 2a + b
+    const int base = lane - sub;
+    v0 = __shfl_sync(0xffffffffu, k, base);
+    v1 = __shfl_sync(0xffffffffu, k, base + LP / 4);
+    v2 = __shfl_sync(0xffffffffu, k, base + LP / 2);
+    v3 = __shfl_sync(0xffffffffu, k, base + LP / 2 + LP / 4);
+}
+
+// One Jacobi rotation of columns gp, gq by the LP-lane group whose lane index within the
+// group is `sub`; for SVD_FULL also of the accumulated V columns vp, vq (length nv).
+// Columns are zero-padded to 2*LP*e2 complex entries, so lane `sub` owns the float4 pairs
+// sub + LP*i, i < e2, with no bounds test (zero rows stay zero under rotation).  Every lane
+// of the warp must call this (the reductions use the full warp mask); inactive groups read
+// column 0 and discard the result.  Returns true if the pair was rotated.
+template <int LP, int MAXE2, bool WITH_V>
+__device__ __forceinline__ bool jacobi_pair(float2* gp, float2* gq, int e2, int sub, int lane,
+                                            float tol2, bool active, float2* vp, float2* vq,
+                                            int nv) {
+    float4* p4 = reinterpret_cast<float4*>(gp);
+    float4* q4 = reinterpret_cast<float4*>(gq);
+    float4 xp[MAXE2], xq[MAXE2];
     float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
 #pragma unroll
-    for (int i = 0; i < MAXE; ++i) {
-        const int e = lane + 32 * i;
-        if (e < m) {
-            xp[i] = gp[e];
-            xq[i] = gq[e];
-        } else {
-            xp[i] = make_float2(0.f, 0.f);
-            xq[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < MAXE2; ++i) {
+        if (i < e2) {
+            const float4 a = p4[sub + LP * i], b = q4[sub + LP * i];
+            xp[i] = a;
+            xq[i] = b;
+            al = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, al))));
+            be = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, be))));
+            gr = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, gr))));
+            gi = fmaf(a.x, b.y, fmaf(-a.y, b.x, fmaf(a.z, b.w, fmaf(-a.w, b.z, gi))));
         }
-        al = fmaf(xp[i].x, xp[i].x, fmaf(xp[i].y, xp[i].y, al));
-        be = fmaf(xq[i].x, xq[i].x, fmaf(xq[i].y, xq[i].y, be));
-        gr = fmaf(xp[i].x, xq[i].x, fmaf(xp[i].y, xq[i].y, gr));
-        gi = fmaf(xp[i].x, xq[i].y, fmaf(-xp[i].y, xq[i].x, gi));
     }
-    al = warp_sum(al);
-    be = warp_sum(be);
-    gr = warp_sum(gr);
-    gi = warp_sum(gi);
-    const float ag = sqrtf(fmaf(gr, gr, gi * gi));
-    if (!(ag > tol * sqrtf(al) * sqrtf(be))) return false;
-    const float zeta = (be - al) / (2.f * ag);
+    group_sum4<LP>(al, be, gr, gi, sub, lane);
+    const float ag2 = fmaf(gr, gr, gi * gi);
+    // |gamma| > tol sqrt(alpha beta), squared
+    if (!active || !(ag2 > (tol2 * al) * be)) return false;
+    const float inv_ag = rsqrt_nr(ag2);
+    const float zeta = 0.5f * (be - al) * inv_ag;
     const float az = fabsf(zeta);
-    float t = (az > 1e8f) ? 0.5f / az : 1.f / (az + sqrtf(fmaf(zeta, zeta, 1.f)));
+    float t;
+    if (az > 1e8f) {
+        t = 0.5f * rcp_nr(az);
+    } else {
+        const float q = fmaf(zeta, zeta, 1.f);
+        t = rcp_nr(az + q * rsqrt_nr(q));
+    }
     t = copysignf(t, zeta);
-    const float c = 1.f / sqrtf(fmaf(t, t, 1.f));
-    const float s = c * t;
-    const float er = gr / ag, ei = gi / ag;
+    float c, s;
+    rotation_cs(t, c, s);
+    const float er = gr * inv_ag, ei = gi * inv_ag;
+    const float sr = s * er, si = s * ei;  // s e; s conj(e) = (sr, -si)
+    // g_p <- c g_p - s conj(e) g_q,  g_q <- s e g_p + c g_q
 #pragma unroll
-    for (int i = 0; i < MAXE; ++i) {
-        const int e = lane + 32 * i;
-        if (e < m) {
-            const float2 a = xp[i], b = xq[i];
-            const float cbx = fmaf(er, b.x, ei * b.y), cby = fmaf(er, b.y, -ei * b.x);  // conj(e) b
-            const float eax = fmaf(er, a.x, -ei * a.y), eay = fmaf(er, a.y, ei * a.x);  // e a
-            gp[e] = make_float2(fmaf(c, a.x, -s * cbx), fmaf(c, a.y, -s * cby));
-            gq[e] = make_float2(fmaf(s, eax, c * b.x), fmaf(s, eay, c * b.y));
+    for (int i = 0; i < MAXE2; ++i) {
+        if (i < e2) {
+            const float4 a = xp[i], b = xq[i];
+            float4 np, nq;
+            np.x = fmaf(c, a.x, fmaf(-sr, b.x, -si * b.y));
+            np.y = fmaf(c, a.y, fmaf(-sr, b.y, si * b.x));
+            np.z = fmaf(c, a.z, fmaf(-sr, b.z, -si * b.w));
+            np.w = fmaf(c, a.w, fmaf(-sr, b.w, si * b.z));
+            nq.x = fmaf(sr, a.x, fmaf(-si, a.y, c * b.x));
+            nq.y = fmaf(sr, a.y, fmaf(si, a.x, c * b.y));
+            nq.z = fmaf(sr, a.z, fmaf(-si, a.w, c * b.z));
+            nq.w = fmaf(sr, a.w, fmaf(si, a.z, c * b.w));
+            p4[sub + LP * i] = np;
+            q4[sub + LP * i] = nq;
         }
     }
     if (WITH_V) {
-        for (int e = lane; e < nv; e += 32) {
+        for (int e = sub; e < nv; e += LP) {
             const float2 a = vp[e], b = vq[e];
-            const float cbx = fmaf(er, b.x, ei * b.y), cby = fmaf(er, b.y, -ei * b.x);
-            const float eax = fmaf(er, a.x, -ei * a.y), eay = fmaf(er, a.y, ei * a.x);
-            vp[e] = make_float2(fmaf(c, a.x, -s * cbx), fmaf(c, a.y, -s * cby));
-            vq[e] = make_float2(fmaf(s, eax, c * b.x), fmaf(s, eay, c * b.y));
+            vp[e] = make_float2(fmaf(c, a.x, fmaf(-sr, b.x, -si * b.y)),
+                                fmaf(c, a.y, fmaf(-sr, b.y, si * b.x)));
+            vq[e] = make_float2(fmaf(sr, a.x, fmaf(-si, a.y, c * b.x)),
+                                fmaf(sr, a.y, fmaf(si, a.x, c * b.y)));
         }
     }
     return true;
@@ -144,11 +229,15 @@ __host__ __device__ inline int aux_bytes(int m, int n) {
     return (b + 15) & ~15;
 }
 
-__host__ __device__ inline int odd_ld(int m) { return m | 1; }
+// Column stride of G in complex entries: m rounded up to whole float4 pairs of every lane
+// of a group (zero rows pad the tail).
+__host__ __device__ inline int col_e2(int m, int lp) { return (m + 2 * lp - 1) / (2 * lp); }
+__host__ __device__ inline int col_ld(int m, int lp) { return 2 * lp * col_e2(m, lp); }
 
-template <int MODE, int MAXE, bool SMEM>
-__global__ void __launch_bounds__(kMaxThreads, 1) svd_kernel(const SvdJob* __restrict__ jobs,
-                                                              SvdParams prm) {
+template <int MODE, int LP, int MAXE2, bool SMEM>
+__global__ void __launch_bounds__(MAXE2 >= 8 ? 512 : 1024, 1)
+    svd_kernel(const SvdJob* __restrict__ jobs, SvdParams prm) {
+    constexpr int MAXE = 2 * MAXE2;  // complex elements per lane in the scalar phases
     extern __shared__ float4 smem4[];
     __shared__ int s_rot, s_cnt;
     const SvdJob J = jobs[blockIdx.x];
@@ -158,8 +247,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) svd_kernel(const SvdJob* __res
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int T = blockDim.x;
     const bool real = J.real_slice != 0;
+    constexpr int SPW = 32 / LP;             // pairs (or columns) a warp carries at once
+    const int grp = lane / LP, sub = lane % LP;
+    const int slots = nw * SPW;
+    const int slot = warp * SPW + grp;
 
-    const int ld = SMEM ? odd_ld(m) : m;
+    const int e2 = col_e2(m, LP);
+    const int ld = col_ld(m, LP);
     float2* G = SMEM ? reinterpret_cast<float2*>(smem4) : J.work;
     char* auxp = reinterpret_cast<char*>(smem4) + (SMEM ? (size_t)n * ld * sizeof(float2) : 0);
     float* sig = reinterpret_cast<float*>(auxp);
@@ -176,9 +270,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) svd_kernel(const SvdJob* __res
     int* valid = reinterpret_cast<int*>(dco + m);
 
     float2* VG = nullptr;
-    if (MODE == SVD_FULL) VG = SMEM ? J.work : J.work + (size_t)m * n;
+    if (MODE == SVD_FULL) VG = SMEM ? J.work : J.work + (size_t)n * ld;
 
-    // ---- load G (= A or A^H) -------------------------------------------------
+    // ---- load G (= A or A^H), zero rows m..ld-1 --------------------------------
+    if (ld > m) {
+        const int pad = ld - m;
+        for (int idx = tid; idx < n * pad; idx += T) {
+            const int c = idx / pad, e = m + (idx - c * pad);
+            G[(size_t)c * ld + e] = make_float2(0.f, 0.f);
+        }
+    }
     if (!tr) {
         for (int idx = tid; idx < m * n; idx += T) {
             const int c = idx / m, e = idx - c * m;
@@ -203,7 +304,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) svd_kernel(const SvdJob* __res
     __syncthreads();
 
     // ---- Jacobi sweeps ----------------------------------------------------------
-    const float tol = prm.tol > 0.f ? prm.tol : fmaxf(8.f, sqrtf((float)m)) * kEps;
+    const float tol = prm.tol > 0.f ? prm.tol : 8.f * kEps;
+    const float tol2 = tol * tol;
     const int N = n + (n & 1);
     int sweeps = 0;
     bool converged = n < 2;
@@ -211,17 +313,18 @@ __global__ void __launch_bounds__(kMaxThreads, 1) svd_kernel(const SvdJob* __res
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int r = 0; r < N - 1; ++r) {
-            for (int pi = warp; pi < N / 2; pi += nw) {
-                int a, b;
+            for (int base = 0; base < N / 2; base += slots) {  // uniform over the block
+                const int pi = base + slot;
+                int a = 0, b = 0;
                 if (pi == 0) { a = N - 1; b = r; }
                 else { a = (r + pi) % (N - 1); b = (r - pi + N - 1) % (N - 1); }
-                if (a >= n || b >= n) continue;
-                const int p = min(a, b), q = max(a, b);
-                bool did = jacobi_pair<MAXE, MODE == SVD_FULL>(
-                    G + (size_t)p * ld, G + (size_t)q * ld, m, lane, tol,
+                const bool active = pi < N / 2 && a < n && b < n;
+                const int p = active ? min(a, b) : 0, q = active ? max(a, b) : 0;
+                bool did = jacobi_pair<LP, MAXE2, MODE == SVD_FULL>(
+                    G + (size_t)p * ld, G + (size_t)q * ld, e2, sub, lane, tol2, active,
                     MODE == SVD_FULL ? VG + (size_t)p * n : nullptr,
                     MODE == SVD_FULL ? VG + (size_t)q * n : nullptr, n);
-                if (did && lane == 0) s_rot = 1;
+                if (did && sub == 0) s_rot = 1;
             }
             __syncthreads();
         }
@@ -235,12 +338,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) svd_kernel(const SvdJob* __res
     }
 
     // ---- column norms: sigma_j = ||b_j|| ----------------------------------------
-    for (int c = warp; c < n; c += nw) {
-        const float2* g = G + (size_t)c * ld;
+    for (int cb = 0; cb < n; cb += slots) {  // uniform over the block
+        const int c = cb + slot;
         float s = 0.f;
-        for (int e = lane; e < m; e += 32) s = fmaf(g[e].x, g[e].x, fmaf(g[e].y, g[e].y, s));
-        s = warp_sum(s);
-        if (lane == 0) sig[c] = sqrtf(s);
+        if (c < n) {
+            const float2* g = G + (size_t)c * ld;
+            for (int e = sub; e < m; e += LP) s = fmaf(g[e].x, g[e].x, fmaf(g[e].y, g[e].y, s));
+        }
+        s = group_sum<LP>(s);
+        if (c < n && sub == 0) sig[c] = sqrtf(s);
     }
     __syncthreads();
 
@@ -285,13 +391,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) svd_kernel(const SvdJob* __res
         __syncthreads();
         const int cnt = s_cnt;
         // W_G(:, c) = sum_k ratio_k invs_k^2 b_k (b_k^H g_c), g_c re-read from the slice
-        for (int c = warp; c < n; c += nw) {
+        for (int cb = 0; cb < n; cb += slots) {  // uniform over the block
+            const int c = cb + slot;
+            const bool act = c < n;
             float2 a[MAXE], w[MAXE];
 #pragma unroll
             for (int i = 0; i < MAXE; ++i) {
-                const int e = lane + 32 * i;
+                const int e = sub + LP * i;
                 float2 v = make_float2(0.f, 0.f);
-                if (e < m) {
+                if (act && e < m) {
                     v = tr ? J.A[c + (int64_t)n1 * e] : J.A[e + (int64_t)n1 * c];
                     if (tr) v.y = -v.y;
                     if (real) v.y = 0.f;
@@ -305,21 +413,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1) svd_kernel(const SvdJob* __res
                 float dr = 0.f, di = 0.f;
 #pragma unroll
                 for (int i = 0; i < MAXE; ++i) {
-                    const int e = lane + 32 * i;
+                    const int e = sub + LP * i;
                     if (e < m) {
                         const float2 bv = b[e];
                         dr = fmaf(bv.x, a[i].x, fmaf(bv.y, a[i].y, dr));
                         di = fmaf(bv.x, a[i].y, fmaf(-bv.y, a[i].x, di));
                     }
                 }
-                dr = warp_sum(dr);
-                di = warp_sum(di);
+                dr = group_sum<LP>(dr);
+                di = group_sum<LP>(di);
                 const float sc = ratio[j] * invs[j] * invs[j];
                 dr *= sc;
                 di *= sc;
 #pragma unroll
                 for (int i = 0; i < MAXE; ++i) {
-                    const int e = lane + 32 * i;
+                    const int e = sub + LP * i;
                     if (e < m) {
                         const float2 bv = b[e];
                         w[i].x = fmaf(dr, bv.x, fmaf(-di, bv.y, w[i].x));
@@ -327,14 +435,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) svd_kernel(const SvdJob* __res
                     }
                 }
             }
+            if (act) {
 #pragma unroll
-            for (int i = 0; i < MAXE; ++i) {
-                const int e = lane + 32 * i;
-                if (e < m) {
-                    float2 v = w[i];
-                    if (real) v.y = 0.f;
-                    if (tr) J.W[c + (int64_t)n1 * e] = make_float2(v.x, -v.y);
-                    else J.W[e + (int64_t)n1 * c] = v;
+                for (int i = 0; i < MAXE; ++i) {
+                    const int e = sub + LP * i;
+                    if (e < m) {
+                        float2 v = w[i];
+                        if (real) v.y = 0.f;
+                        if (tr) J.W[c + (int64_t)n1 * e] = make_float2(v.x, -v.y);
+                        else J.W[e + (int64_t)n1 * c] = v;
+                    }
                 }
             }
         }
@@ -444,9 +554,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) svd_kernel(const SvdJob* __res
     }
 }
 
-template <int MODE, int MAXE, bool SMEM>
+template <int MODE, int LP, int MAXE2, bool SMEM>
 cudaError_t launch_one(const SvdLaunch& L, const SvdParams& p, cudaStream_t s) {
-    auto k = svd_kernel<MODE, MAXE, SMEM>;
+    auto k = svd_kernel<MODE, LP, MAXE2, SMEM>;
     if (L.smem_bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              L.smem_bytes);
@@ -457,22 +567,24 @@ cudaError_t launch_one(const SvdLaunch& L, const SvdParams& p, cudaStream_t s) {
 }
 
 template <int MODE, bool SMEM>
-cudaError_t launch_maxe(const SvdLaunch& L, const SvdParams& p, cudaStream_t s) {
-    switch (L.maxe) {
-        case 1: return launch_one<MODE, 1, SMEM>(L, p, s);
-        case 2: return launch_one<MODE, 2, SMEM>(L, p, s);
-        case 3: return launch_one<MODE, 3, SMEM>(L, p, s);
-        case 4: return launch_one<MODE, 4, SMEM>(L, p, s);
-        case 5: return launch_one<MODE, 5, SMEM>(L, p, s);
-        case 8: return launch_one<MODE, 8, SMEM>(L, p, s);
-        case 16: return launch_one<MODE, 16, SMEM>(L, p, s);
+cudaError_t launch_cfg(const SvdLaunch& L, const SvdParams& p, cudaStream_t s) {
+    switch (L.lp * 100 + L.maxe) {
+        case 802: return launch_one<MODE, 8, 2, SMEM>(L, p, s);
+        case 804: return launch_one<MODE, 8, 4, SMEM>(L, p, s);
+        case 808: return launch_one<MODE, 8, 8, SMEM>(L, p, s);
+        case 1602: return launch_one<MODE, 16, 2, SMEM>(L, p, s);
+        case 1604: return launch_one<MODE, 16, 4, SMEM>(L, p, s);
+        case 1608: return launch_one<MODE, 16, 8, SMEM>(L, p, s);
+        case 3202: return launch_one<MODE, 32, 2, SMEM>(L, p, s);
+        case 3204: return launch_one<MODE, 32, 4, SMEM>(L, p, s);
+        case 3208: return launch_one<MODE, 32, 8, SMEM>(L, p, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int MODE>
 cudaError_t launch_mode(const SvdLaunch& L, const SvdParams& p, cudaStream_t s) {
-    return L.in_smem ? launch_maxe<MODE, true>(L, p, s) : launch_maxe<MODE, false>(L, p, s);
+    return L.in_smem ? launch_cfg<MODE, true>(L, p, s) : launch_cfg<MODE, false>(L, p, s);
 }
 
 // Reductions over the decreasing singular values sigma[k * r + i] of the h directly
@@ -560,26 +672,40 @@ __global__ void diag_scatter_kernel(const float* __restrict__ tubes, int r, int 
 
 }  // namespace
 
-bool svd_plan(int n1, int n2, int mode, int* maxe, bool* in_smem, int* smem_bytes, int* threads,
-              int64_t* work_elems) {
+bool svd_plan(int n1, int n2, int mode, SvdConfig* cfg) {
     const int m = n1 > n2 ? n1 : n2, n = n1 > n2 ? n2 : n1;
-    if (m > TP_MAX_SVD_DIM || n < 0) return false;
-    const int need = (m + 31) / 32;
-    int e = need <= 5 ? (need < 1 ? 1 : need) : (need <= 8 ? 8 : 16);
-    *maxe = e;
+    if (m > TP_MAX_SVD_DIM || n < 0 || m < 1) return false;
+    // lanes per column pair: little zero padding, about 4-6 float4 pairs per lane
+    int lp = 32;
+    double best = 1e30;
+    for (int cand : {8, 16, 32}) {
+        const int e2 = col_e2(m, cand);
+        if (e2 > 8) continue;
+        const double score = (double)(col_ld(m, cand) - m) / m + 0.03 * fabs(e2 - 5.0);
+        if (score < best) { best = score; lp = cand; }
+    }
+    const int e2 = col_e2(m, lp);
+    const int maxe2 = e2 <= 2 ? 2 : (e2 <= 4 ? 4 : 8);
+    cfg->lp = lp;
+    cfg->maxe = maxe2;
+    const int ld = col_ld(m, lp);
     const int aux = aux_bytes(m, n);
-    const int64_t gbytes = (int64_t)n * odd_ld(m) * sizeof(float2);
+    const int64_t gbytes = (int64_t)n * ld * sizeof(float2);
     const int64_t limit = 227 * 1024 - 1024;  // static shared + margin
     const bool sm = gbytes + aux <= limit;
-    *in_smem = sm;
-    *smem_bytes = sm ? (int)(gbytes + aux) : aux;
-    const int pairs = (n + 1) / 2;
-    *threads = pairs >= 24 ? 512 : (pairs >= 8 ? 256 : 128);
-    if (e >= 8 && *threads > 256) *threads = 256;
+    cfg->in_smem = sm;
+    cfg->smem_bytes = sm ? (int)(gbytes + aux) : aux;
+    // pair slots: the pairs of a round split evenly over as few passes as the warp cap allows
+    const int pairs = (n + 1) / 2, spw = 32 / lp;
+    const int wmax = maxe2 >= 8 ? 16 : 32;
+    const int passes = (pairs + wmax * spw - 1) / (wmax * spw);
+    int warps = (pairs + passes * spw - 1) / (passes * spw);
+    warps = warps < 2 ? 2 : warps;
+    cfg->threads = 32 * warps;
     int64_t w = 0;
-    if (!sm) w += (int64_t)m * n;
+    if (!sm) w += (int64_t)n * ld;
     if (mode == SVD_FULL) w += (int64_t)n * n;
-    *work_elems = w;
+    cfg->work_elems = (w + 31) & ~(int64_t)31;  // keeps every slice's scratch 256-byte aligned
     return true;
 }
 
