@@ -175,6 +175,32 @@ typedef struct tp_tensor_desc {
 tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count,
                               const tp_options* opts, void* stream);
 
+/*
+ * tp_prox_tnn without any device allocation. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory while they run -- for instance code
+ * that must not trigger the implicit synchronisation or the latency of an allocator call
+ * inside a time-critical loop, or a process whose device memory is handed out by another
+ * framework's allocator so that the library may not obtain any of its own.
+ *
+ * It computes exactly what tp_prox_tnn computes, with the same kernels, but all scratch (the
+ * half spectrum, the per-slice job records and the status word) lives in one file-scope
+ * static device array of TP_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads the
+ * library holds until the process exits. A tensor fits when
+ *   n1*n2*(n3/2+1)*8 bytes of spectrum (+ the working matrices of slices larger than shared
+ *   memory) + about 80*(n3/2+1) bytes of job records <= 16 MiB;
+ * larger tensors are rejected with TP_ERR_UNSUPPORTED before anything is enqueued. The call
+ * never calls cudaMalloc, cudaFree or any allocating routine.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * and fills the twiddle table, with that device current; make it before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (the status word is
+ * cleared at the start of every call): calls that overlap on the GPU -- on different
+ * streams, or from several host threads without ordering -- race and must not be issued.
+ * Arguments, options, errors and aliasing (X == Y allowed) are those of tp_prox_tnn.
+ */
+#define TP_NOALLOC_SCRATCH_BYTES (16u << 20)
+tp_status tp_prox_tnn_noalloc(const float* Y, float* X, int64_t n1, int64_t n2, int64_t n3,
+                              double tau, const tp_options* opts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,7 +70,10 @@ _SIGS = {
                     [ctypes.c_double, ctypes.POINTER(Options), ctypes.c_void_p]),
     "tp_prox_tnn_batched": (ctypes.c_int, [ctypes.POINTER(TensorDesc), ctypes.c_int64,
                                            ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_prox_tnn_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int64] * 3 +
+                            [ctypes.c_double, ctypes.POINTER(Options), ctypes.c_void_p]),
 }
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 def lib() -> ctypes.CDLL:
@@ -254,6 +257,21 @@ def prox_tnn(Y: torch.Tensor, tau: float, out: torch.Tensor | None = None,
     o = opts or options()
     _check(lib().tp_prox_tnn(_ptr(Y), _ptr(X), n1, n2, n3, float(tau), ctypes.byref(o),
                              _stream(stream)), "tp_prox_tnn")
+    return X
+
+
+def prox_tnn_noalloc(Y: torch.Tensor, tau: float, out: torch.Tensor | None = None,
+                     opts: Options | None = None, stream=None) -> torch.Tensor:
+    """prox_tnn through tp_prox_tnn_noalloc: the library allocates nothing during the call
+    (its scratch is a fixed 16 MiB device array), for callers that cannot allocate device
+    memory while they run. Calls must not overlap on the GPU; `out` must be preallocated by
+    the caller if the caller itself cannot allocate."""
+    Y = _prep(Y, "Y")
+    n1, n2, n3 = Y.shape
+    X = empty(n1, n2, n3, Y.device) if out is None else out
+    o = opts or options()
+    _check(lib().tp_prox_tnn_noalloc(_ptr(Y), _ptr(X), n1, n2, n3, float(tau), ctypes.byref(o),
+                                     _stream(stream)), "tp_prox_tnn_noalloc")
     return X
 
 
