@@ -12,7 +12,8 @@ The JSON line also carries:
                 the library at stage boundaries, against the FP32 ALU peak;
   e2e           the same metric with pinned host inputs copied in and outputs copied back
                 inside the timed region;
-  tprod         t-product TFLOP/s on A 2048x1024x64 times B 1024x1024x64 (plain FP32);
+  tprod         t-product TFLOP/s on A 2048x1024x64 times B 1024x1024x64 in FP32,
+                BF16x3 and 3xTF32 slice-GEMM arithmetic;
   cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
 
 `--impl reference` times the FP64 oracle itself (host cores) on the same workload.
@@ -366,8 +367,14 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
             "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
 
 
+BF16_PEAK_TFLOPS = 1944.2        # measured dense bf16 (MEASURED_PEAKS.json, burst)
+TF32_PEAK_TFLOPS = BF16_PEAK_TFLOPS * 1.1 / 2.25   # nominal tf32 : bf16 ratio
+
+
 def tprod_leg(args, tp, synth, device):
-    """Plain FP32 t-product of A 2048x1024x64 and B 1024x1024x64 (one rank)."""
+    """t-product of A 2048x1024x64 and B 1024x1024x64 (one rank) in the three slice-GEMM
+    arithmetics. Useful flops = (2 #real + 8 #complex slices) n1 n2 l; the split forms run
+    3x that on the tensor pipe."""
     import torch
     g = synth.gemm(0)
     A, B = tp.to_device(g["A"], device), tp.to_device(g["B"], device)
@@ -378,27 +385,37 @@ def tprod_leg(args, tp, synth, device):
     nreal = 2 if n3 % 2 == 0 else 1
     flops = (2.0 * nreal + 8.0 * (h - nreal)) * n1 * n2 * l
     steps = max(3, min(args.steps, 10))
-    for _ in range(2):
-        tp.tprod(A, B, out=C, opts=tp.options(sync=False))
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
-    for s in evs:
-        for e in s:
-            e.record()
-    torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for i in range(steps):
-        tp.tprod(A, B, out=C, opts=tp.options(sync=False, stage_events=evs[i]))
-    t1.record()
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / steps
-    st = [sum(s[j].elapsed_time(s[j + 1]) for s in evs) / steps for j in range(3)]
-    gemm_tflops = flops / (st[1] / 1e3) / 1e12
-    return {"workload": "A 2048x1024x64 * B 1024x1024x64, N(0,1)", "precision": "fp32",
-            "tflops": flops / (ms / 1e3) / 1e12, "ms_per_call": ms, "flops": flops,
-            "stages_ms": {"rfft": st[0], "gemm": st[1], "irfft": st[2]},
-            "gemm_roofline": {"bound": "alu", "achieved": gemm_tflops, "peak": FP32_PEAK_TFLOPS,
-                              "unit": "TFLOP/s", "frac": gemm_tflops / FP32_PEAK_TFLOPS}}
+    out = {"workload": "A 2048x1024x64 * B 1024x1024x64, N(0,1)", "flops": flops}
+    for prec in ("fp32", "bf16x3", "3xtf32"):
+        for _ in range(2):
+            tp.tprod(A, B, out=C, opts=tp.options(precision=prec, sync=False))
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        for s_ in evs:
+            for e in s_:
+                e.record()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for i in range(steps):
+            tp.tprod(A, B, out=C, opts=tp.options(precision=prec, sync=False, stage_events=evs[i]))
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / steps
+        st = [sum(s_[j].elapsed_time(s_[j + 1]) for s_ in evs) / steps for j in range(3)]
+        gemm_tflops = flops / (st[1] / 1e3) / 1e12
+        if prec == "fp32":
+            roof = {"bound": "alu", "achieved": gemm_tflops, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": gemm_tflops / FP32_PEAK_TFLOPS}
+        else:
+            peak = BF16_PEAK_TFLOPS if prec == "bf16x3" else TF32_PEAK_TFLOPS
+            pipe = 3.0 * gemm_tflops
+            roof = {"bound": "tensor", "achieved": pipe, "peak": peak, "unit": "TFLOP/s",
+                    "frac": pipe / peak, "note": "3 split MMAs per useful flop; stage includes "
+                    "the hi/lo split kernels"}
+        out[prec] = {"tflops": flops / (ms / 1e3) / 1e12, "ms_per_call": ms,
+                     "stages_ms": {"rfft": st[0], "gemm": st[1], "irfft": st[2]},
+                     "gemm_useful_tflops": gemm_tflops, "gemm_roofline": roof}
+    return out
 
 
 def main():

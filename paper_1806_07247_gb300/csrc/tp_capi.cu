@@ -400,7 +400,6 @@ tp_status tp_tprod(const float* A, const float* B, float* C, int64_t n1, int64_t
     if (n1 == 0 || l == 0 || n3 == 0) return TP_OK;
     if (!C) return TP_ERR_INVALID_ARG;
     if (n2 > 0 && (!A || !B)) return TP_ERR_INVALID_ARG;
-    if (o.precision != TP_PREC_FP32) return TP_ERR_UNSUPPORTED;
     TP_TRY(prepare());
     if (n2 == 0) {
         TP_CUDA(cudaMemsetAsync(C, 0, sizeof(float) * n1 * l * n3, s));
@@ -408,12 +407,20 @@ tp_status tp_tprod(const float* A, const float* B, float* C, int64_t n1, int64_t
     }
     const int h = free_slices((int)n3);
     const int64_t PA = n1 * n2, PB = n2 * l, PC = n1 * l;
+    const bool tc = o.precision != TP_PREC_FP32;
+    const int64_t plane_bytes =
+        tc ? cgemm_tc_plane_bytes((int)n1, (int)l, (int)n2, h, o.precision) : 0;
     Workspace ws(s);
     TP_TRY(ws.reserve(cbytes(PA * h) + cbytes(PB * h) + cbytes(PC * h) +
-                      2 * Workspace::round(sizeof(FftJob) * 3)));
+                      2 * Workspace::round(sizeof(FftJob) * 3) + Workspace::round(4) +
+                      Workspace::round((size_t)plane_bytes)));
     float2* Ab = ws.take<float2>(PA * h);
     float2* Bb = ws.take<float2>(PB * h);
     float2* Cb = ws.take<float2>(PC * h);
+    uint32_t* d_err = ws.take<uint32_t>(1);
+    void* planes = tc ? static_cast<void*>(ws.take<char>((size_t)plane_bytes)) : nullptr;
+    TP_TRY(ws.check());
+    if (tc) TP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
     FftBatch fwd, inv;
     fwd.add(A, Ab, PA, (int)n3);
     fwd.add(B, Bb, PB, (int)n3);
@@ -421,12 +428,23 @@ tp_status tp_tprod(const float* A, const float* B, float* C, int64_t n1, int64_t
     TP_TRY(fwd.launch(ws, false, s));
     TP_TRY(o.mark(1, s));
     TP_TRY(ws.check());
-    TP_CUDA(launch_cgemm_fp32(Ab, Bb, Cb, (int)n1, (int)l, (int)n2, PA, PB, PC, h, s));
+    if (tc)
+        TP_CUDA(launch_cgemm_tc(Ab, Bb, Cb, (int)n1, (int)l, (int)n2, h, o.precision, planes, d_err, s));
+    else
+        TP_CUDA(launch_cgemm_fp32(Ab, Bb, Cb, (int)n1, (int)l, (int)n2, PA, PB, PC, h, s));
     TP_TRY(o.mark(2, s));
     inv.add(C, Cb, PC, (int)n3);
     TP_TRY(inv.launch(ws, true, s));
     TP_TRY(o.mark(3, s));
-    return finish(nullptr, o, s);
+    if (!tc) return finish(nullptr, o, s);
+    TP_TRY(finish(nullptr, o, s));
+    if (o.sync) {
+        uint32_t herr = 0;
+        TP_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaStreamSynchronize(s));
+        if (herr) return TP_ERR_CUDA;
+    }
+    return TP_OK;
 }
 
 tp_status tp_tran(const float* A, float* AT, int64_t n1, int64_t n2, int64_t n3, void* stream) {

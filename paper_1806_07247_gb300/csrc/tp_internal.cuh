@@ -48,6 +48,13 @@ int fft_tiles(int64_t P, int max_n3);
 cudaError_t launch_cgemm_fp32(const float2* A, const float2* B, float2* C, int M, int N, int K,
                               int64_t sA, int64_t sB, int64_t sC, int nslices, cudaStream_t s);
 
+// Tensor-core path (tp_gemm_tc.cu): split-precision planes (bytes below, in `planes`) and the
+// tcgen05 GEMM; `err` (device, zeroed by the caller) receives a non-zero bit on a timeout.
+int64_t cgemm_tc_plane_bytes(int M, int N, int K, int nslices, int precision);
+cudaError_t launch_cgemm_tc(const float2* A, const float2* B, float2* C, int M, int N, int K,
+                            int nslices, int precision, void* planes, uint32_t* err,
+                            cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Slice SVDs (tp_svd.cu)
 // ---------------------------------------------------------------------------
