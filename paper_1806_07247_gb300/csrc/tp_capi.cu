@@ -204,6 +204,7 @@ struct SvdBatch {
 struct FftBatch {
     std::vector<FftJob> jobs;
     int max_n3 = 1;
+    int uniform_n3 = -1;  // common n3 of all jobs, 0 once two differ
     bool vec = true;
     void add(const float* x, float2* X, int64_t P, int n3) {
         if (P <= 0 || n3 <= 0) return;
@@ -215,6 +216,7 @@ struct FftBatch {
         j.tile_begin = 0;
         jobs.push_back(j);
         max_n3 = std::max(max_n3, n3);
+        uniform_n3 = (uniform_n3 == -1 || uniform_n3 == n3) ? n3 : 0;
         vec = vec && (P % 4 == 0) && aligned16(x) && aligned16(X);
     }
     tp_status launch(Workspace& ws, bool inverse, cudaStream_t s) {
@@ -222,14 +224,15 @@ struct FftBatch {
         int64_t tiles = 0;
         for (auto& j : jobs) {
             j.tile_begin = (int32_t)tiles;
-            tiles += fft_tiles(j.P, max_n3);
+            tiles += fft_tiles(j.P, max_n3, uniform_n3);
         }
         if (tiles > 0x7fffffffLL) return TP_ERR_UNSUPPORTED;
         FftJob* d = ws.take<FftJob>(jobs.size());
         TP_TRY(ws.check());
         TP_TRY(upload(d, jobs, s));
-        cudaError_t e = inverse ? launch_irfft(d, (int)jobs.size(), (int)tiles, max_n3, vec, s)
-                                : launch_rfft(d, (int)jobs.size(), (int)tiles, max_n3, vec, s);
+        cudaError_t e =
+            inverse ? launch_irfft(d, (int)jobs.size(), (int)tiles, max_n3, uniform_n3, vec, s)
+                    : launch_rfft(d, (int)jobs.size(), (int)tiles, max_n3, uniform_n3, vec, s);
         return from_cuda(e);
     }
 };

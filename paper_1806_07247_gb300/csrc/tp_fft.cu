@@ -12,6 +12,9 @@
 // Twiddles.  w(n, m) = exp(2*pi*i*m/n) for 0 <= m < n and every n <= TP_MAX_N3 are
 // computed once per device on the host in FP64 (quarter points exact) and kept in a
 // static device table; the exponent (k*t) mod n3 is advanced by integer addition.
+//
+// This direct form serves every n3; a launch whose tubes all have the same power-of-two
+// n3 <= 64 uses the register FFT kernels further below instead.
 #include <math.h>
 
 #include <mutex>
@@ -230,6 +233,121 @@ __global__ void __launch_bounds__(kFftThreads) irfft_kernel(const FftJob* __rest
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Power-of-two n3 <= 64: one thread per tube, the tube in registers.  The real DFT of
+// length n3 = 2N is one complex FFT of length N on z[t] = x[2t] + i x[2t+1] (radix-2,
+// decimation in time, fully unrolled) followed by the split of Z into the DFTs of the even
+// and odd samples: X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[N-k]) / 2,
+// O = (Z[k] - conj Z[N-k]) / (2i), W = exp(-2 pi i / n3).  The inverse runs the same steps
+// backwards.  Twiddles are exp(2 pi i m / 64) from a constant table, indexed by
+// compile-time constants.  Loads and stores are coalesced across the threads of a warp
+// (consecutive tubes), so the kernels move each byte once.
+// ---------------------------------------------------------------------------------------
+__constant__ float2 c_tw64[64];
+
+__host__ __device__ constexpr int bit_reverse(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+__host__ __device__ constexpr int log2_pow2(int n) {
+    int b = 0;
+    while ((1 << b) < n) ++b;
+    return b;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// In-place complex FFT of length N (power of two <= 32) on data already in bit-reversed
+// order, unnormalised; INV selects exp(+2 pi i ...) kernels.  Every index is a compile-time
+// constant after unrolling, so z stays in registers.
+template <int N, bool INV>
+__device__ __forceinline__ void cfft_bitrev_regs(float2 (&z)[N]) {
+    constexpr int B = log2_pow2(N);
+#pragma unroll
+    for (int st = 0; st < B; ++st) {
+        const int m = 2 << st;
+#pragma unroll
+        for (int k = 0; k < N; k += m) {
+#pragma unroll
+            for (int j = 0; j < m / 2; ++j) {
+                float2 w = c_tw64[(64 / m) * j];
+                if (!INV) w.y = -w.y;
+                const float2 t = cmul(w, z[k + j + m / 2]);
+                const float2 u = z[k + j];
+                z[k + j] = make_float2(u.x + t.x, u.y + t.y);
+                z[k + j + m / 2] = make_float2(u.x - t.x, u.y - t.y);
+            }
+        }
+    }
+}
+
+template <int N3>
+__global__ void __launch_bounds__(256) rfft_reg_kernel(const FftJob* __restrict__ jobs, int njobs) {
+    constexpr int N = N3 / 2;
+    const FftJob J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int64_t p = (int64_t)(blockIdx.x - J.tile_begin) * 256 + threadIdx.x;
+    if (p >= J.P) return;
+    const int64_t P = J.P;
+    constexpr int B = log2_pow2(N);
+    float2 z[N];  // z[t] = x[2t] + i x[2t+1], stored at bit_reverse(t)
+#pragma unroll
+    for (int t = 0; t < N; ++t)
+        z[bit_reverse(t, B)] =
+            make_float2(__ldg(J.x + p + P * (2 * t)), __ldg(J.x + p + P * (2 * t + 1)));
+    cfft_bitrev_regs<N, false>(z);
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        const float2 zk = z[k % N], zc = z[(N - k) % N];
+        const float2 e = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+        const float2 o = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+        float2 w = c_tw64[(64 / N3) * k % 64];
+        w.y = -w.y;
+        if (k == N) w = make_float2(-1.f, 0.f);
+        float2 X = make_float2(e.x + (w.x * o.x - w.y * o.y), e.y + (w.x * o.y + w.y * o.x));
+        if (k == 0 || k == N) X.y = 0.f;
+        J.X[p + P * k] = X;
+    }
+}
+
+template <int N3>
+__global__ void __launch_bounds__(256) irfft_reg_kernel(const FftJob* __restrict__ jobs, int njobs) {
+    constexpr int N = N3 / 2;
+    const FftJob J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int64_t p = (int64_t)(blockIdx.x - J.tile_begin) * 256 + threadIdx.x;
+    if (p >= J.P) return;
+    const int64_t P = J.P;
+    float2 X[N + 1];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) X[k] = __ldg(J.X + p + P * k);
+    X[0].y = 0.f;  // the real slices of Eq. 8
+    X[N].y = 0.f;
+    constexpr int B = log2_pow2(N);
+    float2 z[N];  // Z[k] = E[k] + i O[k], stored at bit_reverse(k)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const float2 xk = X[k], xc = X[N - k];
+        const float2 e = make_float2(0.5f * (xk.x + xc.x), 0.5f * (xk.y - xc.y));
+        const float2 d = make_float2(0.5f * (xk.x - xc.x), 0.5f * (xk.y + xc.y));
+        const float2 w = c_tw64[(64 / N3) * k];   // exp(+2 pi i k / n3)
+        const float2 o = cmul(d, w);
+        z[bit_reverse(k, B)] = make_float2(e.x - o.y, e.y + o.x);
+    }
+    cfft_bitrev_regs<N, true>(z);
+    const float s = 1.f / (float)N;
+    float* xo = const_cast<float*>(J.x);
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        xo[p + P * (2 * t)] = z[t].x * s;
+        xo[p + P * (2 * t + 1)] = z[t].y * s;
+    }
+}
+
+bool reg_fft_size(int n3) { return n3 >= 2 && n3 <= 64 && (n3 & (n3 - 1)) == 0; }
+
 std::mutex g_tw_mutex;
 bool g_tw_ready[128] = {};
 
@@ -264,6 +382,8 @@ cudaError_t ensure_twiddles() {
     }
     err = cudaMemcpyToSymbol(g_twiddle, host.data(), sizeof(float2) * host.size());
     if (err != cudaSuccess) return err;
+    err = cudaMemcpyToSymbol(c_tw64, host.data() + tw_offset(64), sizeof(float2) * 64);
+    if (err != cudaSuccess) return err;
     // the largest dynamic shared memory any launch of these kernels asks for
     const int fwd = (int)fft_smem_bytes(TP_MAX_N3, false), inv = (int)fft_smem_bytes(TP_MAX_N3, true);
     int mf = fwd, mi = inv;
@@ -281,14 +401,31 @@ cudaError_t ensure_twiddles() {
     return cudaSuccess;
 }
 
-int fft_tiles(int64_t P, int max_n3) {
-    int tp = tubes_per_cta(max_n3);
+int fft_tiles(int64_t P, int max_n3, int uniform_n3) {
+    const int tp = reg_fft_size(uniform_n3) ? 256 : tubes_per_cta(max_n3);
     return (int)((P + tp - 1) / tp);
 }
 
-cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3, bool vec_ok,
-                        cudaStream_t s) {
+template <bool INV>
+cudaError_t launch_reg(const FftJob* d_jobs, int njobs, int tiles, int n3, cudaStream_t s) {
+    switch (n3) {
+#define TP_REG_CASE(n)                                                                 \
+    case n:                                                                            \
+        if (INV) irfft_reg_kernel<n><<<tiles, 256, 0, s>>>(d_jobs, njobs);             \
+        else rfft_reg_kernel<n><<<tiles, 256, 0, s>>>(d_jobs, njobs);                  \
+        break;
+        TP_REG_CASE(2) TP_REG_CASE(4) TP_REG_CASE(8) TP_REG_CASE(16) TP_REG_CASE(32)
+        TP_REG_CASE(64)
+#undef TP_REG_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
+                        int uniform_n3, bool vec_ok, cudaStream_t s) {
     if (total_tiles <= 0) return cudaSuccess;
+    if (reg_fft_size(uniform_n3)) return launch_reg<false>(d_jobs, njobs, total_tiles, uniform_n3, s);
     int tp = tubes_per_cta(max_n3);
     size_t smem = fft_smem_bytes(max_n3, false);
     if (vec_ok) rfft_kernel<true><<<total_tiles, kFftThreads, smem, s>>>(d_jobs, njobs, tp);
@@ -296,9 +433,10 @@ cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int ma
     return cudaGetLastError();
 }
 
-cudaError_t launch_irfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3, bool vec_ok,
-                         cudaStream_t s) {
+cudaError_t launch_irfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
+                         int uniform_n3, bool vec_ok, cudaStream_t s) {
     if (total_tiles <= 0) return cudaSuccess;
+    if (reg_fft_size(uniform_n3)) return launch_reg<true>(d_jobs, njobs, total_tiles, uniform_n3, s);
     int tp = tubes_per_cta(max_n3);
     size_t smem = fft_smem_bytes(max_n3, true);
     if (vec_ok) irfft_kernel<true><<<total_tiles, kFftThreads, smem, s>>>(d_jobs, njobs, tp);

@@ -33,14 +33,15 @@ struct FftJob {
 // Fills the per-device twiddle table on first use; returns cudaSuccess or the error.
 cudaError_t ensure_twiddles();
 
-// Forward real DFT of every tube, frequencies 0..h-1 (unnormalised, Eq. 2).
+// Forward real DFT of every tube, frequencies 0..h-1 (unnormalised, Eq. 2).  uniform_n3 is
+// the common n3 of all jobs of the launch, or 0 when they differ.
 cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
-                        bool vec_ok, cudaStream_t s);
+                        int uniform_n3, bool vec_ok, cudaStream_t s);
 // Inverse DFT from the half spectrum with the conjugate mirror implied, scaled by 1/n3.
 cudaError_t launch_irfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
-                         bool vec_ok, cudaStream_t s);
-// CTAs one job needs (tubes per CTA depend on the launch's largest n3).
-int fft_tiles(int64_t P, int max_n3);
+                         int uniform_n3, bool vec_ok, cudaStream_t s);
+// CTAs one job needs (tubes per CTA depend on the kernel the launch uses).
+int fft_tiles(int64_t P, int max_n3, int uniform_n3);
 
 // ---------------------------------------------------------------------------
 // Slice GEMMs (tp_gemm.cu): C_k = A_k B_k for k < nslices, complex, column-major.

@@ -140,8 +140,8 @@ extern "C" tp_status tp_prox_tnn_noalloc(const float* Y, float* X, int64_t n1, i
     if (cudaGetLastError() != cudaSuccess) return TP_ERR_CUDA;
     const bool vec = (P % 4 == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15u) == 0) &&
                      ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
-    const int tiles = fft_tiles(P, (int)n3);
-    if (launch_rfft(fft, 1, tiles, (int)n3, vec, s) != cudaSuccess) return TP_ERR_CUDA;
+    const int tiles = fft_tiles(P, (int)n3, (int)n3);
+    if (launch_rfft(fft, 1, tiles, (int)n3, (int)n3, vec, s) != cudaSuccess) return TP_ERR_CUDA;
     SvdLaunch L;
     L.jobs = svd;
     L.njobs = h;
@@ -157,7 +157,7 @@ extern "C" tp_status tp_prox_tnn_noalloc(const float* Y, float* X, int64_t n1, i
     p.sweeps_out = o.sweeps_out;
     p.status = status;
     if (launch_svd(L, p, s) != cudaSuccess) return TP_ERR_CUDA;
-    if (launch_irfft(fft + 1, 1, tiles, (int)n3, vec, s) != cudaSuccess) return TP_ERR_CUDA;
+    if (launch_irfft(fft + 1, 1, tiles, (int)n3, (int)n3, vec, s) != cudaSuccess) return TP_ERR_CUDA;
     if (!o.sync) return TP_OK;
     uint32_t hstatus = 0;
     if (cudaMemcpyAsync(&hstatus, status, sizeof(hstatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)

@@ -53,11 +53,14 @@ def test_tprod_parity(tp, dims):
     assert rel(C, ref) < TOL_FP32
 
 
-def test_tprod_identity_tensor(tp):
-    A = randn((40, 24, 9), 3)
-    Ct = host(tp, tp.tprod(dev(tp, A), dev(tp, O.teye(24, 9).astype(np.float32))))
+@pytest.mark.parametrize("n3", [1, 2, 3, 4, 8, 9, 16, 32, 64, 65, 128])
+def test_tprod_identity_tensor(tp, n3):
+    # Def. 2.3: A * I = I * A = A; covers the register FFT sizes (powers of two <= 64) and the
+    # direct DFT beside them
+    A = randn((40, 24, n3), 3)
+    Ct = host(tp, tp.tprod(dev(tp, A), dev(tp, O.teye(24, n3).astype(np.float32))))
     assert rel(Ct, A) < 1e-6
-    Ct = host(tp, tp.tprod(dev(tp, O.teye(40, 9).astype(np.float32)), dev(tp, A)))
+    Ct = host(tp, tp.tprod(dev(tp, O.teye(40, n3).astype(np.float32)), dev(tp, A)))
     assert rel(Ct, A) < 1e-6
 
 
