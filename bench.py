@@ -7,9 +7,13 @@ in {2..12} (t-product of N(0,1) factors) plus N(0, 0.05^2) noise, tau = 2x the n
 of one Fourier slice.  Metric: prox_tnn Fourier slices per second (a slice is one of the
 ceil((n3+1)/2) directly computed frontal slices of a tensor).
 
+The headline value is the learned form (rank proposer + randomized SVT, Jacobi fallback),
+with the plain FP32 Jacobi path measured beside it ("plain") on the same batch; the
+proposer is trained beforehand, untimed, on batches drawn with other seeds.
+
 The JSON line also carries:
-  roofline      the slice-SVT kernels (dominant), timed live with CUDA events recorded by
-                the library at stage boundaries, against the FP32 ALU peak;
+  roofline      the dominant slice kernel of the step, timed live with CUDA events recorded
+                by the library at stage boundaries, against the FP32 ALU peak;
   e2e           the same metric with pinned host inputs copied in and outputs copied back
                 inside the timed region;
   tprod         t-product TFLOP/s on A 2048x1024x64 times B 1024x1024x64 in FP32,
@@ -53,6 +57,8 @@ def parse():
     p.add_argument("--no-tprod", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--train-batches", type=int, default=4,
+                   help="512-tensor batches (other seeds) that label the proposer's training set")
     return p.parse_args()
 
 
@@ -224,6 +230,67 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
+def sketch_model_flops(shapes, widths, counts=None):
+    """Model count of the sketch SVT kernel for one slice of width l: five passes of an
+    n1 x n2 by n2 x l complex product (range finder, one power iteration, B, residual check),
+    four n1 x n2 complex mat-vecs (norm estimate) and the W update; 8 flops per complex MAC."""
+    total, idx = 0.0, 0
+    for n1, n2, n3 in shapes:
+        for _ in range(n3 // 2 + 1):
+            l = int(widths[idx])
+            if l > 0:
+                total += 8.0 * n1 * n2 * (5 * l + 4 + l)
+            idx += 1
+    return total
+
+
+def time_prox(tp, args, Ys, Xs, taus, descs, method, world, barrier, device, clocks=None):
+    """Warm-up, then `steps` timed batched calls with stage events; returns timing and the
+    per-slice diagnostics of the last call."""
+    import torch
+    import torch.distributed as dist
+    nsl = sum(Y.shape[2] // 2 + 1 for Y in Ys)
+    sweeps = torch.zeros(nsl, dtype=torch.int32, device=device)
+    flags = torch.zeros(nsl, dtype=torch.int32, device=device)
+    widths = torch.zeros(nsl, dtype=torch.int32, device=device)
+    for _ in range(args.warmup):
+        tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=tp.options(sync=False, method=method), descs=descs)
+    torch.cuda.synchronize()
+    tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=tp.options(sync=True, method=method, sweeps_out=sweeps,
+                                                          slice_flags_out=flags,
+                                                          sketch_width_out=widths), descs=descs)
+
+    def events():
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(tp.STAGE_EVENTS)]
+        for e in evs:
+            e.record()
+        return evs
+
+    stage = [events() for _ in range(args.steps)]
+    opts = [tp.options(sync=False, method=method, stage_events=stage[i]) for i in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    if clocks:
+        clocks.start()
+    t0.record()
+    for i in range(args.steps):
+        tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=opts[i], descs=descs)
+    t1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    names = ["rfft", "proposer", "sketch_svt", "jacobi_svt", "irfft"]
+    st = {n: sum(s_[j].elapsed_time(s_[j + 1]) for s_ in stage) / args.steps
+          for j, n in enumerate(names)}
+    return {"ms": float(ms_t.item()), "stages": st, "sweeps": sweeps.cpu().numpy(), "clocks": clk,
+            "flags": flags.cpu().numpy(), "widths": widths.cpu().numpy()}
+
+
 def run_tp(args):
     import torch
     import torch.distributed as dist
@@ -244,74 +311,84 @@ def run_tp(args):
     specs, Ys, taus, slices, nbytes, shapes = make_batch(tp, synth, args.count, rank, device)
     Xs = [tp.empty(*Y.shape, device=device) for Y in Ys]
     descs = tp.make_descs(Ys, Xs, taus)
-    nsl = slices
-    sweeps = torch.zeros(nsl, dtype=torch.int32, device=device)
-
-    def events(n):
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
-        for e in evs:
-            e.record()
-        return evs
-
-    base_opts = tp.options(sync=False)
-    for _ in range(args.warmup):
-        tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=base_opts, descs=descs)
-    torch.cuda.synchronize()
-    # convergence status of the workload (one synchronous call, untimed)
-    tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=tp.options(sync=True, sweeps_out=sweeps),
-                        descs=descs)
-
-    stage = [events(4) for _ in range(args.steps)]
-    step_opts = [tp.options(sync=False, sweeps_out=sweeps, stage_events=stage[i])
-                 for i in range(args.steps)]
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = Clocks(local)
-    torch.cuda.synchronize()
-    barrier()
-    clocks.start()
-    t0.record()
-    for i in range(args.steps):
-        tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=step_opts[i], descs=descs)
-    t1.record()
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = t0.elapsed_time(t1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = slices * world * args.steps / (ms_max / 1e3)
-
-    # stage times (ms per step): DFT, slice SVT, inverse DFT
-    st = [[s[j].elapsed_time(s[j + 1]) for j in range(3)] for s in stage]
-    st_mean = [sum(x[j] for x in st) / len(st) for j in range(3)]
-    sw = sweeps.cpu().numpy()
-    flops = jacobi_model_flops(shapes, sw)
     groups = svd_launch_groups([(a, b) for a, b, _ in shapes])
-    svt_tflops = flops / (st_mean[1] / 1e3) / 1e12
-    # DFT stages: algorithmic bytes = real tensor + half spectrum (complex FP32)
     spec_bytes = sum(8 * a * b * (c // 2 + 1) for a, b, c in shapes)
-    dft_gbs = (nbytes + spec_bytes) / (st_mean[0] / 1e3) / 1e9
-    idft_gbs = (nbytes + spec_bytes) / (st_mean[2] / 1e3) / 1e9
+
+    # --- plain FP32 path (one-sided Jacobi on every slice)
+    plain = time_prox(tp, args, Ys, Xs, taus, descs, "jacobi", world, barrier, device)
+    X_plain = [X.clone() for X in Xs]
+    jflops = jacobi_model_flops(shapes, plain["sweeps"])
+    jt = plain["stages"]["jacobi_svt"]
+    plain_value = slices * world * args.steps / (plain["ms"] / 1e3)
+    plain_line = {"value": plain_value, "ms_per_step": plain["ms"] / args.steps,
+                  "stages_ms": plain["stages"],
+                  "roofline": {"kernel": "svd_kernel<SVD_PROX> (one-sided Jacobi + SVT)",
+                               "bound": "alu", "achieved": jflops / (jt / 1e3) / 1e12,
+                               "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": jflops / (jt / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                               "model": "sum over slices of sweeps*n(n-1)/2*40*m flops",
+                               "sweeps_mean": float(plain["sweeps"].mean())}}
+
+    # --- learned path: proposer trained (untimed) on separately seeded batches
+    t_train = time.perf_counter()
+    train_Y, train_tau = [], []
+    for sd in range(args.train_batches):
+        _, Yt, tt, _, _, _ = make_batch(tp, synth, 512, 1000 + 97 * rank + sd, device)
+        train_Y += Yt
+        train_tau += tt
+    train_slices = sum(Y.shape[2] // 2 + 1 for Y in train_Y)
+    mse = tp.proposer_train(train_Y, train_tau, steps=300, seed=11)
+    del train_Y
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+    learned = time_prox(tp, args, Ys, Xs, taus, descs, "learned", world, barrier, device,
+                        clocks=Clocks(local))
+    dev = 0.0
+    for Xl, Xp in zip(Xs, X_plain):
+        d = float(torch.linalg.vector_norm(Xl - Xp) / torch.linalg.vector_norm(Xp).clamp_min(1e-30))
+        dev = max(dev, d)
+    ms_max = learned["ms"]
+    value = slices * world * args.steps / (ms_max / 1e3)
+    st = learned["stages"]
+    sk_flops = sketch_model_flops(shapes, learned["widths"])
+    sk_tflops = sk_flops / (st["sketch_svt"] / 1e3) / 1e12
+    fb = learned["flags"]
+    dominant = "sketch_svt" if st["sketch_svt"] >= st["jacobi_svt"] else "jacobi_svt"
+    if dominant == "sketch_svt":
+        roof = {"kernel": "sketch_svt_kernel (randomized range finder + small Jacobi SVD + SVT)",
+                "bound": "alu", "achieved": sk_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": sk_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                "model": "per sketched slice 8*n1*n2*(6*l+4) flops (l = sketch width)"}
+    else:
+        fl = jacobi_model_flops(shapes, learned["sweeps"] * (fb == 1))
+        a = fl / (st["jacobi_svt"] / 1e3) / 1e12
+        roof = {"kernel": "svd_kernel<SVD_PROX> on the fallback slices", "bound": "alu",
+                "achieved": a, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": a / FP32_PEAK_TFLOPS, "traffic": None,
+                "model": "sum over fallback slices of sweeps*n(n-1)/2*40*m flops"}
+    dft_gbs = (nbytes + spec_bytes) / (st["rfft"] / 1e3) / 1e9
+    idft_gbs = (nbytes + spec_bytes) / (st["irfft"] / 1e3) / 1e9
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "tensors": len(specs), "free_slices": slices,
+            "config": {"workload": WORKLOAD, "method": "learned rank proposer + randomized SVT, "
+                       "Jacobi fallback", "tensors": len(specs), "free_slices": slices,
                        "seed": rank, "input_bytes": nbytes,
                        "l2": "inputs larger than L2 (%.2f GB in + out per step)" % (2 * nbytes / 1e9)},
-            "gpu_launches": (2 + groups) * args.steps,
-            "clocks": clk,
-            "roofline": {"kernel": "svd_kernel<SVD_PROX> (one-sided Jacobi + SVT), %d launches/step" % groups,
-                         "bound": "alu", "achieved": svt_tflops, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": svt_tflops / FP32_PEAK_TFLOPS, "traffic": None,
-                         "model": "sum over slices of sweeps*n(n-1)/2*40*m flops",
-                         "sweeps_mean": float(sw.mean()), "sweeps_max": int(sw.max())},
-            "stages_ms": {"rfft": st_mean[0], "svt": st_mean[1], "irfft": st_mean[2]},
+            "gpu_launches": (5 + groups) * args.steps,
+            "roofline": roof,
+            "stages_ms": st,
+            "learned": {"fallback_fraction": float((fb == 1).mean()),
+                        "max_rel_dev_vs_plain": dev, "train_slices": train_slices,
+                        "train_mse": mse, "train_seconds": t_train,
+                        "sketch_width_mean": float(learned["widths"][fb == 0].mean()) if (fb == 0).any() else 0.0,
+                        "vs_plain": value / plain_value},
+            "plain": plain_line,
             "dft_gbs": {"rfft": dft_gbs, "irfft": idft_gbs}}
 
+    line["clocks"] = learned["clocks"]
     if not args.no_e2e:
         line["e2e"] = e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device)
     if not args.no_tprod and rank == 0:
@@ -337,7 +414,7 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
         h.copy_(Y.permute(2, 1, 0).reshape(-1).cpu())
     flat_in = [Y.permute(2, 1, 0).reshape(-1) for Y in Ys]     # views of the device buffers
     flat_out = [X.permute(2, 1, 0).reshape(-1) for X in Xs]
-    opts = tp.options(sync=False)
+    opts = tp.options(sync=False, method="learned")
 
     def step():
         for d, h in zip(flat_in, hin):
@@ -389,7 +466,8 @@ def tprod_leg(args, tp, synth, device):
     for prec in ("fp32", "bf16x3", "3xtf32"):
         for _ in range(2):
             tp.tprod(A, B, out=C, opts=tp.options(precision=prec, sync=False))
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(tp.STAGE_EVENTS)]
+               for _ in range(steps)]
         for s_ in evs:
             for e in s_:
                 e.record()
@@ -401,7 +479,8 @@ def tprod_leg(args, tp, synth, device):
         t1.record()
         torch.cuda.synchronize()
         ms = t0.elapsed_time(t1) / steps
-        st = [sum(s_[j].elapsed_time(s_[j + 1]) for s_ in evs) / steps for j in range(3)]
+        seg = lambda a, b: sum(s_[a].elapsed_time(s_[b]) for s_ in evs) / steps
+        st = [seg(0, 1), seg(3, 4), seg(4, 5)]
         gemm_tflops = flops / (st[1] / 1e3) / 1e12
         if prec == "fp32":
             roof = {"bound": "alu", "achieved": gemm_tflops, "peak": FP32_PEAK_TFLOPS,

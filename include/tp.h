@@ -79,10 +79,36 @@ typedef struct tp_options {
                             <= 0 selects 8 * 2^-23 */
     int32_t* sweeps_out; /* optional DEVICE array, one int per directly computed Fourier
                             slice (tensor-major, slice-minor): Jacobi sweeps used */
-    void* const* stage_events; /* optional HOST array of 4 cudaEvent_t, recorded on `stream`
-                            before the tube DFT, after it, after the per-slice kernels and
-                            after the inverse DFT (or final reduction); for timing */
+    void* const* stage_events; /* optional HOST array of TP_STAGE_EVENTS cudaEvent_t recorded
+                            on `stream` for timing: [0] before the tube DFT, [1] after it,
+                            [2] after the rank proposer, [3] after the sketch SVT, [4] after
+                            the Jacobi / GEMM slice kernels, [5] after the inverse DFT (or final
+                            reduction). Stages an operation does not run are recorded at the
+                            same point as the stage before them. */
+    int32_t method;      /* prox_tnn slice SVT: TP_METHOD_JACOBI (default) or TP_METHOD_LEARNED */
+    int32_t* slice_flags_out; /* optional DEVICE array, one int per directly computed slice
+                            (same indexing as sweeps_out): with TP_METHOD_LEARNED, 0 if the
+                            sketch path finished the slice, 1 if it fell back to Jacobi */
+    int32_t* sketch_width_out; /* optional DEVICE array, same indexing: the sketch width the
+                            proposer chose (0: the slice went straight to Jacobi) */
 } tp_options;
+
+#define TP_STAGE_EVENTS 6
+
+/*
+ * Slice SVT methods of prox_tnn (Algorithm 3, step 2).
+ * TP_METHOD_JACOBI:  one-sided Jacobi SVD of every slice (the plain FP32 path).
+ * TP_METHOD_LEARNED: not in the paper. A trained proposer (tp_proposer_train) predicts
+ *   k = #{sigma > tau} of each slice from cheap sketch features; a randomized range finder of
+ *   width k + 8 with one power iteration and a small Jacobi SVD gives the top singular
+ *   triplets; the slice is accepted only if the smallest computed singular value is below
+ *   tau, the kept triplets' residuals ||A r - sigma u|| (times their weight (sigma - tau)/sigma
+ *   in the result) are below 1e-5 sigma_max and the
+ *   deflated matrix's norm is estimated below 0.8 tau; every other slice is recomputed by
+ *   the Jacobi path. Error target 1e-4 relative (Frobenius) against the exact prox.
+ */
+#define TP_METHOD_JACOBI 0
+#define TP_METHOD_LEARNED 1
 
 /* Fill *opts with the defaults used when a NULL options pointer is passed. */
 void tp_options_default(tp_options* opts);
@@ -157,6 +183,23 @@ tp_status tp_tubalrank(const float* A, int64_t* out, double* s_out, int64_t n1, 
 tp_status tp_prox_tnn(const float* Y, float* X, int64_t n1, int64_t n2, int64_t n3,
                       double tau, const tp_options* opts, void* stream);
 
+/*
+ * The rank proposer of TP_METHOD_LEARNED (not in the paper): an MLP 12 -> 64 -> 64 -> 1 (ReLU,
+ * FP32) per device. Its parameters are TP_PROPOSER_FLOATS floats laid out as
+ * W1[64][12], b1[64], W2[64][64], b2[64], w3[64], b3, feature mean[12], feature std[12].
+ *
+ * tp_proposer_train: runs the plain Jacobi prox path on the given tensors (outputs are not
+ *   written) to label every directly computed slice with #{sigma > tau}, computes the slice
+ *   features, and fits the MLP with `steps` full-batch Adam steps (learning rate lr, weights
+ *   initialised from `seed`) on the device with the library's own kernels. The fitted
+ *   proposer becomes the current device's; *mse_out (host, optional) receives the final
+ *   mean squared error in counts^2. Synchronous.
+ * tp_proposer_get / tp_proposer_set: copy the current device's parameters out to / in from
+ *   a HOST array of TP_PROPOSER_FLOATS floats (to save and restore a trained proposer).
+ *   tp_proposer_get returns TP_ERR_INVALID_ARG if no proposer was trained or set.
+ */
+#define TP_PROPOSER_FLOATS (64 * 12 + 64 + 64 * 64 + 64 + 64 + 1 + 2 * 12)
+
 /* One tensor of a batched call. */
 typedef struct tp_tensor_desc {
     const float* in; /* device, n1 x n2 x n3 */
@@ -174,6 +217,11 @@ typedef struct tp_tensor_desc {
  */
 tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count,
                               const tp_options* opts, void* stream);
+
+tp_status tp_proposer_train(const tp_tensor_desc* descs, int64_t count, int32_t steps, double lr,
+                            uint64_t seed, double* mse_out, void* stream);
+tp_status tp_proposer_get(float* host_params);
+tp_status tp_proposer_set(const float* host_params);
 
 /*
  * tp_prox_tnn without any device allocation. The paper has no counterpart: this entry point

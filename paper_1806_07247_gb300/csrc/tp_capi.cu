@@ -97,10 +97,21 @@ struct Opts {
     double jacobi_tol = 0.0;
     int32_t* sweeps_out = nullptr;
     void* const* events = nullptr;
+    int method = TP_METHOD_JACOBI;
+    int32_t* slice_flags_out = nullptr;
+    int32_t* sketch_width_out = nullptr;
     // Record stage boundary i (0..3) on the stream when the caller asked for it.
     tp_status mark(int i, cudaStream_t s) const {
         if (!events || !events[i]) return TP_OK;
         return from_cuda(cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s));
+    }
+    // Record stages i..j (inclusive) at this point.
+    tp_status marks(int i, int j, cudaStream_t s) const {
+        for (int k = i; k <= j; ++k) {
+            tp_status st = mark(k, s);
+            if (st != TP_OK) return st;
+        }
+        return TP_OK;
     }
 };
 
@@ -119,6 +130,10 @@ tp_status resolve(const tp_options* o, Opts* r) {
     r->jacobi_tol = o->jacobi_tol;
     r->sweeps_out = o->sweeps_out;
     r->events = o->stage_events;
+    if (o->method != TP_METHOD_JACOBI && o->method != TP_METHOD_LEARNED) return TP_ERR_INVALID_ARG;
+    r->method = o->method;
+    r->slice_flags_out = o->slice_flags_out;
+    r->sketch_width_out = o->sketch_width_out;
     return TP_OK;
 }
 
@@ -151,9 +166,9 @@ tp_status finish(uint32_t* d_status, const Opts& o, cudaStream_t s) {
 // Group per-slice SVD jobs by kernel instantiation and launch each group.
 struct SvdBatch {
     struct Item {
-        SvdJob job;
-        SvdConfig cfg;
-        int64_t cost;
+        SvdJob job{};
+        SvdConfig cfg{};
+        int64_t cost = 0;
     };
     std::vector<Item> items;
 
@@ -208,7 +223,7 @@ struct FftBatch {
     bool vec = true;
     void add(const float* x, float2* X, int64_t P, int n3) {
         if (P <= 0 || n3 <= 0) return;
-        FftJob j;
+        FftJob j{};
         j.x = x;
         j.X = X;
         j.P = P;
@@ -239,14 +254,29 @@ struct FftBatch {
 
 size_t cbytes(int64_t count) { return Workspace::round((size_t)count * sizeof(float2)); }
 
-// Batched prox over validated descriptors.
-tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cudaStream_t s) {
-    // sizes first
+// Batched prox over validated descriptors.  With TP_METHOD_LEARNED the slices first go
+// through features -> proposer -> sketch SVT; the Jacobi launches then skip the slices the
+// sketch path accepted.  With `train` set (proposer training) the Jacobi path labels every
+// slice with its count, features are kept, and no output tensor is written.
+struct ProxCapture {
+    int steps = 300;
+    float lr = 3e-3f;
+    uint64_t seed = 0;
+    double mse = 0.0;
+    int64_t slices = 0;
+};
+
+tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cudaStream_t s,
+                       ProxCapture* train = nullptr) {
+    const bool learned = (o.method == TP_METHOD_LEARNED) && !train;
+    const bool need_feat = learned || train;
     size_t bytes = Workspace::round(sizeof(uint32_t));
     int64_t slices = 0;
     std::vector<SvdConfig> cfg(count);
     std::vector<int64_t> work(count, 0);
     int64_t nfft = 0;
+    int max_n1 = 1, max_n2 = 1;
+    size_t sk_smem = 0;
     for (int64_t t = 0; t < count; ++t) {
         const int64_t n1 = d[t].n1, n2 = d[t].n2, n3 = d[t].n3;
         if (n1 == 0 || n2 == 0 || n3 == 0) continue;
@@ -257,17 +287,39 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         if (work[t] > 0) bytes += cbytes(work[t] * h);
         slices += h;
         ++nfft;
+        max_n1 = std::max<int>(max_n1, (int)n1);
+        max_n2 = std::max<int>(max_n2, (int)n2);
+        const size_t need = sketch_smem_need((int)n1, (int)n2, kSketchMaxL);
+        if (need <= (size_t)(200 * 1024)) sk_smem = std::max(sk_smem, need);
     }
     if (nfft == 0) return TP_OK;
     bytes += 2 * Workspace::round(sizeof(FftJob) * (nfft + 1));
     bytes += Workspace::round(sizeof(SvdJob) * (slices + 1));
+    if (need_feat) {
+        bytes += Workspace::round(sizeof(SvdJob) * (slices + 1));        // natural-order jobs
+        bytes += Workspace::round(sizeof(float) * kProposerInputs * slices);
+        bytes += 3 * Workspace::round(sizeof(int32_t) * slices);          // ell, flags, counts
+    }
+    if (train) bytes += Workspace::round(sizeof(float) * proposer_fit_scratch_floats((int)slices));
     Workspace ws(s);
     TP_TRY(ws.reserve(bytes));
     uint32_t* d_status = ws.take<uint32_t>(1);
     TP_TRY(ws.check());
     TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+    float* feat = nullptr;
+    int32_t *ell = nullptr, *flags = nullptr, *counts = nullptr;
+    SvdJob* d_nat = nullptr;
+    if (need_feat) {
+        d_nat = ws.take<SvdJob>(slices);
+        feat = ws.take<float>((size_t)kProposerInputs * slices);
+        ell = ws.take<int32_t>(slices);
+        flags = ws.take<int32_t>(slices);
+        counts = ws.take<int32_t>(slices);
+        TP_TRY(ws.check());
+    }
     FftBatch fwd, inv;
     SvdBatch svd;
+    std::vector<SvdJob> natural;
     int64_t sidx = 0;
     for (int64_t t = 0; t < count; ++t) {
         const int64_t n1 = d[t].n1, n2 = d[t].n2, n3 = d[t].n3;
@@ -279,7 +331,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         fwd.add(d[t].in, spec, P, (int)n3);
         inv.add(d[t].out, spec, P, (int)n3);
         for (int k = 0; k < h; ++k) {
-            SvdBatch::Item it;
+            SvdBatch::Item it{};
             SvdJob& j = it.job;
             j.A = spec + P * k;
             j.W = spec + P * k;
@@ -290,21 +342,61 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             j.n2 = (int)n2;
             j.real_slice = is_real_slice(k, (int)n3) ? 1 : 0;
             j.ucols = j.vcols = 0;
-            j.sweeps_index = (int32_t)(sidx++);
+            j.sweeps_index = (int32_t)sidx;
             j.tau = d[t].tau;
+            j.skip = learned ? flags + sidx : nullptr;
+            j.count_out = train ? counts + sidx : nullptr;
+            if (need_feat) natural.push_back(j);
             it.cfg = cfg[t];
             const int64_t m = std::max(n1, n2), n = std::min(n1, n2);
             it.cost = m * n * n;
             svd.items.push_back(it);
+            ++sidx;
         }
     }
+    TP_TRY(ws.check());
     TP_TRY(o.mark(0, s));
     TP_TRY(fwd.launch(ws, false, s));
     TP_TRY(o.mark(1, s));
+    if (need_feat) {
+        TP_TRY(upload(d_nat, natural, s));
+        TP_CUDA(launch_features(d_nat, (int)slices, max_n1, max_n2, feat, 0x2545f491u, s));
+    }
+    if (!learned) TP_TRY(o.marks(2, 3, s));
+    if (learned) {
+        TP_CUDA(launch_proposer(feat, d_nat, (int)slices, ell, s));
+        TP_TRY(o.mark(2, s));
+        SketchParams sp;
+        sp.ell = ell;
+        sp.flag = flags;
+        sp.count = counts;
+        sp.seed = 0x9e3779b9u;
+        sp.power_iters = 1;
+        sp.resid_tol = 1e-5f;
+        sp.smem_bytes = (int)sk_smem;
+        TP_CUDA(launch_sketch_svt(d_nat, (int)slices, sk_smem, sp, s));
+        TP_TRY(o.mark(3, s));
+        if (o.slice_flags_out)
+            TP_CUDA(cudaMemcpyAsync(o.slice_flags_out, flags, sizeof(int32_t) * slices,
+                                    cudaMemcpyDeviceToDevice, s));
+        if (o.sketch_width_out)
+            TP_CUDA(cudaMemcpyAsync(o.sketch_width_out, ell, sizeof(int32_t) * slices,
+                                    cudaMemcpyDeviceToDevice, s));
+    }
     TP_TRY(svd.launch(ws, SVD_PROX, o, d_status, s));
-    TP_TRY(o.mark(2, s));
+    TP_TRY(o.mark(4, s));
+    if (train) {
+        float* scratch = ws.take<float>(proposer_fit_scratch_floats((int)slices));
+        TP_TRY(ws.check());
+        const tp_status fs = finish(d_status, o, s);
+        if (fs != TP_OK && fs != TP_ERR_NOT_CONVERGED) return fs;
+        train->slices = slices;
+        TP_CUDA(proposer_fit(feat, counts, (int)slices, train->steps, train->lr, train->seed,
+                             scratch, &train->mse, s));
+        return TP_OK;
+    }
     TP_TRY(inv.launch(ws, true, s));
-    TP_TRY(o.mark(3, s));
+    TP_TRY(o.mark(5, s));
     return finish(d_status, o, s);
 }
 
@@ -331,7 +423,7 @@ tp_status sigma_op(const float* A, int64_t n1, int64_t n2, int64_t n3, int kind,
     fwd.add(A, spec, P, (int)n3);
     SvdBatch svd;
     for (int k = 0; k < h; ++k) {
-        SvdBatch::Item it;
+        SvdBatch::Item it{};
         SvdJob& j = it.job;
         j.A = spec + P * k;
         j.W = nullptr;
@@ -350,13 +442,13 @@ tp_status sigma_op(const float* A, int64_t n1, int64_t n2, int64_t n3, int kind,
     }
     TP_TRY(o.mark(0, s));
     TP_TRY(fwd.launch(ws, false, s));
-    TP_TRY(o.mark(1, s));
+    TP_TRY(o.marks(1, 3, s));
     TP_TRY(svd.launch(ws, SVD_SIGMA, o, d_status, s));
-    TP_TRY(o.mark(2, s));
+    TP_TRY(o.mark(4, s));
     TP_TRY(ws.check());
     TP_CUDA(launch_sigma_reduce(sig, h, (int)r, (int)n3, kind, tol, std::max(n1, n2), out_d, out_i,
                                 s_out, s));
-    TP_TRY(o.mark(3, s));
+    TP_TRY(o.mark(5, s));
     return finish(d_status, o, s);
 }
 
@@ -373,6 +465,9 @@ void tp_options_default(tp_options* opts) {
     opts->jacobi_tol = 0.0;
     opts->sweeps_out = nullptr;
     opts->stage_events = nullptr;
+    opts->method = TP_METHOD_JACOBI;
+    opts->slice_flags_out = nullptr;
+    opts->sketch_width_out = nullptr;
 }
 
 const char* tp_last_error_string(void) {
@@ -429,16 +524,16 @@ tp_status tp_tprod(const float* A, const float* B, float* C, int64_t n1, int64_t
     fwd.add(B, Bb, PB, (int)n3);
     TP_TRY(o.mark(0, s));
     TP_TRY(fwd.launch(ws, false, s));
-    TP_TRY(o.mark(1, s));
+    TP_TRY(o.marks(1, 3, s));
     TP_TRY(ws.check());
     if (tc)
         TP_CUDA(launch_cgemm_tc(Ab, Bb, Cb, (int)n1, (int)l, (int)n2, h, o.precision, planes, d_err, s));
     else
         TP_CUDA(launch_cgemm_fp32(Ab, Bb, Cb, (int)n1, (int)l, (int)n2, PA, PB, PC, h, s));
-    TP_TRY(o.mark(2, s));
+    TP_TRY(o.mark(4, s));
     inv.add(C, Cb, PC, (int)n3);
     TP_TRY(inv.launch(ws, true, s));
-    TP_TRY(o.mark(3, s));
+    TP_TRY(o.mark(5, s));
     if (!tc) return finish(nullptr, o, s);
     TP_TRY(finish(nullptr, o, s));
     if (o.sync) {
@@ -499,7 +594,7 @@ tp_status tp_tsvd(const float* A, float* U, float* S, float* V, int64_t n1, int6
     TP_TRY(fwd.launch(ws, false, s));
     SvdBatch svd;
     for (int k = 0; k < h; ++k) {
-        SvdBatch::Item it;
+        SvdBatch::Item it{};
         SvdJob& j = it.job;
         j.A = spec + P * k;
         j.W = Ub + PU * k;
@@ -585,6 +680,55 @@ tp_status tp_prox_tnn(const float* Y, float* X, int64_t n1, int64_t n2, int64_t 
     return tp_prox_tnn_batched(&d, 1, opts, stream);
 }
 
+static tp_status check_descs(const tp_tensor_desc* descs, int64_t count) {
+    if (count < 0 || (count > 0 && !descs)) return TP_ERR_INVALID_ARG;
+    for (int64_t t = 0; t < count; ++t) {
+        const tp_tensor_desc& d = descs[t];
+        TP_TRY(check_dims(d.n1, d.n2, d.n3));
+        if (isnan(d.tau) || d.tau < 0.0) return TP_ERR_INVALID_ARG;
+        if (d.n1 == 0 || d.n2 == 0 || d.n3 == 0) continue;
+        if (!d.in) return TP_ERR_INVALID_ARG;
+        if (std::max(d.n1, d.n2) > TP_MAX_SVD_DIM) return TP_ERR_UNSUPPORTED;
+    }
+    return TP_OK;
+}
+
+tp_status tp_proposer_train(const tp_tensor_desc* descs, int64_t count, int32_t steps, double lr,
+                            uint64_t seed, double* mse_out, void* stream) {
+    TP_TRY(check_descs(descs, count));
+    if (steps < 1 || steps > 100000 || !(lr > 0.0) || lr > 1.0) return TP_ERR_INVALID_ARG;
+    int64_t slices = 0;
+    for (int64_t t = 0; t < count; ++t)
+        if (descs[t].n1 > 0 && descs[t].n2 > 0 && descs[t].n3 > 0) slices += free_slices((int)descs[t].n3);
+    if (slices == 0 || slices > (1 << 24)) return TP_ERR_INVALID_ARG;
+    TP_TRY(prepare());
+    Opts o;
+    o.sync = 1;
+    ProxCapture cap;
+    cap.steps = steps;
+    cap.lr = (float)lr;
+    cap.seed = seed;
+    tp_status st = prox_batched(descs, count, o, static_cast<cudaStream_t>(stream), &cap);
+    if (st != TP_OK && st != TP_ERR_NOT_CONVERGED) return st;
+    if (mse_out) *mse_out = cap.mse;
+    return TP_OK;
+}
+
+tp_status tp_proposer_get(float* host_params) {
+    if (!host_params) return TP_ERR_INVALID_ARG;
+    if (!proposer_ready()) return TP_ERR_INVALID_ARG;
+    TP_CUDA(proposer_get(host_params));
+    return TP_OK;
+}
+
+tp_status tp_proposer_set(const float* host_params) {
+    if (!host_params) return TP_ERR_INVALID_ARG;
+    for (int i = 0; i < kProposerFloats; ++i)
+        if (!isfinite(host_params[i])) return TP_ERR_INVALID_ARG;
+    TP_CUDA(proposer_set(host_params));
+    return TP_OK;
+}
+
 tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count, const tp_options* opts,
                               void* stream) {
     Opts o;
@@ -600,6 +744,7 @@ tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count, const 
     }
     if (count == 0) return TP_OK;
     TP_TRY(prepare());
+    if (o.method == TP_METHOD_LEARNED && !proposer_ready()) return TP_ERR_INVALID_ARG;
     return prox_batched(descs, count, o, static_cast<cudaStream_t>(stream));
 }
 

@@ -23,11 +23,11 @@ inline __host__ __device__ bool is_real_slice(int k, int n3) {
 // One tensor's tubes: x is P tubes x n3 samples (tube p, sample t at x[p + P*t]),
 // X is P tubes x h complex frequencies (X[p + P*k]).
 struct FftJob {
-    const float* x;      // rfft: input; irfft: output (written)
-    float2* X;           // rfft: output; irfft: input
-    int64_t P;           // tubes (n1*n2)
-    int32_t n3;
-    int32_t tile_begin;  // first CTA of this job in the launch
+    const float* x = nullptr;  // rfft: input; irfft: output (written)
+    float2* X = nullptr;       // rfft: output; irfft: input
+    int64_t P = 0;             // tubes (n1*n2)
+    int32_t n3 = 0;
+    int32_t tile_begin = 0;    // first CTA of this job in the launch
 };
 
 // Fills the per-device twiddle table on first use; returns cudaSuccess or the error.
@@ -61,17 +61,21 @@ cudaError_t launch_cgemm_tc(const float2* A, const float2* B, float2* C, int M, 
 // ---------------------------------------------------------------------------
 enum SvdMode : int32_t { SVD_SIGMA = 0, SVD_PROX = 1, SVD_FULL = 2 };
 
+// Every field has a default so that a record built field by field (on the host or on the
+// device) never carries an indeterminate pointer.
 struct SvdJob {
-    const float2* A;     // Fourier slice, n1 x n2, column-major, ld n1
-    float2* W;           // PROX: output slice (may equal A); FULL: Ubar slice (n1 x ucols)
-    float2* Vout;        // FULL: Vbar slice (n2 x vcols)
-    float2* work;        // global scratch: FULL needs n*n (V_G); large slices need m*n (G)
-    float* sigma;        // min(n1,n2) singular values, decreasing (SIGMA, FULL)
-    int32_t n1, n2;
-    int32_t real_slice;  // 1 for the real slices of Eq. 8
-    int32_t ucols, vcols;  // FULL: columns of U and V to produce
-    int32_t sweeps_index;  // index into sweeps_out, or -1
-    double tau;          // PROX threshold
+    const float2* A = nullptr;   // Fourier slice, n1 x n2, column-major, ld n1
+    float2* W = nullptr;         // PROX: output slice (may equal A); FULL: Ubar (n1 x ucols)
+    float2* Vout = nullptr;      // FULL: Vbar slice (n2 x vcols)
+    float2* work = nullptr;      // global scratch: FULL needs n*n (V_G); big slices need m*n (G)
+    float* sigma = nullptr;      // min(n1,n2) singular values, decreasing (SIGMA, FULL)
+    int32_t n1 = 0, n2 = 0;
+    int32_t real_slice = 0;      // 1 for the real slices of Eq. 8
+    int32_t ucols = 0, vcols = 0;  // FULL: columns of U and V to produce
+    int32_t sweeps_index = -1;   // index into sweeps_out, or -1
+    double tau = 0.0;            // PROX threshold
+    const int32_t* skip = nullptr;  // if set and *skip == 0 the slice is already done (sketch)
+    int32_t* count_out = nullptr;   // PROX: receives #{sigma > tau} if set
 };
 
 struct SvdLaunch {
@@ -112,6 +116,42 @@ cudaError_t launch_diag_spectrum(const float* sigma, int h, int r, float2* Sbar_
                                  cudaStream_t s);
 cudaError_t launch_diag_scatter(const float* tubes, int r, int n3, float* S, int64_t nS1,
                                 int64_t nS2, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Learned-rank randomized SVT (tp_sketch.cu)
+// ---------------------------------------------------------------------------
+constexpr int kSketchMaxL = 32;        // widest sketch
+constexpr int kProposerInputs = 12;    // features per slice
+constexpr int kProposerFloats = TP_PROPOSER_FLOATS;
+
+struct SketchParams {
+    const int32_t* ell;   // per job: sketch width (0: go to the full Jacobi SVD)
+    int32_t* flag;        // per job: 0 = W written by the sketch path, 1 = needs Jacobi
+    int32_t* count;       // per job: #{sigma > tau} on success (optional)
+    uint32_t seed;
+    int power_iters;
+    float resid_tol;
+    int smem_bytes;       // dynamic shared memory of the launch
+};
+
+__host__ __device__ inline size_t sketch_smem_need(int n1, int n2, int l) {
+    return sizeof(float2) * ((size_t)2 * n1 * l + (size_t)n2 * l + (size_t)l * l + n1 + n2 +
+                             2 * kSketchMaxL) +
+           sizeof(float) * (2 * kSketchMaxL + 32) + 64;
+}
+size_t features_smem_bytes(int n1, int n2);
+cudaError_t launch_features(const SvdJob* jobs, int njobs, int max_n1, int max_n2, float* feat,
+                            uint32_t seed, cudaStream_t s);
+cudaError_t launch_proposer(const float* feat, const SvdJob* jobs, int njobs, int32_t* ell,
+                            cudaStream_t s);
+cudaError_t launch_sketch_svt(const SvdJob* jobs, int njobs, size_t smem, const SketchParams& p,
+                              cudaStream_t s);
+bool proposer_ready();
+cudaError_t proposer_set(const float* host);
+cudaError_t proposer_get(float* host);
+cudaError_t proposer_fit(const float* d_feat, const int32_t* d_count, int n, int steps, float lr,
+                         uint64_t seed, float* scratch, double* mse, cudaStream_t s);
+size_t proposer_fit_scratch_floats(int n);
 
 // ---------------------------------------------------------------------------
 // Transpose (tp_tran.cu)

@@ -85,6 +85,8 @@ __global__ void noalloc_jobs_kernel(FftJob* fft, SvdJob* svd, const float* Y, fl
         j.vcols = 0;
         j.sweeps_index = with_sweeps ? k : -1;
         j.tau = tau;
+        j.skip = nullptr;
+        j.count_out = nullptr;
         svd[k] = j;
     }
 }

@@ -1,0 +1,780 @@
+// Learned-rank randomized singular value thresholding of the Fourier slices: the fast path
+// of prox_tnn (Algorithm 3, step 2) for slices whose number of singular values above tau is
+// small, with the full one-sided Jacobi SVD (tp_svd.cu) as fallback and judge.
+//
+// Per slice A (n1 x n2 complex, column-major, in place in the half spectrum):
+//   1. a tiny MLP (12 -> 64 -> 64 -> 1, ReLU) reads cheap sketch features -- log ||A||_F / tau,
+//      the diagonal of the QR factor of an 8-column sketch A Omega_8 over tau, log n1, log n2,
+//      log min(n1, n2) -- and predicts k = #{sigma > tau}; the sketch width is l = k + 8;
+//   2. randomized range finder: Y = A Omega (Omega n2 x l, random +-1 / (+-1 +- i)/sqrt 2
+//      from a counter-based hash), q power iterations (Z = A^H Q, Y = A Z), each followed by
+//      Gram-Schmidt orthonormalisation (two passes), Q = orth(Y);
+//   3. small SVD: Z = A^H Q (n2 x l); one-sided Jacobi on the l columns of Z, accumulating
+//      V (l x l): Z V = D, sigma_j = ||d_j||, so A ~ Q Z^H = (Q V) diag(sigma) (D / sigma)^H;
+//   4. acceptance: (a) the smallest of the l computed singular values is below tau (else the
+//      rank was underestimated); (b) every kept triplet (u, sigma, r) has
+//      ||A r - sigma u|| (sigma - tau) / sigma <= rtol * sigma_max, its weight in W; (c) two
+//      power iterations on the deflated matrix
+//      A - U_k S_k R_k^H estimate its norm below 0.8 tau (no singular value above tau missed);
+//   5. W = sum_{sigma_j > tau} (sigma_j - tau) u_j r_j^H written over A.
+// A slice that fails a check keeps A untouched and is flagged; the Jacobi SVT kernel then
+// processes exactly the flagged slices.  The MLP is trained with hand-written kernels on
+// (features, #{sigma > tau}) pairs produced by the plain Jacobi path.
+#include <math.h>
+
+#include <mutex>
+#include <vector>
+
+#include "tp_internal.cuh"
+#include "tp_rotation.cuh"
+
+namespace tp {
+
+namespace {
+
+constexpr int kT = 256;  // threads per CTA
+constexpr int kLMax = kSketchMaxL;
+constexpr int kD = kProposerInputs;
+constexpr int kH = 64;
+constexpr int kW1 = 0, kB1 = kW1 + kH * kD, kW2 = kB1 + kH, kB2 = kW2 + kH * kH, kW3 = kB2 + kH,
+              kB3 = kW3 + kH, kMean = kB3 + 1, kStd = kMean + kD, kNParams = kMean;
+static_assert(kStd + kD == kProposerFloats, "proposer layout");
+
+// Per-device proposer: weights, biases and the feature standardisation.
+__device__ float g_proposer[kProposerFloats];
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85ebca6bu;
+    x ^= x >> 13;
+    x *= 0xc2b2ae35u;
+    x ^= x >> 16;
+    return x;
+}
+
+// Entry (r, c) of the random test matrix of slice `slice`: +-1 on real slices,
+// (+-1 +- i)/sqrt(2) otherwise.
+__device__ __forceinline__ float2 omega(uint32_t seed, uint32_t slice, uint32_t r, uint32_t c,
+                                        bool real) {
+    const uint32_t h = mix32(seed ^ mix32(slice * 0x9e3779b9u ^ mix32(r * 0x632be5abu + c)));
+    const float a = (h & 1u) ? 1.f : -1.f, b = (h & 2u) ? 1.f : -1.f;
+    return real ? make_float2(a, 0.f) : make_float2(a * 0.70710678f, b * 0.70710678f);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ float block_sum(float v, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float s = 0.f;
+    for (int w = 0; w < kT / 32; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+__device__ __forceinline__ float2 ld_a(const float2* A, int64_t idx, bool real) {
+    float2 v = A[idx];
+    if (real) v.y = 0.f;
+    return v;
+}
+
+// Y (n1 x l, ld n1) = A X (X: n2 x l, ld n2, shared).  Threads own rows; when rows are fewer
+// than threads, the l columns are split into chunks over thread groups.
+__device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, const float2* X,
+                       float2* Y, int l) {
+    const int groups = max(1, min(kT / max(n1, 1), 4));
+    const int chunk = (l + groups - 1) / groups;
+    for (int t = threadIdx.x; t < n1 * groups; t += kT) {
+        const int i = t % n1, g = t / n1;
+        const int j0 = g * chunk, j1 = min(l, j0 + chunk);
+        float2 acc[kLMax];
+#pragma unroll
+        for (int j = 0; j < kLMax; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int c = 0; c < n2; ++c) {
+            const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
+#pragma unroll
+            for (int j = 0; j < kLMax; ++j) {
+                if (j >= j0 && j < j1) {
+                    const float2 x = X[c + n2 * j];
+                    acc[j].x = fmaf(a.x, x.x, fmaf(-a.y, x.y, acc[j].x));
+                    acc[j].y = fmaf(a.x, x.y, fmaf(a.y, x.x, acc[j].y));
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kLMax; ++j)
+            if (j >= j0 && j < j1) Y[i + n1 * j] = acc[j];
+    }
+}
+
+// Z (n2 x l, ld n2) = A^H Y (Y: n1 x l, ld n1, shared).  Threads own columns of A and a range
+// of its rows; partial sums meet in Z through shared-memory atomics.
+__device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real, const float2* Y,
+                        float2* Z, int l) {
+    for (int t = threadIdx.x; t < n2 * l; t += kT) Z[t] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int parts = max(1, min(kT / max(n2, 1), 8));
+    const int span = (n1 + parts - 1) / parts;
+    for (int t = threadIdx.x; t < n2 * parts; t += kT) {
+        const int c = t % n2, pr = t / n2;
+        const int i0 = pr * span, i1 = min(n1, i0 + span);
+        float2 acc[kLMax];
+#pragma unroll
+        for (int j = 0; j < kLMax; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int i = i0; i < i1; ++i) {
+            const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
+#pragma unroll
+            for (int j = 0; j < kLMax; ++j) {
+                if (j < l) {
+                    const float2 y = Y[i + n1 * j];
+                    acc[j].x = fmaf(a.x, y.x, fmaf(a.y, y.y, acc[j].x));  // conj(a) y
+                    acc[j].y = fmaf(a.x, y.y, fmaf(-a.y, y.x, acc[j].y));
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kLMax; ++j) {
+            if (j < l) {
+                atomicAdd(&Z[c + n2 * j].x, acc[j].x);
+                atomicAdd(&Z[c + n2 * j].y, acc[j].y);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Two-pass classical Gram-Schmidt on the l columns (length n, ld n) of Y, in place.
+// A column whose remainder is below 1e-6 of its original norm is set to zero.
+__device__ void orthonormalize(float2* Y, int n, int l, float* red, float2* coef) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = 0; j < l; ++j) {
+        float2* y = Y + n * j;
+        float n0 = 0.f;
+        for (int e = threadIdx.x; e < n; e += kT) n0 = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, n0));
+        n0 = block_sum(n0, red);
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int i = warp; i < j; i += kT / 32) {
+                const float2* q = Y + n * i;
+                float dr = 0.f, di = 0.f;
+                for (int e = lane; e < n; e += 32) {
+                    dr = fmaf(q[e].x, y[e].x, fmaf(q[e].y, y[e].y, dr));
+                    di = fmaf(q[e].x, y[e].y, fmaf(-q[e].y, y[e].x, di));
+                }
+                dr = warp_sum(dr);
+                di = warp_sum(di);
+                if (lane == 0) coef[i] = make_float2(dr, di);
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < n; e += kT) {
+                float2 v = y[e];
+                for (int i = 0; i < j; ++i) {
+                    const float2 q = Y[e + n * i], d = coef[i];
+                    v.x -= fmaf(d.x, q.x, -d.y * q.y);
+                    v.y -= fmaf(d.x, q.y, d.y * q.x);
+                }
+                y[e] = v;
+            }
+            __syncthreads();
+        }
+        float n1 = 0.f;
+        for (int e = threadIdx.x; e < n; e += kT) n1 = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, n1));
+        n1 = block_sum(n1, red);
+        const float inv = (n1 > 1e-12f * n0 && n1 > 0.f) ? rsqrtf(n1) : 0.f;
+        for (int e = threadIdx.x; e < n; e += kT) {
+            y[e].x *= inv;
+            y[e].y *= inv;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
+                                                        SketchParams P) {
+    extern __shared__ float4 smem4[];
+    __shared__ int s_rot;
+    const int job = blockIdx.x;
+    const SvdJob J = jobs[job];
+    const int n1 = J.n1, n2 = J.n2;
+    const bool real = J.real_slice != 0;
+    const int l = P.ell[job];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (l <= 0 || l >= min(n1, n2) || l > kLMax ||
+        sketch_smem_need(n1, n2, l) > (size_t)P.smem_bytes) {
+        if (tid == 0) P.flag[job] = 1;
+        return;
+    }
+    float2* Q = reinterpret_cast<float2*>(smem4);  // n1 x l
+    float2* U = Q + (size_t)n1 * l;                 // n1 x l
+    float2* Z = U + (size_t)n1 * l;                 // n2 x l
+    float2* V = Z + (size_t)n2 * l;                 // l x l
+    float2* xv = V + l * l;                         // n2
+    float2* yv = xv + n2;                           // n1
+    float2* coef = yv + n1;                         // 2 kLMax
+    float* sig = reinterpret_cast<float*>(coef + 2 * kLMax);
+    float* fac = sig + kLMax;
+    float* red = fac + kLMax;
+    const float2* A = J.A;
+
+    // range finder
+    for (int t = tid; t < n2 * l; t += kT) Z[t] = omega(P.seed, job, t % n2, t / n2, real);
+    __syncthreads();
+    mult_a(A, n1, n2, real, Z, Q, l);
+    __syncthreads();
+    orthonormalize(Q, n1, l, red, coef);
+    for (int it = 0; it < P.power_iters; ++it) {
+        mult_ah(A, n1, n2, real, Q, Z, l);
+        orthonormalize(Z, n2, l, red, coef);
+        mult_a(A, n1, n2, real, Z, Q, l);
+        __syncthreads();
+        orthonormalize(Q, n1, l, red, coef);
+    }
+    mult_ah(A, n1, n2, real, Q, Z, l);  // Z = A^H Q = B^H
+
+    // one-sided Jacobi on the l columns of Z, V accumulated
+    for (int t = tid; t < l * l; t += kT) V[t] = make_float2((t % l) == (t / l) ? 1.f : 0.f, 0.f);
+    __syncthreads();
+    const float tol = 8.f * 1.1920928955078125e-07f, tol2 = tol * tol;
+    const int Np = l + (l & 1);
+    bool conv = false;
+    for (int sweep = 0; sweep < 40 && !conv; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int r = 0; r < Np - 1; ++r) {
+            for (int pi = warp; pi < Np / 2; pi += kT / 32) {
+                int a, b;
+                if (pi == 0) { a = Np - 1; b = r; }
+                else { a = (r + pi) % (Np - 1); b = (r - pi + Np - 1) % (Np - 1); }
+                if (a >= l || b >= l) continue;
+                const int p = min(a, b), q = max(a, b);
+                float2* gp = Z + n2 * p;
+                float2* gq = Z + n2 * q;
+                float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+                for (int e = lane; e < n2; e += 32) {
+                    const float2 x = gp[e], y = gq[e];
+                    al = fmaf(x.x, x.x, fmaf(x.y, x.y, al));
+                    be = fmaf(y.x, y.x, fmaf(y.y, y.y, be));
+                    gr = fmaf(x.x, y.x, fmaf(x.y, y.y, gr));
+                    gi = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi));
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                gr = warp_sum(gr);
+                gi = warp_sum(gi);
+                const float ag2 = fmaf(gr, gr, gi * gi);
+                if (!(ag2 > (tol2 * al) * be)) continue;
+                float c, sr, si;
+                jacobi_rotation(al, be, gr, gi, ag2, c, sr, si);
+                for (int e = lane; e < n2; e += 32) {
+                    const float2 x = gp[e], y = gq[e];
+                    gp[e] = make_float2(fmaf(c, x.x, fmaf(-sr, y.x, -si * y.y)),
+                                        fmaf(c, x.y, fmaf(-sr, y.y, si * y.x)));
+                    gq[e] = make_float2(fmaf(sr, x.x, fmaf(-si, x.y, c * y.x)),
+                                        fmaf(sr, x.y, fmaf(si, x.x, c * y.y)));
+                }
+                float2* vp = V + l * p;
+                float2* vq = V + l * q;
+                for (int e = lane; e < l; e += 32) {
+                    const float2 x = vp[e], y = vq[e];
+                    vp[e] = make_float2(fmaf(c, x.x, fmaf(-sr, y.x, -si * y.y)),
+                                        fmaf(c, x.y, fmaf(-sr, y.y, si * y.x)));
+                    vq[e] = make_float2(fmaf(sr, x.x, fmaf(-si, x.y, c * y.x)),
+                                        fmaf(sr, x.y, fmaf(si, x.x, c * y.y)));
+                }
+                if (lane == 0) s_rot = 1;
+            }
+            __syncthreads();
+        }
+        conv = (s_rot == 0);
+        __syncthreads();
+    }
+    // sigma_j = ||d_j||
+    for (int j = warp; j < l; j += kT / 32) {
+        float s = 0.f;
+        for (int e = lane; e < n2; e += 32) s = fmaf(Z[e + n2 * j].x, Z[e + n2 * j].x, fmaf(Z[e + n2 * j].y, Z[e + n2 * j].y, s));
+        s = warp_sum(s);
+        if (lane == 0) sig[j] = sqrtf(s);
+    }
+    __syncthreads();
+    // (a) the sketch must reach below tau; kept set decided in FP64
+    float smin = 3.4e38f, smax = 0.f;
+    int k = 0;
+    for (int j = 0; j < l; ++j) {
+        smin = fminf(smin, sig[j]);
+        smax = fmaxf(smax, sig[j]);
+        k += ((double)sig[j] > J.tau);
+    }
+    bool ok = conv && !((double)smin > J.tau);
+    // U = Q V (n1 x l); D -> R = D / sigma (columns with sigma > tau only matter)
+    if (ok) {
+        for (int t = tid; t < n1 * l; t += kT) {
+            const int i = t % n1, j = t / n1;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int m = 0; m < l; ++m) {
+                const float2 q = Q[i + n1 * m], v = V[m + l * j];
+                acc.x = fmaf(q.x, v.x, fmaf(-q.y, v.y, acc.x));
+                acc.y = fmaf(q.x, v.y, fmaf(q.y, v.x, acc.y));
+            }
+            U[t] = acc;
+        }
+        for (int j = tid; j < l; j += kT) fac[j] = ((double)sig[j] > J.tau) ? 1.f / sig[j] : 0.f;
+        __syncthreads();
+        for (int t = tid; t < n2 * l; t += kT) {
+            const float f = fac[t / n2];
+            Z[t].x *= f;
+            Z[t].y *= f;
+        }
+        __syncthreads();
+        // (b) residuals of the kept triplets: || A r_j - sigma_j u_j ||  (A R into Q)
+        mult_a(A, n1, n2, real, Z, Q, l);
+        __syncthreads();
+        float worst = 0.f;
+        for (int j = 0; j < l; ++j) {
+            if (!((double)sig[j] > J.tau)) continue;
+            float s = 0.f;
+            for (int e = tid; e < n1; e += kT) {
+                const float2 a = Q[e + n1 * j], u = U[e + n1 * j];
+                const float dx = a.x - sig[j] * u.x, dy = a.y - sig[j] * u.y;
+                s = fmaf(dx, dx, fmaf(dy, dy, s));
+            }
+            s = block_sum(s, red);
+            // the triplet enters W with weight (sigma - tau) / sigma
+            worst = fmaxf(worst, sqrtf(s) * (float)(((double)sig[j] - J.tau) / sig[j]));
+        }
+        ok = worst <= P.resid_tol * smax;
+    }
+    if (ok) {
+        // (c) norm of A - U_k S_k R_k^H by two power iterations from a random start
+        for (int c = tid; c < n2; c += kT) xv[c] = omega(P.seed ^ 0x5bd1e995u, job, c, 0, real);
+        __syncthreads();
+        float est = 0.f;
+        for (int it = 0; it < 2; ++it) {
+            float nx = 0.f;
+            for (int c = tid; c < n2; c += kT) nx = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, nx));
+            nx = block_sum(nx, red);
+            const float inx = nx > 0.f ? rsqrtf(nx) : 0.f;
+            for (int c = tid; c < n2; c += kT) { xv[c].x *= inx; xv[c].y *= inx; }
+            // coef_j = sigma_j (r_j^H x)
+            for (int j = warp; j < l; j += kT / 32) {
+                float dr = 0.f, di = 0.f;
+                for (int c = lane; c < n2; c += 32) {
+                    const float2 rr = Z[c + n2 * j], x = xv[c];
+                    dr = fmaf(rr.x, x.x, fmaf(rr.y, x.y, dr));
+                    di = fmaf(rr.x, x.y, fmaf(-rr.y, x.x, di));
+                }
+                dr = warp_sum(dr);
+                di = warp_sum(di);
+                if (lane == 0) coef[j] = make_float2(sig[j] * fac[j] * sig[j] * dr, sig[j] * fac[j] * sig[j] * di);
+            }
+            __syncthreads();
+            // y = A x - U coef
+            for (int i = tid; i < n1; i += kT) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int c = 0; c < n2; ++c) {
+                    const float2 a = ld_a(A, i + (int64_t)n1 * c, real), x = xv[c];
+                    acc.x = fmaf(a.x, x.x, fmaf(-a.y, x.y, acc.x));
+                    acc.y = fmaf(a.x, x.y, fmaf(a.y, x.x, acc.y));
+                }
+                for (int j = 0; j < l; ++j) {
+                    const float2 u = U[i + n1 * j], d = coef[j];
+                    acc.x -= fmaf(u.x, d.x, -u.y * d.y);
+                    acc.y -= fmaf(u.x, d.y, u.y * d.x);
+                }
+                yv[i] = acc;
+            }
+            __syncthreads();
+            // coef_j = sigma_j (u_j^H y)
+            for (int j = warp; j < l; j += kT / 32) {
+                float dr = 0.f, di = 0.f;
+                for (int i = lane; i < n1; i += 32) {
+                    const float2 u = U[i + n1 * j], y = yv[i];
+                    dr = fmaf(u.x, y.x, fmaf(u.y, y.y, dr));
+                    di = fmaf(u.x, y.y, fmaf(-u.y, y.x, di));
+                }
+                dr = warp_sum(dr);
+                di = warp_sum(di);
+                if (lane == 0) coef[j] = make_float2(sig[j] * fac[j] * sig[j] * dr, sig[j] * fac[j] * sig[j] * di);
+            }
+            __syncthreads();
+            // x = A^H y - R coef
+            for (int c = tid; c < n2; c += kT) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int i = 0; i < n1; ++i) {
+                    const float2 a = ld_a(A, i + (int64_t)n1 * c, real), y = yv[i];
+                    acc.x = fmaf(a.x, y.x, fmaf(a.y, y.y, acc.x));
+                    acc.y = fmaf(a.x, y.y, fmaf(-a.y, y.x, acc.y));
+                }
+                for (int j = 0; j < l; ++j) {
+                    const float2 rr = Z[c + n2 * j], d = coef[j];
+                    acc.x -= fmaf(rr.x, d.x, -rr.y * d.y);
+                    acc.y -= fmaf(rr.x, d.y, rr.y * d.x);
+                }
+                xv[c] = acc;
+            }
+            __syncthreads();
+            float nx2 = 0.f;
+            for (int c = tid; c < n2; c += kT) nx2 = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, nx2));
+            nx2 = block_sum(nx2, red);
+            est = sqrtf(sqrtf(nx2));  // ||E^H E x||^(1/2) with ||x|| = 1
+        }
+        ok = (double)est < 0.8 * J.tau;
+    }
+    if (!ok) {
+        if (tid == 0) P.flag[job] = 1;
+        return;
+    }
+    // 5. W = sum_{sigma_j > tau} (sigma_j - tau) u_j r_j^H over A
+    for (int j = tid; j < l; j += kT)
+        fac[j] = ((double)sig[j] > J.tau) ? (float)((double)sig[j] - J.tau) : 0.f;
+    __syncthreads();
+    for (int t = tid; t < n1 * n2; t += kT) {
+        const int i = t % n1, c = t / n1;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int j = 0; j < l; ++j) {
+            const float f = fac[j];
+            if (f == 0.f) continue;
+            const float2 u = U[i + n1 * j], rr = Z[c + n2 * j];
+            // f u conj(r)
+            acc.x = fmaf(f, fmaf(u.x, rr.x, u.y * rr.y), acc.x);
+            acc.y = fmaf(f, fmaf(u.y, rr.x, -u.x * rr.y), acc.y);
+        }
+        if (real) acc.y = 0.f;
+        J.W[t] = acc;
+    }
+    if (tid == 0) {
+        P.flag[job] = 0;
+        if (P.count) P.count[job] = k;
+    }
+}
+
+// Features of each slice for the proposer (see the file comment); one CTA per slice.
+__global__ void __launch_bounds__(kT) features_kernel(const SvdJob* __restrict__ jobs,
+                                                      float* __restrict__ feat, uint32_t seed) {
+    extern __shared__ float4 smem4[];
+    const int job = blockIdx.x;
+    const SvdJob J = jobs[job];
+    const int n1 = J.n1, n2 = J.n2, tid = threadIdx.x;
+    const bool real = J.real_slice != 0;
+    constexpr int S = 8;
+    float2* X = reinterpret_cast<float2*>(smem4);  // n2 x S
+    float2* Y = X + (size_t)n2 * S;                // n1 x S
+    float2* coef = Y + (size_t)n1 * S;
+    float* red = reinterpret_cast<float*>(coef + S);
+    float* dg = red + 32;
+    const float2* A = J.A;
+    float fr = 0.f;
+    for (int64_t t = tid; t < (int64_t)n1 * n2; t += kT) {
+        const float2 a = ld_a(A, t, real);
+        fr = fmaf(a.x, a.x, fmaf(a.y, a.y, fr));
+    }
+    fr = block_sum(fr, red);
+    for (int t = tid; t < n2 * S; t += kT) X[t] = omega(seed, job, t % n2, t / n2, real);
+    __syncthreads();
+    const int l = min(S, n2);
+    mult_a(A, n1, n2, real, X, Y, l);
+    __syncthreads();
+    // modified Gram-Schmidt: |R_jj| = norm of column j after removing the previous ones
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int j = 0; j < l; ++j) {
+        float2* y = Y + n1 * j;
+        for (int i = warp; i < j; i += kT / 32) {
+            const float2* q = Y + n1 * i;
+            float dr = 0.f, di = 0.f;
+            for (int e = lane; e < n1; e += 32) {
+                dr = fmaf(q[e].x, y[e].x, fmaf(q[e].y, y[e].y, dr));
+                di = fmaf(q[e].x, y[e].y, fmaf(-q[e].y, y[e].x, di));
+            }
+            dr = warp_sum(dr);
+            di = warp_sum(di);
+            if (lane == 0) coef[i] = make_float2(dr, di);
+        }
+        __syncthreads();
+        for (int e = tid; e < n1; e += kT) {
+            float2 v = y[e];
+            for (int i = 0; i < j; ++i) {
+                const float2 q = Y[e + n1 * i], d = coef[i];
+                v.x -= fmaf(d.x, q.x, -d.y * q.y);
+                v.y -= fmaf(d.x, q.y, d.y * q.x);
+            }
+            y[e] = v;
+        }
+        __syncthreads();
+        float nn = 0.f;
+        for (int e = tid; e < n1; e += kT) nn = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, nn));
+        nn = block_sum(nn, red);
+        const float rjj = sqrtf(nn);
+        if (tid == 0) dg[j] = rjj;
+        const float inv = rjj > 0.f ? 1.f / rjj : 0.f;
+        for (int e = tid; e < n1; e += kT) { y[e].x *= inv; y[e].y *= inv; }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const float itau = J.tau > 0.0 ? (float)(1.0 / J.tau) : 1e30f;
+        float d[S];
+        for (int j = 0; j < S; ++j) d[j] = j < l ? dg[j] : 0.f;
+        for (int a = 0; a < S; ++a)  // sort decreasing
+            for (int b = a + 1; b < S; ++b)
+                if (d[b] > d[a]) { const float t = d[a]; d[a] = d[b]; d[b] = t; }
+        float* f = feat + (size_t)job * kD;
+        f[0] = logf(sqrtf(fr) * itau + 1e-6f);
+        for (int j = 0; j < S; ++j) f[1 + j] = logf(d[j] * itau + 1e-6f);
+        f[9] = logf((float)n1);
+        f[10] = logf((float)n2);
+        f[11] = logf((float)min(n1, n2));
+    }
+}
+
+// Proposer inference: one thread per slice, ell = clamp(ceil(k_hat) + 8).
+__global__ void mlp_infer_kernel(const float* __restrict__ feat, const SvdJob* __restrict__ jobs,
+                                 int n, int32_t* __restrict__ ell) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const float* w = g_proposer;
+    float x[kD];
+#pragma unroll
+    for (int d = 0; d < kD; ++d) x[d] = (feat[(size_t)s * kD + d] - w[kMean + d]) / w[kStd + d];
+    float h1[kH];
+#pragma unroll 4
+    for (int a = 0; a < kH; ++a) {
+        float v = w[kB1 + a];
+#pragma unroll
+        for (int d = 0; d < kD; ++d) v = fmaf(w[kW1 + a * kD + d], x[d], v);
+        h1[a] = fmaxf(v, 0.f);
+    }
+    float out = w[kB3];
+    for (int a = 0; a < kH; ++a) {
+        float v = w[kB2 + a];
+#pragma unroll 8
+        for (int b = 0; b < kH; ++b) v = fmaf(w[kW2 + a * kH + b], h1[b], v);
+        out = fmaf(w[kW3 + a], fmaxf(v, 0.f), out);
+    }
+    const int r = min(jobs[s].n1, jobs[s].n2);
+    int l = (int)ceilf(fmaxf(out, 0.f)) + 8;
+    l = min(l, kLMax);
+    ell[s] = (l >= r) ? 0 : l;  // 0: sketching cannot help, full Jacobi
+}
+
+// Training: per-sample forward/backward of the squared error, gradients summed in shared
+// memory per CTA and then into `grad`; `loss` accumulates the summed squared error.
+__global__ void __launch_bounds__(kT) mlp_grad_kernel(const float* __restrict__ X,
+                                                      const float* __restrict__ y, int n,
+                                                      const float* __restrict__ w,
+                                                      float* __restrict__ grad, float* loss) {
+    __shared__ float g[kNParams];
+    __shared__ float sl;
+    for (int t = threadIdx.x; t < kNParams; t += kT) g[t] = 0.f;
+    if (threadIdx.x == 0) sl = 0.f;
+    __syncthreads();
+    const int s = blockIdx.x * kT + threadIdx.x;
+    if (s < n) {
+        float x[kD];
+#pragma unroll
+        for (int d = 0; d < kD; ++d) x[d] = X[(size_t)s * kD + d];
+        float h1[kH], h2[kH];
+        for (int a = 0; a < kH; ++a) {
+            float v = w[kB1 + a];
+#pragma unroll
+            for (int d = 0; d < kD; ++d) v = fmaf(w[kW1 + a * kD + d], x[d], v);
+            h1[a] = fmaxf(v, 0.f);
+        }
+        float out = w[kB3];
+        for (int a = 0; a < kH; ++a) {
+            float v = w[kB2 + a];
+            for (int b = 0; b < kH; ++b) v = fmaf(w[kW2 + a * kH + b], h1[b], v);
+            h2[a] = fmaxf(v, 0.f);
+            out = fmaf(w[kW3 + a], h2[a], out);
+        }
+        const float diff = out - y[s];
+        atomicAdd(&sl, diff * diff);
+        const float dout = 2.f * diff / (float)n;
+        atomicAdd(&g[kB3], dout);
+        float dh1[kH];
+#pragma unroll
+        for (int b = 0; b < kH; ++b) dh1[b] = 0.f;
+        for (int a = 0; a < kH; ++a) {
+            atomicAdd(&g[kW3 + a], dout * h2[a]);
+            const float dh2 = h2[a] > 0.f ? dout * w[kW3 + a] : 0.f;
+            if (dh2 != 0.f) {
+                atomicAdd(&g[kB2 + a], dh2);
+                for (int b = 0; b < kH; ++b) {
+                    if (h1[b] > 0.f) atomicAdd(&g[kW2 + a * kH + b], dh2 * h1[b]);
+                    dh1[b] = fmaf(dh2, w[kW2 + a * kH + b], dh1[b]);
+                }
+            }
+        }
+        for (int b = 0; b < kH; ++b) {
+            if (h1[b] <= 0.f) continue;
+            atomicAdd(&g[kB1 + b], dh1[b]);
+#pragma unroll
+            for (int d = 0; d < kD; ++d) atomicAdd(&g[kW1 + b * kD + d], dh1[b] * x[d]);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kNParams; t += kT)
+        if (g[t] != 0.f) atomicAdd(&grad[t], g[t]);
+    if (threadIdx.x == 0) atomicAdd(loss, sl);
+}
+
+// Adam update of the proposer parameters; zeroes the gradient for the next step.
+__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ grad, float* __restrict__ m,
+                            float* __restrict__ v, int step, float lr) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= kNParams) return;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float g = grad[t];
+    const float mt = b1 * m[t] + (1.f - b1) * g, vt = b2 * v[t] + (1.f - b2) * g * g;
+    m[t] = mt;
+    v[t] = vt;
+    const float mh = mt / (1.f - powf(b1, (float)step)), vh = vt / (1.f - powf(b2, (float)step));
+    w[t] -= lr * mh / (sqrtf(vh) + eps);
+    grad[t] = 0.f;
+}
+
+std::mutex g_prop_mutex;
+bool g_prop_ready[128] = {};
+
+}  // namespace
+
+size_t features_smem_bytes(int n1, int n2) {
+    return sizeof(float2) * ((size_t)n2 * 8 + (size_t)n1 * 8 + 8) + sizeof(float) * (32 + 8) + 64;
+}
+
+cudaError_t launch_features(const SvdJob* jobs, int njobs, int max_n1, int max_n2, float* feat,
+                            uint32_t seed, cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    const size_t smem = features_smem_bytes(max_n1, max_n2);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    features_kernel<<<njobs, kT, smem, s>>>(jobs, feat, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_proposer(const float* feat, const SvdJob* jobs, int njobs, int32_t* ell,
+                            cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    mlp_infer_kernel<<<(njobs + 127) / 128, 128, 0, s>>>(feat, jobs, njobs, ell);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_svt(const SvdJob* jobs, int njobs, size_t smem, const SketchParams& p,
+                              cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sketch_svt_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    sketch_svt_kernel<<<njobs, kT, smem, s>>>(jobs, p);
+    return cudaGetLastError();
+}
+
+bool proposer_ready() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return false;
+    std::lock_guard<std::mutex> lock(g_prop_mutex);
+    return g_prop_ready[dev];
+}
+
+cudaError_t proposer_set(const float* host) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    e = cudaMemcpyToSymbol(g_proposer, host, sizeof(float) * kProposerFloats);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_prop_mutex);
+    g_prop_ready[dev] = true;
+    return cudaSuccess;
+}
+
+cudaError_t proposer_get(float* host) {
+    return cudaMemcpyFromSymbol(host, g_proposer, sizeof(float) * kProposerFloats);
+}
+
+// Fit the proposer to (feat, count) pairs resident on the device: standardise the features
+// (statistics computed on the host), Xavier-style initialisation from `seed`, `steps` full-
+// batch Adam steps of the squared error.  Returns the final mean squared error in *mse.
+cudaError_t proposer_fit(const float* d_feat, const int32_t* d_count, int n, int steps, float lr,
+                         uint64_t seed, float* scratch, double* mse, cudaStream_t s) {
+    if (n <= 0) return cudaErrorInvalidValue;
+    std::vector<float> f((size_t)n * kD);
+    std::vector<int32_t> c(n);
+    cudaError_t e = cudaMemcpyAsync(f.data(), d_feat, sizeof(float) * f.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.data(), d_count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    std::vector<float> w(kProposerFloats, 0.f);
+    for (int d = 0; d < kD; ++d) {
+        double m = 0, v = 0;
+        for (int i = 0; i < n; ++i) m += f[(size_t)i * kD + d];
+        m /= n;
+        for (int i = 0; i < n; ++i) {
+            const double t = f[(size_t)i * kD + d] - m;
+            v += t * t;
+        }
+        v = sqrt(v / n);
+        w[kMean + d] = (float)m;
+        w[kStd + d] = (float)(v > 1e-6 ? v : 1.0);
+    }
+    std::vector<float> xs((size_t)n * kD), ys(n);
+    for (int i = 0; i < n; ++i) {
+        for (int d = 0; d < kD; ++d)
+            xs[(size_t)i * kD + d] = (f[(size_t)i * kD + d] - w[kMean + d]) / w[kStd + d];
+        ys[i] = (float)c[i];
+    }
+    uint64_t st = seed * 6364136223846793005ull + 1442695040888963407ull;
+    auto uni = [&]() {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        return ((st >> 40) & 0xFFFFFF) / 16777216.0 * 2.0 - 1.0;
+    };
+    for (int i = 0; i < kH * kD; ++i) w[kW1 + i] = (float)(uni() * sqrt(6.0 / (kD + kH)));
+    for (int i = 0; i < kH * kH; ++i) w[kW2 + i] = (float)(uni() * sqrt(6.0 / (2 * kH)));
+    for (int i = 0; i < kH; ++i) w[kW3 + i] = (float)(uni() * sqrt(6.0 / (kH + 1)));
+    for (int i = 0; i < kH; ++i) w[kB1 + i] = w[kB2 + i] = 0.01f;
+    double mean_y = 0;
+    for (int i = 0; i < n; ++i) mean_y += ys[i];
+    w[kB3] = (float)(mean_y / n);
+    // scratch: X (n*kD), y (n), params, grad, m, v, loss
+    float* dX = scratch;
+    float* dy = dX + (size_t)n * kD;
+    float* dw = dy + n;
+    float* dg = dw + kProposerFloats;
+    float* dm = dg + kProposerFloats;
+    float* dv = dm + kProposerFloats;
+    float* dl = dv + kProposerFloats;
+    e = cudaMemcpyAsync(dX, xs.data(), sizeof(float) * xs.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, ys.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dw, w.data(), sizeof(float) * kProposerFloats, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dg, 0, sizeof(float) * (3 * kProposerFloats + 1), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    const int blocks = (n + kT - 1) / kT;
+    for (int it = 1; it <= steps; ++it) {
+        if (it == steps) cudaMemsetAsync(dl, 0, sizeof(float), s);
+        mlp_grad_kernel<<<blocks, kT, 0, s>>>(dX, dy, n, dw, dg, dl);
+        adam_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(dw, dg, dm, dv, it, lr);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    float hl = 0.f;
+    e = cudaMemcpyAsync(w.data(), dw, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hl, dl, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (mse) *mse = hl / n;
+    return proposer_set(w.data());
+}
+
+size_t proposer_fit_scratch_floats(int n) { return (size_t)n * (kD + 1) + 4 * kProposerFloats + 1; }
+
+}  // namespace tp

@@ -41,6 +41,7 @@
 #include <math.h>
 
 #include "tp_internal.cuh"
+#include "tp_rotation.cuh"
 
 namespace tp {
 
@@ -91,36 +92,6 @@ __device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
     for (int o = LP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
-}
-
-// 1/sqrt(x) and 1/x from the hardware approximations plus one Newton step (about 1 ulp).
-__device__ __forceinline__ float rsqrt_nr(float x) {
-    const float r = rsqrtf(x);
-    return r * fmaf(-0.5f * x * r, r, 1.5f);
-}
-__device__ __forceinline__ float rcp_nr(float x) {
-    const float r = __fdividef(1.f, x);
-    return r * fmaf(-x, r, 2.f);
-}
-
-// Cosine and sine of the Jacobi rotation with tangent t (|t| <= 1): c = 1/sqrt(1 + t^2),
-// s = c t.  c^2 + s^2 = 1 must hold to about an ulp with no bias, because every column is
-// rotated some n * sweeps times and a biased norm drift accumulates into the singular
-// values.  1 + t^2 is therefore kept exactly as qh + ql (error-free product and Fast2Sum),
-// and the hardware reciprocal square root gets one Newton step whose residual
-// 1 - (qh + ql) r^2 is evaluated with the exact product qh r = h + hl.  The _rn intrinsics
-// keep the compiler from fusing or reassociating these steps.
-__device__ __forceinline__ void rotation_cs(float t, float& c, float& s) {
-    const float hi = __fmul_rn(t, t);
-    const float lo = fmaf(t, t, -hi);
-    const float qh = __fadd_rn(1.f, hi);
-    const float ql = __fadd_rn(__fadd_rn(__fsub_rn(1.f, qh), hi), lo);
-    const float r = rsqrtf(qh);
-    const float h = __fmul_rn(qh, r);
-    const float hl = fmaf(qh, r, -h);
-    const float rho = __fsub_rn(fmaf(-h, r, 1.f), r * fmaf(ql, r, hl));
-    c = fmaf(0.5f * r, rho, r);
-    s = __fmul_rn(c, t);
 }
 
 // Sums of four values over the aligned LP-lane group (LP >= 8), returned in every lane:
@@ -241,6 +212,7 @@ __global__ void __launch_bounds__(MAXE2 >= 8 ? 512 : 1024, 1)
     extern __shared__ float4 smem4[];
     __shared__ int s_rot, s_cnt;
     const SvdJob J = jobs[blockIdx.x];
+    if (J.skip && *J.skip == 0) return;  // slice finished by the sketch path
     const int n1 = J.n1, n2 = J.n2;
     const bool tr = n1 < n2;
     const int m = tr ? n2 : n1, n = tr ? n1 : n2;
@@ -386,7 +358,10 @@ __global__ void __launch_bounds__(MAXE2 >= 8 ? 512 : 1024, 1)
                 if (f) kept[cnt + __popc(mask & ((1u << lane) - 1u))] = c;
                 cnt += __popc(mask);
             }
-            if (lane == 0) s_cnt = cnt;
+            if (lane == 0) {
+                s_cnt = cnt;
+                if (J.count_out) *J.count_out = cnt;
+            }
         }
         __syncthreads();
         const int cnt = s_cnt;

@@ -41,7 +41,9 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("econ", ctypes.c_int32),
                 ("max_sweeps", ctypes.c_int32), ("sync", ctypes.c_int32),
                 ("jacobi_tol", ctypes.c_double), ("sweeps_out", ctypes.c_void_p),
-                ("stage_events", ctypes.c_void_p)]
+                ("stage_events", ctypes.c_void_p), ("method", ctypes.c_int32),
+                ("slice_flags_out", ctypes.c_void_p), ("sketch_width_out", ctypes.c_void_p)]
+STAGE_EVENTS = 6
 
 
 class TensorDesc(ctypes.Structure):
@@ -72,7 +74,14 @@ _SIGS = {
                                            ctypes.POINTER(Options), ctypes.c_void_p]),
     "tp_prox_tnn_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int64] * 3 +
                             [ctypes.c_double, ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_proposer_train": (ctypes.c_int, [ctypes.POINTER(TensorDesc), ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.c_double, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "tp_proposer_get": (ctypes.c_int, [ctypes.c_void_p]),
+    "tp_proposer_set": (ctypes.c_int, [ctypes.c_void_p]),
 }
+METHODS = {"jacobi": 0, "learned": 1}
+PROPOSER_FLOATS = 64 * 12 + 64 + 64 * 64 + 64 + 64 + 1 + 2 * 12
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -98,9 +107,16 @@ def status_string(status: int) -> str:
 
 def options(precision: str = "fp32", econ: bool = False, max_sweeps: int = 30, sync: bool = True,
             jacobi_tol: float = 0.0, sweeps_out: torch.Tensor | None = None,
-            stage_events=None) -> Options:
-    """tp_options; stage_events is a list of 4 recorded torch.cuda.Event (see tp.h)."""
+            stage_events=None, method: str = "jacobi",
+            slice_flags_out: torch.Tensor | None = None,
+            sketch_width_out: torch.Tensor | None = None) -> Options:
+    """tp_options; stage_events is a list of STAGE_EVENTS recorded torch.cuda.Event (tp.h)."""
     o = Options()
+    o.method = METHODS[method]
+    for name, t in (("slice_flags_out", slice_flags_out), ("sketch_width_out", sketch_width_out)):
+        if t is not None:
+            assert t.is_cuda and t.dtype == torch.int32
+            setattr(o, name, t.data_ptr())
     o.precision = PRECISIONS[precision]
     o.econ = int(bool(econ))
     o.max_sweeps = int(max_sweeps)
@@ -110,7 +126,8 @@ def options(precision: str = "fp32", econ: bool = False, max_sweeps: int = 30, s
         assert sweeps_out.is_cuda and sweeps_out.dtype == torch.int32
         o.sweeps_out = sweeps_out.data_ptr()
     if stage_events is not None:
-        arr = (ctypes.c_void_p * 4)(*[ev.cuda_event for ev in stage_events])
+        assert len(stage_events) == STAGE_EVENTS
+        arr = (ctypes.c_void_p * STAGE_EVENTS)(*[ev.cuda_event for ev in stage_events])
         o._events_keepalive = arr
         o.stage_events = ctypes.cast(arr, ctypes.c_void_p).value
     return o
@@ -295,6 +312,29 @@ def prox_tnn_batched(Ys, taus, outs=None, opts: Options | None = None, stream=No
     _check(lib().tp_prox_tnn_batched(d, len(Ys), ctypes.byref(o), _stream(stream)),
            "tp_prox_tnn_batched")
     return Xs
+
+
+def proposer_train(Ys, taus, steps: int = 300, lr: float = 3e-3, seed: int = 0, stream=None) -> float:
+    """Fit the rank proposer of the learned prox method on the slices of these tensors
+    (labelled by the plain Jacobi path); returns the final mean squared error."""
+    Ys = [_prep(Y, "Y") for Y in Ys]
+    d = make_descs(Ys, Ys, taus)
+    mse = ctypes.c_double(0.0)
+    _check(lib().tp_proposer_train(d, len(Ys), int(steps), float(lr), int(seed), ctypes.byref(mse),
+                                   _stream(stream)), "tp_proposer_train")
+    return mse.value
+
+
+def proposer_get() -> np.ndarray:
+    out = np.zeros(PROPOSER_FLOATS, dtype=np.float32)
+    _check(lib().tp_proposer_get(out.ctypes.data), "tp_proposer_get")
+    return out
+
+
+def proposer_set(params: np.ndarray) -> None:
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    assert params.size == PROPOSER_FLOATS
+    _check(lib().tp_proposer_set(params.ctypes.data), "tp_proposer_set")
 
 
 def exported_symbols():
