@@ -276,7 +276,6 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     std::vector<int64_t> work(count, 0);
     int64_t nfft = 0;
     int max_n1 = 1, max_n2 = 1;
-    size_t sk_smem = 0;
     for (int64_t t = 0; t < count; ++t) {
         const int64_t n1 = d[t].n1, n2 = d[t].n2, n3 = d[t].n3;
         if (n1 == 0 || n2 == 0 || n3 == 0) continue;
@@ -289,8 +288,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         ++nfft;
         max_n1 = std::max<int>(max_n1, (int)n1);
         max_n2 = std::max<int>(max_n2, (int)n2);
-        const size_t need = sketch_smem_need((int)n1, (int)n2, kSketchMaxL);
-        if (need <= (size_t)(200 * 1024)) sk_smem = std::max(sk_smem, need);
+
     }
     if (nfft == 0) return TP_OK;
     bytes += 2 * Workspace::round(sizeof(FftJob) * (nfft + 1));
@@ -298,7 +296,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     if (need_feat) {
         bytes += Workspace::round(sizeof(SvdJob) * (slices + 1));        // natural-order jobs
         bytes += Workspace::round(sizeof(float) * kProposerInputs * slices);
-        bytes += 3 * Workspace::round(sizeof(int32_t) * slices);          // ell, flags, counts
+        bytes += 4 * Workspace::round(sizeof(int32_t) * slices);  // ell, flags, counts, order
     }
     if (train) bytes += Workspace::round(sizeof(float) * proposer_fit_scratch_floats((int)slices));
     Workspace ws(s);
@@ -307,7 +305,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     TP_TRY(ws.check());
     TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
     float* feat = nullptr;
-    int32_t *ell = nullptr, *flags = nullptr, *counts = nullptr;
+    int32_t *ell = nullptr, *flags = nullptr, *counts = nullptr, *d_order = nullptr;
     SvdJob* d_nat = nullptr;
     if (need_feat) {
         d_nat = ws.take<SvdJob>(slices);
@@ -315,6 +313,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         ell = ws.take<int32_t>(slices);
         flags = ws.take<int32_t>(slices);
         counts = ws.take<int32_t>(slices);
+        d_order = ws.take<int32_t>(slices);
         TP_TRY(ws.check());
     }
     FftBatch fwd, inv;
@@ -366,15 +365,44 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     if (learned) {
         TP_CUDA(launch_proposer(feat, d_nat, (int)slices, ell, s));
         TP_TRY(o.mark(2, s));
-        SketchParams sp;
-        sp.ell = ell;
-        sp.flag = flags;
-        sp.count = counts;
-        sp.seed = 0x9e3779b9u;
-        sp.power_iters = 1;
-        sp.resid_tol = 1e-5f;
-        sp.smem_bytes = (int)sk_smem;
-        TP_CUDA(launch_sketch_svt(d_nat, (int)slices, sk_smem, sp, s));
+        // size classes by worst-case shared memory (sketch width 32): 4, 3, 2 and 1 CTAs per
+        // SM; slices beyond the last class get a launch without shared memory and fall back
+        const size_t caps[5] = {56 * 1024, 75 * 1024, 113 * 1024, 220 * 1024, 0};
+        std::vector<std::vector<int32_t>> cls(5);
+        for (int64_t j = 0; j < slices; ++j) {
+            const size_t need = sketch_smem_need(natural[j].n1, natural[j].n2, kSketchMaxL);
+            int c = 4;
+            for (int q = 0; q < 4; ++q)
+                if (need <= caps[q]) { c = q; break; }
+            cls[c].push_back((int32_t)j);
+        }
+        std::vector<int32_t> order;
+        std::vector<size_t> start(5), smem(5, 0);
+        for (int c = 0; c < 5; ++c) {
+            std::stable_sort(cls[c].begin(), cls[c].end(), [&](int32_t a, int32_t b) {
+                return (int64_t)natural[a].n1 * natural[a].n2 > (int64_t)natural[b].n1 * natural[b].n2;
+            });
+            start[c] = order.size();
+            for (int32_t j : cls[c]) {
+                order.push_back(j);
+                if (c < 4)
+                    smem[c] = std::max(smem[c], sketch_smem_need(natural[j].n1, natural[j].n2, kSketchMaxL));
+            }
+        }
+        TP_TRY(upload(d_order, order, s));
+        for (int c = 0; c < 5; ++c) {
+            if (cls[c].empty()) continue;
+            SketchParams sp;
+            sp.order = d_order + start[c];
+            sp.ell = ell;
+            sp.flag = flags;
+            sp.count = counts;
+            sp.seed = 0x9e3779b9u;
+            sp.power_iters = 1;
+            sp.resid_tol = 1e-5f;
+            sp.smem_bytes = (int)smem[c];
+            TP_CUDA(launch_sketch_svt(d_nat, (int)cls[c].size(), smem[c], sp, s));
+        }
         TP_TRY(o.mark(3, s));
         if (o.slice_flags_out)
             TP_CUDA(cudaMemcpyAsync(o.slice_flags_out, flags, sizeof(int32_t) * slices,

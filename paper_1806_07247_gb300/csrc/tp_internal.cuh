@@ -125,6 +125,7 @@ constexpr int kProposerInputs = 12;    // features per slice
 constexpr int kProposerFloats = TP_PROPOSER_FLOATS;
 
 struct SketchParams {
+    const int32_t* order = nullptr;  // CTA -> job index (nullptr: identity)
     const int32_t* ell;   // per job: sketch width (0: go to the full Jacobi SVD)
     int32_t* flag;        // per job: 0 = W written by the sketch path, 1 = needs Jacobi
     int32_t* count;       // per job: #{sigma > tau} on success (optional)
@@ -135,8 +136,8 @@ struct SketchParams {
 };
 
 __host__ __device__ inline size_t sketch_smem_need(int n1, int n2, int l) {
-    return sizeof(float2) * ((size_t)2 * n1 * l + (size_t)n2 * l + (size_t)l * l + n1 + n2 +
-                             2 * kSketchMaxL) +
+    return sizeof(float2) * ((size_t)2 * n1 * l + (size_t)n2 * l + (size_t)l * l + (size_t)8 * n1 +
+                             n1 + n2 + 2 * kSketchMaxL) +
            sizeof(float) * (2 * kSketchMaxL + 32) + 64;
 }
 size_t features_smem_bytes(int n1, int n2);
@@ -144,7 +145,7 @@ cudaError_t launch_features(const SvdJob* jobs, int njobs, int max_n1, int max_n
                             uint32_t seed, cudaStream_t s);
 cudaError_t launch_proposer(const float* feat, const SvdJob* jobs, int njobs, int32_t* ell,
                             cudaStream_t s);
-cudaError_t launch_sketch_svt(const SvdJob* jobs, int njobs, size_t smem, const SketchParams& p,
+cudaError_t launch_sketch_svt(const SvdJob* jobs, int ncta, size_t smem, const SketchParams& p,
                               cudaStream_t s);
 bool proposer_ready();
 cudaError_t proposer_set(const float* host);

@@ -85,83 +85,95 @@ __device__ __forceinline__ float2 ld_a(const float2* A, int64_t idx, bool real) 
     return v;
 }
 
-// Y (n1 x l, ld n1) = A X (X: n2 x l, ld n2, shared).  Threads own rows; when rows are fewer
-// than threads, the l columns are split into chunks over thread groups.
+// Y (n1 x l, ld n1) = A X (X: n2 x l, ld n2, shared).  A work item is one row of Y and a
+// chunk of 8 of its columns; all threads of the CTA share the items.
 __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, const float2* X,
                        float2* Y, int l) {
-    const int groups = max(1, min(kT / max(n1, 1), 4));
-    const int chunk = (l + groups - 1) / groups;
-    for (int t = threadIdx.x; t < n1 * groups; t += kT) {
-        const int i = t % n1, g = t / n1;
-        const int j0 = g * chunk, j1 = min(l, j0 + chunk);
-        float2 acc[kLMax];
+    const int nch = (l + 7) >> 3;
+    for (int t = threadIdx.x; t < n1 * nch; t += kT) {
+        const int i = t % n1, j0 = (t / n1) * 8;
+        const int jn = min(8, l - j0);
+        float2 acc[8];
 #pragma unroll
-        for (int j = 0; j < kLMax; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int jj = 0; jj < 8; ++jj) acc[jj] = make_float2(0.f, 0.f);
+        const float2* x = X + (size_t)n2 * j0;
         for (int c = 0; c < n2; ++c) {
             const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
 #pragma unroll
-            for (int j = 0; j < kLMax; ++j) {
-                if (j >= j0 && j < j1) {
-                    const float2 x = X[c + n2 * j];
-                    acc[j].x = fmaf(a.x, x.x, fmaf(-a.y, x.y, acc[j].x));
-                    acc[j].y = fmaf(a.x, x.y, fmaf(a.y, x.x, acc[j].y));
+            for (int jj = 0; jj < 8; ++jj) {
+                if (jj < jn) {
+                    const float2 xv = x[c + (size_t)n2 * jj];
+                    acc[jj].x = fmaf(a.x, xv.x, fmaf(-a.y, xv.y, acc[jj].x));
+                    acc[jj].y = fmaf(a.x, xv.y, fmaf(a.y, xv.x, acc[jj].y));
                 }
             }
         }
 #pragma unroll
-        for (int j = 0; j < kLMax; ++j)
-            if (j >= j0 && j < j1) Y[i + n1 * j] = acc[j];
+        for (int jj = 0; jj < 8; ++jj)
+            if (jj < jn) Y[i + (size_t)n1 * (j0 + jj)] = acc[jj];
     }
 }
 
-// Z (n2 x l, ld n2) = A^H Y (Y: n1 x l, ld n1, shared).  Threads own columns of A and a range
-// of its rows; partial sums meet in Z through shared-memory atomics.
+// Z (n2 x l, ld n2) = A^H Y (Y: n1 x l, ld n1, shared).  A work item is one column of A, a
+// chunk of 8 columns of Y and (when items are fewer than threads) a range of rows; partial
+// sums over row ranges meet in Z through shared-memory atomics.
 __device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real, const float2* Y,
                         float2* Z, int l) {
-    for (int t = threadIdx.x; t < n2 * l; t += kT) Z[t] = make_float2(0.f, 0.f);
-    __syncthreads();
-    const int parts = max(1, min(kT / max(n2, 1), 8));
+    const int nch = (l + 7) >> 3;
+    const int items = n2 * nch;
+    const int parts = max(1, min(kT / max(items, 1), 8));
     const int span = (n1 + parts - 1) / parts;
-    for (int t = threadIdx.x; t < n2 * parts; t += kT) {
-        const int c = t % n2, pr = t / n2;
+    if (parts > 1) {
+        for (int t = threadIdx.x; t < n2 * l; t += kT) Z[t] = make_float2(0.f, 0.f);
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < items * parts; t += kT) {
+        const int c = t % n2, rest = t / n2, ch = rest % nch, pr = rest / nch;
+        const int j0 = ch * 8, jn = min(8, l - j0);
         const int i0 = pr * span, i1 = min(n1, i0 + span);
-        float2 acc[kLMax];
+        float2 acc[8];
 #pragma unroll
-        for (int j = 0; j < kLMax; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int jj = 0; jj < 8; ++jj) acc[jj] = make_float2(0.f, 0.f);
+        const float2* y = Y + (size_t)n1 * j0;
         for (int i = i0; i < i1; ++i) {
             const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
 #pragma unroll
-            for (int j = 0; j < kLMax; ++j) {
-                if (j < l) {
-                    const float2 y = Y[i + n1 * j];
-                    acc[j].x = fmaf(a.x, y.x, fmaf(a.y, y.y, acc[j].x));  // conj(a) y
-                    acc[j].y = fmaf(a.x, y.y, fmaf(-a.y, y.x, acc[j].y));
+            for (int jj = 0; jj < 8; ++jj) {
+                if (jj < jn) {
+                    const float2 yv = y[i + (size_t)n1 * jj];
+                    acc[jj].x = fmaf(a.x, yv.x, fmaf(a.y, yv.y, acc[jj].x));  // conj(a) y
+                    acc[jj].y = fmaf(a.x, yv.y, fmaf(-a.y, yv.x, acc[jj].y));
                 }
             }
         }
 #pragma unroll
-        for (int j = 0; j < kLMax; ++j) {
-            if (j < l) {
-                atomicAdd(&Z[c + n2 * j].x, acc[j].x);
-                atomicAdd(&Z[c + n2 * j].y, acc[j].y);
+        for (int jj = 0; jj < 8; ++jj) {
+            if (jj < jn) {
+                float2* z = Z + c + (size_t)n2 * (j0 + jj);
+                if (parts == 1) {
+                    *z = acc[jj];
+                } else {
+                    atomicAdd(&z->x, acc[jj].x);
+                    atomicAdd(&z->y, acc[jj].y);
+                }
             }
         }
     }
     __syncthreads();
 }
 
-// Two-pass classical Gram-Schmidt on the l columns (length n, ld n) of Y, in place.
-// A column whose remainder is below 1e-6 of its original norm is set to zero.
+// Two-pass classical Gram-Schmidt on the l columns (length n, ld n) of Y, in place.  The
+// first pass's dot products include the column with itself, so its norm before the passes
+// comes for free; a column whose remainder is below 1e-6 of that norm is set to zero.
 __device__ void orthonormalize(float2* Y, int n, int l, float* red, float2* coef) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = 0; j < l; ++j) {
-        float2* y = Y + n * j;
-        float n0 = 0.f;
-        for (int e = threadIdx.x; e < n; e += kT) n0 = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, n0));
-        n0 = block_sum(n0, red);
+        float2* y = Y + (size_t)n * j;
+        float nrm0 = 0.f, nrm1 = 0.f;
         for (int pass = 0; pass < 2; ++pass) {
-            for (int i = warp; i < j; i += kT / 32) {
-                const float2* q = Y + n * i;
+            const int ndots = pass == 0 ? j + 1 : j;
+            for (int i = warp; i < ndots; i += kT / 32) {
+                const float2* q = Y + (size_t)n * i;
                 float dr = 0.f, di = 0.f;
                 for (int e = lane; e < n; e += 32) {
                     dr = fmaf(q[e].x, y[e].x, fmaf(q[e].y, y[e].y, dr));
@@ -172,21 +184,22 @@ __device__ void orthonormalize(float2* Y, int n, int l, float* red, float2* coef
                 if (lane == 0) coef[i] = make_float2(dr, di);
             }
             __syncthreads();
+            if (pass == 0) nrm0 = coef[j].x;
+            float part = 0.f;
             for (int e = threadIdx.x; e < n; e += kT) {
                 float2 v = y[e];
                 for (int i = 0; i < j; ++i) {
-                    const float2 q = Y[e + n * i], d = coef[i];
+                    const float2 q = Y[e + (size_t)n * i], d = coef[i];
                     v.x -= fmaf(d.x, q.x, -d.y * q.y);
                     v.y -= fmaf(d.x, q.y, d.y * q.x);
                 }
                 y[e] = v;
+                part = fmaf(v.x, v.x, fmaf(v.y, v.y, part));
             }
-            __syncthreads();
+            if (pass == 1) nrm1 = block_sum(part, red);
+            else __syncthreads();
         }
-        float n1 = 0.f;
-        for (int e = threadIdx.x; e < n; e += kT) n1 = fmaf(y[e].x, y[e].x, fmaf(y[e].y, y[e].y, n1));
-        n1 = block_sum(n1, red);
-        const float inv = (n1 > 1e-12f * n0 && n1 > 0.f) ? rsqrtf(n1) : 0.f;
+        const float inv = (nrm1 > 1e-12f * nrm0 && nrm1 > 0.f) ? 1.f / sqrtf(nrm1) : 0.f;
         for (int e = threadIdx.x; e < n; e += kT) {
             y[e].x *= inv;
             y[e].y *= inv;
@@ -195,11 +208,12 @@ __device__ void orthonormalize(float2* Y, int n, int l, float* red, float2* coef
     }
 }
 
-__global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
                                                         SketchParams P) {
     extern __shared__ float4 smem4[];
     __shared__ int s_rot;
-    const int job = blockIdx.x;
+    __shared__ float s_res[8];
+    const int job = P.order ? P.order[blockIdx.x] : (int)blockIdx.x;
     const SvdJob J = jobs[job];
     const int n1 = J.n1, n2 = J.n2;
     const bool real = J.real_slice != 0;
@@ -211,10 +225,11 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
         return;
     }
     float2* Q = reinterpret_cast<float2*>(smem4);  // n1 x l
-    float2* U = Q + (size_t)n1 * l;                 // n1 x l
-    float2* Z = U + (size_t)n1 * l;                 // n2 x l
+    float2* U = Q + (size_t)n1 * l;                 // n1 x l: U = Q V
+    float2* Z = U + (size_t)n1 * l;                 // n2 x l (Omega, B^H, D, then R)
     float2* V = Z + (size_t)n2 * l;                 // l x l
-    float2* xv = V + l * l;                         // n2
+    float2* T = V + (size_t)l * l;                  // n1 x 8
+    float2* xv = T + (size_t)n1 * 8;                // n2
     float2* yv = xv + n2;                           // n1
     float2* coef = yv + n1;                         // 2 kLMax
     float* sig = reinterpret_cast<float*>(coef + 2 * kLMax);
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
     float* red = fac + kLMax;
     const float2* A = J.A;
 
-    // range finder
+    // 2. range finder with one (or more) power iterations
     for (int t = tid; t < n2 * l; t += kT) Z[t] = omega(P.seed, job, t % n2, t / n2, real);
     __syncthreads();
     mult_a(A, n1, n2, real, Z, Q, l);
@@ -237,7 +252,7 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
     }
     mult_ah(A, n1, n2, real, Q, Z, l);  // Z = A^H Q = B^H
 
-    // one-sided Jacobi on the l columns of Z, V accumulated
+    // 3. one-sided Jacobi on the l columns of Z, V accumulated
     for (int t = tid; t < l * l; t += kT) V[t] = make_float2((t % l) == (t / l) ? 1.f : 0.f, 0.f);
     __syncthreads();
     const float tol = 8.f * 1.1920928955078125e-07f, tol2 = tol * tol;
@@ -253,8 +268,8 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
                 else { a = (r + pi) % (Np - 1); b = (r - pi + Np - 1) % (Np - 1); }
                 if (a >= l || b >= l) continue;
                 const int p = min(a, b), q = max(a, b);
-                float2* gp = Z + n2 * p;
-                float2* gq = Z + n2 * q;
+                float2* gp = Z + (size_t)n2 * p;
+                float2* gq = Z + (size_t)n2 * q;
                 float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
                 for (int e = lane; e < n2; e += 32) {
                     const float2 x = gp[e], y = gq[e];
@@ -278,8 +293,8 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
                     gq[e] = make_float2(fmaf(sr, x.x, fmaf(-si, x.y, c * y.x)),
                                         fmaf(sr, x.y, fmaf(si, x.x, c * y.y)));
                 }
-                float2* vp = V + l * p;
-                float2* vq = V + l * q;
+                float2* vp = V + (size_t)l * p;
+                float2* vq = V + (size_t)l * q;
                 for (int e = lane; e < l; e += 32) {
                     const float2 x = vp[e], y = vq[e];
                     vp[e] = make_float2(fmaf(c, x.x, fmaf(-sr, y.x, -si * y.y)),
@@ -296,13 +311,16 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
     }
     // sigma_j = ||d_j||
     for (int j = warp; j < l; j += kT / 32) {
-        float s = 0.f;
-        for (int e = lane; e < n2; e += 32) s = fmaf(Z[e + n2 * j].x, Z[e + n2 * j].x, fmaf(Z[e + n2 * j].y, Z[e + n2 * j].y, s));
-        s = warp_sum(s);
-        if (lane == 0) sig[j] = sqrtf(s);
+        float sacc = 0.f;
+        for (int e = lane; e < n2; e += 32) {
+            const float2 z = Z[e + (size_t)n2 * j];
+            sacc = fmaf(z.x, z.x, fmaf(z.y, z.y, sacc));
+        }
+        sacc = warp_sum(sacc);
+        if (lane == 0) sig[j] = sqrtf(sacc);
     }
     __syncthreads();
-    // (a) the sketch must reach below tau; kept set decided in FP64
+    // 4(a): the sketch must reach below tau; the kept set is decided in FP64
     float smin = 3.4e38f, smax = 0.f;
     int k = 0;
     for (int j = 0; j < l; ++j) {
@@ -311,13 +329,13 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
         k += ((double)sig[j] > J.tau);
     }
     bool ok = conv && !((double)smin > J.tau);
-    // U = Q V (n1 x l); D -> R = D / sigma (columns with sigma > tau only matter)
     if (ok) {
+        // U = Q V; R = D / sigma for the kept columns (else 0)
         for (int t = tid; t < n1 * l; t += kT) {
             const int i = t % n1, j = t / n1;
             float2 acc = make_float2(0.f, 0.f);
             for (int m = 0; m < l; ++m) {
-                const float2 q = Q[i + n1 * m], v = V[m + l * j];
+                const float2 q = Q[i + (size_t)n1 * m], v = V[m + (size_t)l * j];
                 acc.x = fmaf(q.x, v.x, fmaf(-q.y, v.y, acc.x));
                 acc.y = fmaf(q.x, v.y, fmaf(q.y, v.x, acc.y));
             }
@@ -331,26 +349,37 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
             Z[t].y *= f;
         }
         __syncthreads();
-        // (b) residuals of the kept triplets: || A r_j - sigma_j u_j ||  (A R into Q)
-        mult_a(A, n1, n2, real, Z, Q, l);
-        __syncthreads();
+        // 4(b): residuals of the kept triplets, 8 columns at a time: T = A R_chunk
         float worst = 0.f;
-        for (int j = 0; j < l; ++j) {
-            if (!((double)sig[j] > J.tau)) continue;
-            float s = 0.f;
-            for (int e = tid; e < n1; e += kT) {
-                const float2 a = Q[e + n1 * j], u = U[e + n1 * j];
-                const float dx = a.x - sig[j] * u.x, dy = a.y - sig[j] * u.y;
-                s = fmaf(dx, dx, fmaf(dy, dy, s));
+        for (int j0 = 0; j0 < l; j0 += 8) {
+            const int jn = min(8, l - j0);
+            mult_a(A, n1, n2, real, Z + (size_t)n2 * j0, T, jn);
+            if (tid < 8) s_res[tid] = 0.f;
+            __syncthreads();
+            for (int jj = 0; jj < jn; ++jj) {
+                const int j = j0 + jj;
+                if (!((double)sig[j] > J.tau)) continue;
+                float sacc = 0.f;
+                for (int e = tid; e < n1; e += kT) {
+                    const float2 a = T[e + (size_t)n1 * jj], u = U[e + (size_t)n1 * j];
+                    const float dx = a.x - sig[j] * u.x, dy = a.y - sig[j] * u.y;
+                    sacc = fmaf(dx, dx, fmaf(dy, dy, sacc));
+                }
+                sacc = warp_sum(sacc);
+                if (lane == 0) atomicAdd(&s_res[jj], sacc);
             }
-            s = block_sum(s, red);
-            // the triplet enters W with weight (sigma - tau) / sigma
-            worst = fmaxf(worst, sqrtf(s) * (float)(((double)sig[j] - J.tau) / sig[j]));
+            __syncthreads();
+            for (int jj = 0; jj < jn; ++jj) {
+                const int j = j0 + jj;
+                if ((double)sig[j] > J.tau)
+                    worst = fmaxf(worst, sqrtf(s_res[jj]) * (float)(((double)sig[j] - J.tau) / sig[j]));
+            }
+            __syncthreads();
         }
         ok = worst <= P.resid_tol * smax;
     }
     if (ok) {
-        // (c) norm of A - U_k S_k R_k^H by two power iterations from a random start
+        // 4(c): norm of A - U_k S_k R_k^H by two power iterations from a random start
         for (int c = tid; c < n2; c += kT) xv[c] = omega(P.seed ^ 0x5bd1e995u, job, c, 0, real);
         __syncthreads();
         float est = 0.f;
@@ -360,17 +389,18 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
             nx = block_sum(nx, red);
             const float inx = nx > 0.f ? rsqrtf(nx) : 0.f;
             for (int c = tid; c < n2; c += kT) { xv[c].x *= inx; xv[c].y *= inx; }
-            // coef_j = sigma_j (r_j^H x)
+            __syncthreads();
+            // coef_j = sigma_j (r_j^H x)   (r_j = 0 for the columns that are not kept)
             for (int j = warp; j < l; j += kT / 32) {
                 float dr = 0.f, di = 0.f;
                 for (int c = lane; c < n2; c += 32) {
-                    const float2 rr = Z[c + n2 * j], x = xv[c];
+                    const float2 rr = Z[c + (size_t)n2 * j], x = xv[c];
                     dr = fmaf(rr.x, x.x, fmaf(rr.y, x.y, dr));
                     di = fmaf(rr.x, x.y, fmaf(-rr.y, x.x, di));
                 }
                 dr = warp_sum(dr);
                 di = warp_sum(di);
-                if (lane == 0) coef[j] = make_float2(sig[j] * fac[j] * sig[j] * dr, sig[j] * fac[j] * sig[j] * di);
+                if (lane == 0) coef[j] = make_float2(sig[j] * dr, sig[j] * di);
             }
             __syncthreads();
             // y = A x - U coef
@@ -382,24 +412,25 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
                     acc.y = fmaf(a.x, x.y, fmaf(a.y, x.x, acc.y));
                 }
                 for (int j = 0; j < l; ++j) {
-                    const float2 u = U[i + n1 * j], d = coef[j];
+                    const float2 u = U[i + (size_t)n1 * j], d = coef[j];
                     acc.x -= fmaf(u.x, d.x, -u.y * d.y);
                     acc.y -= fmaf(u.x, d.y, u.y * d.x);
                 }
                 yv[i] = acc;
             }
             __syncthreads();
-            // coef_j = sigma_j (u_j^H y)
+            // coef_j = sigma_j (u_j^H y) for the kept columns
             for (int j = warp; j < l; j += kT / 32) {
                 float dr = 0.f, di = 0.f;
                 for (int i = lane; i < n1; i += 32) {
-                    const float2 u = U[i + n1 * j], y = yv[i];
+                    const float2 u = U[i + (size_t)n1 * j], y = yv[i];
                     dr = fmaf(u.x, y.x, fmaf(u.y, y.y, dr));
                     di = fmaf(u.x, y.y, fmaf(-u.y, y.x, di));
                 }
                 dr = warp_sum(dr);
                 di = warp_sum(di);
-                if (lane == 0) coef[j] = make_float2(sig[j] * fac[j] * sig[j] * dr, sig[j] * fac[j] * sig[j] * di);
+                const float w = fac[j] > 0.f ? sig[j] : 0.f;
+                if (lane == 0) coef[j] = make_float2(w * dr, w * di);
             }
             __syncthreads();
             // x = A^H y - R coef
@@ -411,7 +442,7 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
                     acc.y = fmaf(a.x, y.y, fmaf(-a.y, y.x, acc.y));
                 }
                 for (int j = 0; j < l; ++j) {
-                    const float2 rr = Z[c + n2 * j], d = coef[j];
+                    const float2 rr = Z[c + (size_t)n2 * j], d = coef[j];
                     acc.x -= fmaf(rr.x, d.x, -rr.y * d.y);
                     acc.y -= fmaf(rr.x, d.y, rr.y * d.x);
                 }
@@ -439,9 +470,8 @@ __global__ void __launch_bounds__(kT) sketch_svt_kernel(const SvdJob* __restrict
         for (int j = 0; j < l; ++j) {
             const float f = fac[j];
             if (f == 0.f) continue;
-            const float2 u = U[i + n1 * j], rr = Z[c + n2 * j];
-            // f u conj(r)
-            acc.x = fmaf(f, fmaf(u.x, rr.x, u.y * rr.y), acc.x);
+            const float2 u = U[i + (size_t)n1 * j], rr = Z[c + (size_t)n2 * j];
+            acc.x = fmaf(f, fmaf(u.x, rr.x, u.y * rr.y), acc.x);  // f u conj(r)
             acc.y = fmaf(f, fmaf(u.y, rr.x, -u.x * rr.y), acc.y);
         }
         if (real) acc.y = 0.f;
@@ -665,15 +695,15 @@ cudaError_t launch_proposer(const float* feat, const SvdJob* jobs, int njobs, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_sketch_svt(const SvdJob* jobs, int njobs, size_t smem, const SketchParams& p,
+cudaError_t launch_sketch_svt(const SvdJob* jobs, int ncta, size_t smem, const SketchParams& p,
                               cudaStream_t s) {
-    if (njobs <= 0) return cudaSuccess;
+    if (ncta <= 0) return cudaSuccess;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(sketch_svt_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sketch_svt_kernel<<<njobs, kT, smem, s>>>(jobs, p);
+    sketch_svt_kernel<<<ncta, kT, smem, s>>>(jobs, p);
     return cudaGetLastError();
 }
 
