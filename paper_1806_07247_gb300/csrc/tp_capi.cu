@@ -365,12 +365,14 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     if (learned) {
         TP_CUDA(launch_proposer(feat, d_nat, (int)slices, ell, s));
         TP_TRY(o.mark(2, s));
-        // size classes by worst-case shared memory (sketch width 32): 4, 3, 2 and 1 CTAs per
-        // SM; slices beyond the last class get a launch without shared memory and fall back
+        // size classes by shared memory at sketch width 24 (a slice whose proposed width needs
+        // more than its class provides falls back): 4, 3, 2 and 1 CTAs per SM; slices beyond
+        // the last class get a launch without shared memory and fall back
+        constexpr int kSizeL = 24;
         const size_t caps[5] = {56 * 1024, 75 * 1024, 113 * 1024, 220 * 1024, 0};
         std::vector<std::vector<int32_t>> cls(5);
         for (int64_t j = 0; j < slices; ++j) {
-            const size_t need = sketch_smem_need(natural[j].n1, natural[j].n2, kSketchMaxL);
+            const size_t need = sketch_smem_need(natural[j].n1, natural[j].n2, kSizeL);
             int c = 4;
             for (int q = 0; q < 4; ++q)
                 if (need <= caps[q]) { c = q; break; }
@@ -386,7 +388,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             for (int32_t j : cls[c]) {
                 order.push_back(j);
                 if (c < 4)
-                    smem[c] = std::max(smem[c], sketch_smem_need(natural[j].n1, natural[j].n2, kSketchMaxL));
+                    smem[c] = std::max(smem[c], sketch_smem_need(natural[j].n1, natural[j].n2, kSizeL));
             }
         }
         TP_TRY(upload(d_order, order, s));

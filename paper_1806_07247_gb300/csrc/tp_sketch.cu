@@ -8,9 +8,10 @@
 //      log min(n1, n2) -- and predicts k = #{sigma > tau}; the sketch width is l = k + 8;
 //   2. randomized range finder: Y = A Omega (Omega n2 x l, random +-1 / (+-1 +- i)/sqrt 2
 //      from a counter-based hash), q power iterations (Z = A^H Q, Y = A Z), each followed by
-//      Gram-Schmidt orthonormalisation (two passes), Q = orth(Y);
-//   3. small SVD: Z = A^H Q (n2 x l); one-sided Jacobi on the l columns of Z, accumulating
-//      V (l x l): Z V = D, sigma_j = ||d_j||, so A ~ Q Z^H = (Q V) diag(sigma) (D / sigma)^H;
+//      shifted CholeskyQR3 orthonormalisation, Q = orth(Y);
+//   3. small SVD: Z = A^H Q (n2 x l) = B^H; one warp diagonalises the l x l Gram matrix
+//      Z^H Z = V diag(lambda) V^H by two-sided Jacobi; D = Z V, sigma_j = ||d_j||, so
+//      A ~ Q Z^H = (Q V) diag(sigma) (D / sigma)^H;
 //   4. acceptance: (a) the smallest of the l computed singular values is below tau (else the
 //      rank was underestimated); (b) every kept triplet (u, sigma, r) has
 //      ||A r - sigma u|| (sigma - tau) / sigma <= rtol * sigma_max, its weight in W; (c) two
@@ -97,6 +98,7 @@ __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, 
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) acc[jj] = make_float2(0.f, 0.f);
         const float2* x = X + (size_t)n2 * j0;
+#pragma unroll 4
         for (int c = 0; c < n2; ++c) {
             const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
 #pragma unroll
@@ -135,6 +137,7 @@ __device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real,
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) acc[jj] = make_float2(0.f, 0.f);
         const float2* y = Y + (size_t)n1 * j0;
+#pragma unroll 4
         for (int i = i0; i < i1; ++i) {
             const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
 #pragma unroll
@@ -162,60 +165,173 @@ __device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real,
     __syncthreads();
 }
 
-// Two-pass classical Gram-Schmidt on the l columns (length n, ld n) of Y, in place.  The
-// first pass's dot products include the column with itself, so its norm before the passes
-// comes for free; a column whose remainder is below 1e-6 of that norm is set to zero.
-__device__ void orthonormalize(float2* Y, int n, int l, float* red, float2* coef) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int j = 0; j < l; ++j) {
-        float2* y = Y + (size_t)n * j;
-        float nrm0 = 0.f, nrm1 = 0.f;
-        for (int pass = 0; pass < 2; ++pass) {
-            const int ndots = pass == 0 ? j + 1 : j;
-            for (int i = warp; i < ndots; i += kT / 32) {
-                const float2* q = Y + (size_t)n * i;
-                float dr = 0.f, di = 0.f;
-                for (int e = lane; e < n; e += 32) {
-                    dr = fmaf(q[e].x, y[e].x, fmaf(q[e].y, y[e].y, dr));
-                    di = fmaf(q[e].x, y[e].y, fmaf(-q[e].y, y[e].x, di));
-                }
-                dr = warp_sum(dr);
-                di = warp_sum(di);
-                if (lane == 0) coef[i] = make_float2(dr, di);
-            }
-            __syncthreads();
-            if (pass == 0) nrm0 = coef[j].x;
-            float part = 0.f;
-            for (int e = threadIdx.x; e < n; e += kT) {
-                float2 v = y[e];
-                for (int i = 0; i < j; ++i) {
-                    const float2 q = Y[e + (size_t)n * i], d = coef[i];
-                    v.x -= fmaf(d.x, q.x, -d.y * q.y);
-                    v.y -= fmaf(d.x, q.y, d.y * q.x);
-                }
-                y[e] = v;
-                part = fmaf(v.x, v.x, fmaf(v.y, v.y, part));
-            }
-            if (pass == 1) nrm1 = block_sum(part, red);
-            else __syncthreads();
+// G (l x l, column-major, full Hermitian) = Y^H Y for Y n x l (ld n).
+__device__ void gram(const float2* Y, int n, int l, float2* G) {
+    for (int t = threadIdx.x; t < l * l; t += kT) {
+        const int a = t % l, b = t / l;
+        if (a > b) continue;
+        const float2* ya = Y + (size_t)n * a;
+        const float2* yb = Y + (size_t)n * b;
+        float gr = 0.f, gi = 0.f;
+#pragma unroll 4
+        for (int e = 0; e < n; ++e) {
+            const float2 u = ya[e], v = yb[e];
+            gr = fmaf(u.x, v.x, fmaf(u.y, v.y, gr));  // conj(u) v
+            gi = fmaf(u.x, v.y, fmaf(-u.y, v.x, gi));
         }
-        const float inv = (nrm1 > 1e-12f * nrm0 && nrm1 > 0.f) ? 1.f / sqrtf(nrm1) : 0.f;
+        G[a + l * b] = make_float2(gr, gi);
+        G[b + l * a] = make_float2(gr, -gi);
+    }
+    __syncthreads();
+}
+
+// Cholesky factor of G + shift I by one warp: L (lower triangle of G, real positive
+// diagonal) overwrites the lower triangle.  Returns false on breakdown.
+__device__ bool cholesky_warp(float2* G, int l, float shift) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    for (int k = 0; k < l; ++k) {
+        float d = 0.f;
+        if (lane == 0) {
+            d = G[k + l * k].x + shift;
+            for (int m = 0; m < k; ++m) {
+                const float2 v = G[k + l * m];
+                d -= fmaf(v.x, v.x, v.y * v.y);
+            }
+            d = (d > 0.f) ? sqrtf(d) : -1.f;
+            G[k + l * k] = make_float2(d, 0.f);
+        }
+        d = __shfl_sync(0xffffffffu, d, 0);
+        if (!(d > 0.f)) { ok = false; break; }
+        for (int i = k + 1 + lane; i < l; i += 32) {
+            float2 v = G[i + l * k];
+            for (int m = 0; m < k; ++m) {
+                const float2 a = G[i + l * m], b = G[k + l * m];  // a conj(b)
+                v.x -= fmaf(a.x, b.x, a.y * b.y);
+                v.y -= fmaf(a.y, b.x, -a.x * b.y);
+            }
+            const float inv = 1.f / d;
+            G[i + l * k] = make_float2(v.x * inv, v.y * inv);
+        }
+        __syncwarp();
+    }
+    return ok;
+}
+
+// Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa): the l columns of
+// Y (n x l, ld n) are orthonormalised in place by three passes of Y <- Y R^-1 with R^H R the
+// Cholesky factorisation of the Gram matrix, the first pass shifted by
+// 11 (n l + l (l + 1)) u ||Y||_F^2 (u = 2^-24) so that it cannot break down.
+// Returns false if a pass still breaks down (the slice then goes to the Jacobi path).
+__device__ bool cholqr3(float2* Y, int n, int l, float2* G, int* s_flag) {
+    const int warp = threadIdx.x >> 5;
+    for (int pass = 0; pass < 3; ++pass) {
+        gram(Y, n, l, G);
+        if (warp == 0) {
+            float shift = 0.f;
+            if (pass == 0) {
+                float tr = 0.f;
+                for (int j = 0; j < l; ++j) tr += G[j + l * j].x;
+                shift = 11.f * (float)(n * l + l * (l + 1)) * 5.9604645e-08f * tr;
+            }
+            const bool ok = cholesky_warp(G, l, shift);
+            if ((threadIdx.x & 31) == 0) *s_flag = ok ? 0 : 1;
+        }
+        __syncthreads();
+        if (*s_flag) return false;
+        // Y <- Y L^-H, one row per thread, in place
         for (int e = threadIdx.x; e < n; e += kT) {
-            y[e].x *= inv;
-            y[e].y *= inv;
+            for (int j = 0; j < l; ++j) {
+                float2 v = Y[e + (size_t)n * j];
+                for (int m = 0; m < j; ++m) {
+                    const float2 q = Y[e + (size_t)n * m], b = G[j + l * m];  // q conj(L_jm)
+                    v.x -= fmaf(q.x, b.x, q.y * b.y);
+                    v.y -= fmaf(q.y, b.x, -q.x * b.y);
+                }
+                const float inv = 1.f / G[j + l * j].x;
+                Y[e + (size_t)n * j] = make_float2(v.x * inv, v.y * inv);
+            }
         }
         __syncthreads();
     }
+    return true;
+}
+
+// Eigen-decomposition G = V diag(lambda) V^H of the l x l Hermitian G by one warp: parallel
+// two-sided Jacobi (round-robin pairs, one group of 32/(pairs) lanes per pair; all row
+// rotations of a round, then all column rotations).  G is overwritten by diag(lambda) (up
+// to the tolerance); V (l x l) receives the eigenvectors.  Returns false without
+// convergence in 30 sweeps.
+__device__ bool eigh_warp(float2* G, float2* V, int l) {
+    const int lane = threadIdx.x & 31;
+    for (int t = lane; t < l * l; t += 32)
+        V[t] = make_float2((t % l) == (t / l) ? 1.f : 0.f, 0.f);
+    __syncwarp();
+    if (l < 2) return true;
+    const int Np = l + (l & 1), P = Np / 2, gs = 32 / P;
+    const int pi = lane / gs, sub = lane % gs;
+    const float tol = 8.f * 1.1920928955078125e-07f, tol2 = tol * tol;
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        int rotated = 0;
+        for (int r = 0; r < Np - 1; ++r) {
+            int a = 0, b = 0;
+            if (pi == 0) { a = Np - 1; b = r; }
+            else { a = (r + pi) % (Np - 1); b = (r - pi + Np - 1) % (Np - 1); }
+            const bool act = pi < P && a < l && b < l;
+            const int p = act ? min(a, b) : 0, q = act ? max(a, b) : 0;
+            float c = 1.f, sr = 0.f, si = 0.f;
+            bool rot = false;
+            if (act) {
+                const float al = G[p + l * p].x, be = G[q + l * q].x;
+                const float2 g = G[p + l * q];
+                const float ag2 = fmaf(g.x, g.x, g.y * g.y);
+                rot = ag2 > (tol2 * fabsf(al)) * fabsf(be) && ag2 > 0.f;
+                if (rot) jacobi_rotation(al, be, g.x, g.y, ag2, c, sr, si);
+            }
+            rotated |= rot;
+            __syncwarp();
+            // rows p, q: G_pk <- c G_pk - s e G_qk, G_qk <- s conj(e) G_pk + c G_qk
+            if (rot) {
+                for (int k = sub; k < l; k += gs) {
+                    const float2 x = G[p + l * k], y = G[q + l * k];
+                    G[p + l * k] = make_float2(fmaf(c, x.x, -fmaf(sr, y.x, -si * y.y)),
+                                               fmaf(c, x.y, -fmaf(sr, y.y, si * y.x)));
+                    G[q + l * k] = make_float2(fmaf(sr, x.x, fmaf(si, x.y, c * y.x)),
+                                               fmaf(sr, x.y, fmaf(-si, x.x, c * y.y)));
+                }
+            }
+            __syncwarp();
+            // columns p, q of G and V: [x, y] <- [c x - s conj(e) y, s e x + c y]
+            if (rot) {
+                for (int k = sub; k < l; k += gs) {
+                    float2 x = G[k + l * p], y = G[k + l * q];
+                    G[k + l * p] = make_float2(fmaf(c, x.x, fmaf(-sr, y.x, -si * y.y)),
+                                               fmaf(c, x.y, fmaf(-sr, y.y, si * y.x)));
+                    G[k + l * q] = make_float2(fmaf(sr, x.x, fmaf(-si, x.y, c * y.x)),
+                                               fmaf(sr, x.y, fmaf(si, x.x, c * y.y)));
+                    x = V[k + l * p];
+                    y = V[k + l * q];
+                    V[k + l * p] = make_float2(fmaf(c, x.x, fmaf(-sr, y.x, -si * y.y)),
+                                               fmaf(c, x.y, fmaf(-sr, y.y, si * y.x)));
+                    V[k + l * q] = make_float2(fmaf(sr, x.x, fmaf(-si, x.y, c * y.x)),
+                                               fmaf(sr, x.y, fmaf(si, x.x, c * y.y)));
+                }
+            }
+            __syncwarp();
+        }
+        if (!__any_sync(0xffffffffu, rotated)) return true;
+    }
+    return false;
 }
 
 __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
-                                                        SketchParams P) {
+                                                           SketchParams P) {
     extern __shared__ float4 smem4[];
-    __shared__ int s_rot;
+    __shared__ int s_flag, s_eig;
     __shared__ float s_res[8];
     const int job = P.order ? P.order[blockIdx.x] : (int)blockIdx.x;
     const SvdJob J = jobs[job];
-    const int n1 = J.n1, n2 = J.n2;
+    const int n1 = J.n1, n2 = J.n2, nm = max(n1, n2);
     const bool real = J.real_slice != 0;
     const int l = P.ell[job];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -224,11 +340,12 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
         if (tid == 0) P.flag[job] = 1;
         return;
     }
-    float2* Q = reinterpret_cast<float2*>(smem4);  // n1 x l
-    float2* U = Q + (size_t)n1 * l;                 // n1 x l: U = Q V
-    float2* Z = U + (size_t)n1 * l;                 // n2 x l (Omega, B^H, D, then R)
+    float2* Q = reinterpret_cast<float2*>(smem4);  // max(n1, n2) x l: Q (n1 x l), later R (n2 x l)
+    float2* U = Q + (size_t)nm * l;                 // n1 x l
+    float2* Z = U + (size_t)n1 * l;                 // n2 x l: Omega, then B^H
     float2* V = Z + (size_t)n2 * l;                 // l x l
-    float2* T = V + (size_t)l * l;                  // n1 x 8
+    float2* G = V + (size_t)l * l;                  // l x l
+    float2* T = G + (size_t)l * l;                  // n1 x 8
     float2* xv = T + (size_t)n1 * 8;                // n2
     float2* yv = xv + n2;                           // n1
     float2* coef = yv + n1;                         // 2 kLMax
@@ -237,100 +354,35 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
     float* red = fac + kLMax;
     const float2* A = J.A;
 
-    // 2. range finder with one (or more) power iterations
+    // 2. range finder with power iterations; shifted CholeskyQR3 orthonormalisations
     for (int t = tid; t < n2 * l; t += kT) Z[t] = omega(P.seed, job, t % n2, t / n2, real);
     __syncthreads();
     mult_a(A, n1, n2, real, Z, Q, l);
     __syncthreads();
-    orthonormalize(Q, n1, l, red, coef);
-    for (int it = 0; it < P.power_iters; ++it) {
+    bool ok = cholqr3(Q, n1, l, G, &s_flag);
+    for (int it = 0; ok && it < P.power_iters; ++it) {
         mult_ah(A, n1, n2, real, Q, Z, l);
-        orthonormalize(Z, n2, l, red, coef);
+        ok = cholqr3(Z, n2, l, G, &s_flag);
+        if (!ok) break;
         mult_a(A, n1, n2, real, Z, Q, l);
         __syncthreads();
-        orthonormalize(Q, n1, l, red, coef);
+        ok = cholqr3(Q, n1, l, G, &s_flag);
     }
-    mult_ah(A, n1, n2, real, Q, Z, l);  // Z = A^H Q = B^H
-
-    // 3. one-sided Jacobi on the l columns of Z, V accumulated
-    for (int t = tid; t < l * l; t += kT) V[t] = make_float2((t % l) == (t / l) ? 1.f : 0.f, 0.f);
-    __syncthreads();
-    const float tol = 8.f * 1.1920928955078125e-07f, tol2 = tol * tol;
-    const int Np = l + (l & 1);
-    bool conv = false;
-    for (int sweep = 0; sweep < 40 && !conv; ++sweep) {
-        if (tid == 0) s_rot = 0;
-        __syncthreads();
-        for (int r = 0; r < Np - 1; ++r) {
-            for (int pi = warp; pi < Np / 2; pi += kT / 32) {
-                int a, b;
-                if (pi == 0) { a = Np - 1; b = r; }
-                else { a = (r + pi) % (Np - 1); b = (r - pi + Np - 1) % (Np - 1); }
-                if (a >= l || b >= l) continue;
-                const int p = min(a, b), q = max(a, b);
-                float2* gp = Z + (size_t)n2 * p;
-                float2* gq = Z + (size_t)n2 * q;
-                float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
-                for (int e = lane; e < n2; e += 32) {
-                    const float2 x = gp[e], y = gq[e];
-                    al = fmaf(x.x, x.x, fmaf(x.y, x.y, al));
-                    be = fmaf(y.x, y.x, fmaf(y.y, y.y, be));
-                    gr = fmaf(x.x, y.x, fmaf(x.y, y.y, gr));
-                    gi = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi));
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                gr = warp_sum(gr);
-                gi = warp_sum(gi);
-                const float ag2 = fmaf(gr, gr, gi * gi);
-                if (!(ag2 > (tol2 * al) * be)) continue;
-                float c, sr, si;
-                jacobi_rotation(al, be, gr, gi, ag2, c, sr, si);
-                for (int e = lane; e < n2; e += 32) {
-                    const float2 x = gp[e], y = gq[e];
-                    gp[e] = make_float2(fmaf(c, x.x, fmaf(-sr, y.x, -si * y.y)),
-                                        fmaf(c, x.y, fmaf(-sr, y.y, si * y.x)));
-                    gq[e] = make_float2(fmaf(sr, x.x, fmaf(-si, x.y, c * y.x)),
-                                        fmaf(sr, x.y, fmaf(si, x.x, c * y.y)));
-                }
-                float2* vp = V + (size_t)l * p;
-                float2* vq = V + (size_t)l * q;
-                for (int e = lane; e < l; e += 32) {
-                    const float2 x = vp[e], y = vq[e];
-                    vp[e] = make_float2(fmaf(c, x.x, fmaf(-sr, y.x, -si * y.y)),
-                                        fmaf(c, x.y, fmaf(-sr, y.y, si * y.x)));
-                    vq[e] = make_float2(fmaf(sr, x.x, fmaf(-si, x.y, c * y.x)),
-                                        fmaf(sr, x.y, fmaf(si, x.x, c * y.y)));
-                }
-                if (lane == 0) s_rot = 1;
-            }
-            __syncthreads();
+    if (ok) {
+        mult_ah(A, n1, n2, real, Q, Z, l);  // Z = A^H Q = B^H
+        // 3. B B^H = Z^H Z = V diag(lambda) V^H by one warp
+        gram(Z, n2, l, G);
+        if (warp == 0) {
+            const bool conv = eigh_warp(G, V, l);
+            if (lane == 0) s_eig = conv ? 1 : 0;
         }
-        conv = (s_rot == 0);
         __syncthreads();
+        ok = s_eig != 0;
     }
-    // sigma_j = ||d_j||
-    for (int j = warp; j < l; j += kT / 32) {
-        float sacc = 0.f;
-        for (int e = lane; e < n2; e += 32) {
-            const float2 z = Z[e + (size_t)n2 * j];
-            sacc = fmaf(z.x, z.x, fmaf(z.y, z.y, sacc));
-        }
-        sacc = warp_sum(sacc);
-        if (lane == 0) sig[j] = sqrtf(sacc);
-    }
-    __syncthreads();
-    // 4(a): the sketch must reach below tau; the kept set is decided in FP64
     float smin = 3.4e38f, smax = 0.f;
     int k = 0;
-    for (int j = 0; j < l; ++j) {
-        smin = fminf(smin, sig[j]);
-        smax = fmaxf(smax, sig[j]);
-        k += ((double)sig[j] > J.tau);
-    }
-    bool ok = conv && !((double)smin > J.tau);
     if (ok) {
-        // U = Q V; R = D / sigma for the kept columns (else 0)
+        // U = Q V (n1 x l); then D = Z V over Q (Q no longer needed), sigma_j = ||d_j||
         for (int t = tid; t < n1 * l; t += kT) {
             const int i = t % n1, j = t / n1;
             float2 acc = make_float2(0.f, 0.f);
@@ -341,19 +393,52 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
             }
             U[t] = acc;
         }
+        __syncthreads();
+        float2* R = Q;
+        for (int t = tid; t < n2 * l; t += kT) {
+            const int c = t % n2, j = t / n2;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int m = 0; m < l; ++m) {
+                const float2 z = Z[c + (size_t)n2 * m], v = V[m + (size_t)l * j];
+                acc.x = fmaf(z.x, v.x, fmaf(-z.y, v.y, acc.x));
+                acc.y = fmaf(z.x, v.y, fmaf(z.y, v.x, acc.y));
+            }
+            R[t] = acc;
+        }
+        __syncthreads();
+        for (int j = warp; j < l; j += kT / 32) {
+            float sacc = 0.f;
+            for (int e = lane; e < n2; e += 32) {
+                const float2 d = R[e + (size_t)n2 * j];
+                sacc = fmaf(d.x, d.x, fmaf(d.y, d.y, sacc));
+            }
+            sacc = warp_sum(sacc);
+            if (lane == 0) sig[j] = sqrtf(sacc);
+        }
+        __syncthreads();
+        // 4(a): the sketch must reach below tau; the kept set is decided in FP64
+        for (int j = 0; j < l; ++j) {
+            smin = fminf(smin, sig[j]);
+            smax = fmaxf(smax, sig[j]);
+            k += ((double)sig[j] > J.tau);
+        }
+        ok = !((double)smin > J.tau);
+    }
+    float2* R = Q;
+    if (ok) {
         for (int j = tid; j < l; j += kT) fac[j] = ((double)sig[j] > J.tau) ? 1.f / sig[j] : 0.f;
         __syncthreads();
         for (int t = tid; t < n2 * l; t += kT) {
             const float f = fac[t / n2];
-            Z[t].x *= f;
-            Z[t].y *= f;
+            R[t].x *= f;
+            R[t].y *= f;
         }
         __syncthreads();
         // 4(b): residuals of the kept triplets, 8 columns at a time: T = A R_chunk
         float worst = 0.f;
         for (int j0 = 0; j0 < l; j0 += 8) {
             const int jn = min(8, l - j0);
-            mult_a(A, n1, n2, real, Z + (size_t)n2 * j0, T, jn);
+            mult_a(A, n1, n2, real, R + (size_t)n2 * j0, T, jn);
             if (tid < 8) s_res[tid] = 0.f;
             __syncthreads();
             for (int jj = 0; jj < jn; ++jj) {
@@ -394,7 +479,7 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
             for (int j = warp; j < l; j += kT / 32) {
                 float dr = 0.f, di = 0.f;
                 for (int c = lane; c < n2; c += 32) {
-                    const float2 rr = Z[c + (size_t)n2 * j], x = xv[c];
+                    const float2 rr = R[c + (size_t)n2 * j], x = xv[c];
                     dr = fmaf(rr.x, x.x, fmaf(rr.y, x.y, dr));
                     di = fmaf(rr.x, x.y, fmaf(-rr.y, x.x, di));
                 }
@@ -406,6 +491,7 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
             // y = A x - U coef
             for (int i = tid; i < n1; i += kT) {
                 float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
                 for (int c = 0; c < n2; ++c) {
                     const float2 a = ld_a(A, i + (int64_t)n1 * c, real), x = xv[c];
                     acc.x = fmaf(a.x, x.x, fmaf(-a.y, x.y, acc.x));
@@ -436,13 +522,14 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
             // x = A^H y - R coef
             for (int c = tid; c < n2; c += kT) {
                 float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
                 for (int i = 0; i < n1; ++i) {
                     const float2 a = ld_a(A, i + (int64_t)n1 * c, real), y = yv[i];
                     acc.x = fmaf(a.x, y.x, fmaf(a.y, y.y, acc.x));
                     acc.y = fmaf(a.x, y.y, fmaf(-a.y, y.x, acc.y));
                 }
                 for (int j = 0; j < l; ++j) {
-                    const float2 rr = Z[c + (size_t)n2 * j], d = coef[j];
+                    const float2 rr = R[c + (size_t)n2 * j], d = coef[j];
                     acc.x -= fmaf(rr.x, d.x, -rr.y * d.y);
                     acc.y -= fmaf(rr.x, d.y, rr.y * d.x);
                 }
@@ -470,7 +557,7 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
         for (int j = 0; j < l; ++j) {
             const float f = fac[j];
             if (f == 0.f) continue;
-            const float2 u = U[i + (size_t)n1 * j], rr = Z[c + (size_t)n2 * j];
+            const float2 u = U[i + (size_t)n1 * j], rr = R[c + (size_t)n2 * j];
             acc.x = fmaf(f, fmaf(u.x, rr.x, u.y * rr.y), acc.x);  // f u conj(r)
             acc.y = fmaf(f, fmaf(u.y, rr.x, -u.x * rr.y), acc.y);
         }
