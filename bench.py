@@ -62,6 +62,32 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's time: every rank's timed region ends at a barrier, the job's
+    time is the maximum."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(n: float, device) -> float:
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(n)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(units_all_ranks: float, steps: int, ms_max: float) -> float:
+    """Weak scaling: every rank processes its own batch; value = all ranks' units per step
+    times the steps, over the slowest rank's time."""
+    return units_all_ranks * steps / (ms_max / 1e3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -280,14 +306,11 @@ def time_prox(tp, args, Ys, Xs, taus, descs, method, world, barrier, device, clo
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop() if clocks else None
-    ms = t0.elapsed_time(t1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = max_over_ranks(t0.elapsed_time(t1), device)
     names = ["rfft", "proposer", "sketch_svt", "jacobi_svt", "irfft"]
     st = {n: sum(s_[j].elapsed_time(s_[j + 1]) for s_ in stage) / args.steps
           for j, n in enumerate(names)}
-    return {"ms": float(ms_t.item()), "stages": st, "sweeps": sweeps.cpu().numpy(), "clocks": clk,
+    return {"ms": ms, "stages": st, "sweeps": sweeps.cpu().numpy(), "clocks": clk,
             "flags": flags.cpu().numpy(), "widths": widths.cpu().numpy()}
 
 
@@ -319,7 +342,8 @@ def run_tp(args):
     X_plain = [X.clone() for X in Xs]
     jflops = jacobi_model_flops(shapes, plain["sweeps"])
     jt = plain["stages"]["jacobi_svt"]
-    plain_value = slices * world * args.steps / (plain["ms"] / 1e3)
+    slices_all = sum_over_ranks(slices, device)
+    plain_value = job_throughput(slices_all, args.steps, plain["ms"])
     plain_line = {"value": plain_value, "ms_per_step": plain["ms"] / args.steps,
                   "stages_ms": plain["stages"],
                   "roofline": {"kernel": "svd_kernel<SVD_PROX> (one-sided Jacobi + SVT)",
@@ -348,7 +372,7 @@ def run_tp(args):
         d = float(torch.linalg.vector_norm(Xl - Xp) / torch.linalg.vector_norm(Xp).clamp_min(1e-30))
         dev = max(dev, d)
     ms_max = learned["ms"]
-    value = slices * world * args.steps / (ms_max / 1e3)
+    value = job_throughput(slices_all, args.steps, ms_max)
     st = learned["stages"]
     sk_flops = sketch_model_flops(shapes, learned["widths"])
     sk_tflops = sk_flops / (st["sketch_svt"] / 1e3) / 1e12
@@ -434,13 +458,9 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
     t1.record()
     torch.cuda.synchronize()
     barrier()
-    ms = t0.elapsed_time(t1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=device)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = max_over_ranks(t0.elapsed_time(t1), device)
     nb = sum(4 * Y.numel() for Y in Ys)
-    return {"value": slices * world * args.steps / (float(ms_t.item()) / 1e3), "unit": UNIT,
+    return {"value": job_throughput(sum_over_ranks(slices, device), args.steps, ms), "unit": UNIT,
             "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
 
 
