@@ -11,6 +11,9 @@ with no blocking, fusion or symmetry trick beyond what the cited passage states:
 
 * the mode-3 DFT is the O(n3^2) sum of Eq. 2 over all n3 frequencies, with the
   DFT matrix of Eq. 1 built from the exact index reduction (k*t) mod n3;
+* the tensor inverse (Def. 2.4) is the first block column of bcirc(A)^-1, from Eq. 9 with
+  A * B = I; the t-QR (Thm. 2.4, no algorithm given) is read as Algorithm 2's construction
+  with a QR of each independent Fourier slice;
 * the t-product is Def. 2.1 / Eq. 9 literally, fold(bcirc(A) . unfold(B)); the
   Fourier-domain form of Eq. 10 (all n3 slices, no mirror) is kept for sizes
   where the bcirc matrix does not fit in memory;
@@ -44,7 +47,7 @@ __all__ = [
     "dft_matrix", "fft3", "ifft3", "circ", "bdiag", "bcirc", "unfold", "fold",
     "tprod", "tprod_fourier", "tprod_entries", "tran", "teye", "n_free_slices",
     "slice_svd", "tsvd", "tubal_singular_values", "tubalrank", "tnn", "tsn",
-    "prox_tnn", "slice_counts", "slice_singular_values",
+    "prox_tnn", "slice_counts", "slice_singular_values", "tinv", "tinv_fourier", "tqr",
 ]
 
 
@@ -302,3 +305,51 @@ def slice_counts(Y: np.ndarray, tau: float) -> np.ndarray:
     sv = slice_singular_values(np.asarray(Y, dtype=np.float64))
     h = n_free_slices(Y.shape[2])
     return np.sum(sv[:h] > tau, axis=1).astype(np.int64)
+
+
+# --------------------------------------------------------------------------- #
+# Def. 2.4  tensor inverse;  Thm. 2.4  t-QR                                    #
+# --------------------------------------------------------------------------- #
+def tinv(A: np.ndarray) -> np.ndarray:
+    """Def. 2.4: B with A * B = B * A = I.  By Eq. 9, A * B = I means
+    bcirc(A) unfold(B) = unfold(I) = [I; 0; ...; 0], so unfold(B) is the first block column
+    of bcirc(A)^-1 (the inverse of a block circulant matrix is block circulant)."""
+    n, n_, n3 = A.shape
+    if n != n_:
+        raise ValueError("tinv needs an n x n x n3 tensor")
+    Binv = np.linalg.inv(bcirc(np.asarray(A, dtype=np.float64)))
+    return fold(Binv[:, :n], n, n, n3)
+
+
+def tinv_fourier(A: np.ndarray) -> np.ndarray:
+    """The same inverse through Eq. 7: the inverse of every Fourier slice (all n3 slices),
+    then the inverse DFT (real part)."""
+    Ab = fft3(np.asarray(A, dtype=np.float64))
+    Bb = np.stack([np.linalg.inv(Ab[:, :, k]) for k in range(A.shape[2])], axis=2)
+    return ifft3(Bb).real
+
+
+def tqr(A: np.ndarray):
+    """Thm. 2.4: A = Q * R with Q (n1 x n1 x n3) orthogonal and R (n1 x n2 x n3) f-upper
+    triangular.  QR of the ceil((n3+1)/2) independent Fourier slices (real arithmetic on the
+    real slices), diag(Rbar^(k)) made real non-negative, conjugate mirrors for the other
+    slices, inverse DFT."""
+    n1, n2, n3 = A.shape
+    Ab = fft3(np.asarray(A, dtype=np.float64))
+    h = n_free_slices(n3)
+    Qb = np.zeros((n1, n1, n3), dtype=np.complex128)
+    Rb = np.zeros((n1, n2, n3), dtype=np.complex128)
+    for k in range(h):
+        M = Ab[:, :, k].real if _is_real_slice(k, n3) else Ab[:, :, k]
+        q, r = np.linalg.qr(M, mode="complete")
+        d = np.diagonal(r).copy()
+        ph = np.where(np.abs(d) > 0, d / np.where(np.abs(d) > 0, np.abs(d), 1), 1.0)
+        m = min(n1, n2)
+        q[:, :m] = q[:, :m] * ph[:m]
+        r[:m, :] = np.conj(ph[:m])[:, None] * r[:m, :]
+        Qb[:, :, k] = q
+        Rb[:, :, k] = r
+    for k in range(h, n3):
+        Qb[:, :, k] = np.conj(Qb[:, :, n3 - k])
+        Rb[:, :, k] = np.conj(Rb[:, :, n3 - k])
+    return ifft3(Qb).real, ifft3(Rb).real

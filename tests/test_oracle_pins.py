@@ -339,3 +339,47 @@ def test_prox_counts_on_gapped_input():
     c = O.slice_counts(Y, 0.1)
     assert c.shape == (3,) and np.all(c == 3)
     assert O.n_free_slices(16) == 9 and O.n_free_slices(5) == 3 and O.n_free_slices(1) == 1
+
+
+# ----------------------------------------------------------------------------- tinv / tqr
+@pytest.mark.parametrize("n,n3", [(1, 1), (3, 1), (4, 4), (5, 5), (6, 2), (3, 7)])
+def test_tinv_def24(n, n3):
+    A = _rand((n, n, n3), 10 * n + n3) + 2.0 * O.teye(n, n3)
+    B = O.tinv(A)
+    np.testing.assert_allclose(O.tprod(A, B), O.teye(n, n3), atol=1e-10)
+    np.testing.assert_allclose(O.tprod(B, A), O.teye(n, n3), atol=1e-10)
+    np.testing.assert_allclose(O.tinv_fourier(A), B, atol=1e-10)
+    if n3 == 1:
+        np.testing.assert_allclose(B[:, :, 0], np.linalg.inv(A[:, :, 0]), atol=1e-12)
+    np.testing.assert_allclose(O.tinv(O.teye(n, n3)), O.teye(n, n3), atol=1e-13)
+
+
+def test_tinv_rejects_non_square():
+    with pytest.raises(ValueError):
+        O.tinv(np.zeros((2, 3, 4)))
+
+
+@pytest.mark.parametrize("shape", [(4, 3, 1), (4, 3, 4), (3, 5, 5), (4, 4, 6), (6, 2, 7), (1, 3, 2)])
+def test_tqr_thm24(shape):
+    n1, n2, n3 = shape
+    A = _rand(shape, sum(shape) + 3)
+    Q, R = O.tqr(A)
+    assert Q.shape == (n1, n1, n3) and R.shape == (n1, n2, n3)
+    np.testing.assert_allclose(O.tprod(Q, R), A, atol=1e-11)                 # Eq. 22
+    np.testing.assert_allclose(O.tprod(O.tran(Q), Q), O.teye(n1, n3), atol=1e-11)
+    np.testing.assert_allclose(O.tprod(Q, O.tran(Q)), O.teye(n1, n3), atol=1e-11)
+    for k in range(n3):                                                      # f-upper triangular
+        assert np.max(np.abs(np.tril(R[:, :, k], -1))) < 1e-12
+    # every Fourier slice of R has a real non-negative diagonal (the normalisation)
+    Rb = O.fft3(R)
+    d = np.stack([np.diagonal(Rb[:, :, k]) for k in range(n3)])
+    assert np.max(np.abs(d.imag)) < 1e-10 and np.min(d.real) > -1e-10
+
+
+def test_tqr_n3_1_is_matrix_qr():
+    A = _rand((5, 3, 1), 4)
+    Q, R = O.tqr(A)
+    q, r = np.linalg.qr(A[:, :, 0], mode="complete")
+    s = np.sign(np.diagonal(r))
+    np.testing.assert_allclose(R[:3, :, 0], s[:, None] * r[:3], atol=1e-12)
+    np.testing.assert_allclose(Q[:, :3, 0], q[:, :3] * s, atol=1e-12)
