@@ -36,7 +36,8 @@
  *            launch error gives TP_ERR_CUDA. No call aborts, traps or prints.
  * Aliasing.  Inputs and outputs must not overlap, except in tp_prox_tnn, where
  *            X == Y (fully in place) is allowed.
- * Limits.    n3 <= TP_MAX_N3. For the SVD-based calls, max(n1, n2) <= TP_MAX_SVD_DIM.
+ * Limits.    n3 <= TP_MAX_N3. For the per-slice factorisations (SVD, inverse, QR),
+ *            max(n1, n2) <= TP_MAX_SVD_DIM.
  *            All counts fit in int64_t; a single tensor has fewer than 2^31 entries
  *            per frontal slice.
  */
@@ -59,7 +60,8 @@ typedef enum tp_status {
     TP_ERR_NO_MEMORY = 3,
     TP_ERR_CUDA = 4,
     TP_ERR_NOT_CONVERGED = 5, /* a Jacobi SVD hit max_sweeps; outputs are still written */
-    TP_ERR_UNSUPPORTED = 6
+    TP_ERR_UNSUPPORTED = 6,
+    TP_ERR_SINGULAR = 7 /* tp_tinv: a Fourier slice is singular to FP32 working precision */
 } tp_status;
 
 /* Arithmetic of the tprod slice GEMMs (Algorithm 1, step 2). */
@@ -182,6 +184,33 @@ tp_status tp_tubalrank(const float* A, int64_t* out, double* s_out, int64_t n1, 
  */
 tp_status tp_prox_tnn(const float* Y, float* X, int64_t n1, int64_t n2, int64_t n3,
                       double tau, const tp_options* opts, void* stream);
+
+/*
+ * Tensor inverse (Def. 2.4): B with A * B = B * A = I (Def. 2.3). By Eq. 10 the Fourier
+ * slices of B are the inverses of those of A, so each of the ceil((n3+1)/2) independent
+ * slices is inverted by Gauss-Jordan elimination with partial pivoting (FP32; real arithmetic
+ * on the real slices), and B is their inverse DFT with the mirror implied.
+ *   A, B: n x n x n3 (n1 == n2 == n, else TP_ERR_SHAPE); n <= TP_MAX_SVD_DIM.
+ * A slice whose pivot at some step is at most n * 2^-23 times the largest magnitude in that
+ * slice is singular: the whole of B is then NaN and, with opts->sync, the call returns
+ * TP_ERR_SINGULAR (asynchronous calls report nothing). B must not overlap A.
+ */
+tp_status tp_tinv(const float* A, float* B, int64_t n1, int64_t n2, int64_t n3,
+                  const tp_options* opts, void* stream);
+
+/*
+ * t-QR A = Q * R (Thm. 2.4): Q orthogonal (Def. 2.5), R f-upper triangular (every frontal
+ * slice upper triangular). The paper states the factorisation without an algorithm; it is
+ * computed as Algorithm 2 computes the t-SVD: a Householder QR of each independent Fourier
+ * slice (real arithmetic on the real slices), the mirrored slices implied, inverse DFT.
+ * Every Fourier slice of R has a real non-negative diagonal, so Q and R are unique where
+ * every slice has full rank (for the first min(n1, n2) columns of Q).
+ *   Full (opts->econ == 0): Q n1 x n1 x n3, R n1 x n2 x n3.
+ *   Economy (opts->econ == 1): Q n1 x r x n3, R r x n2 x n3, r = min(n1, n2).
+ * max(n1, n2) <= TP_MAX_SVD_DIM. Q and R must not overlap A or each other.
+ */
+tp_status tp_tqr(const float* A, float* Q, float* R, int64_t n1, int64_t n2, int64_t n3,
+                 const tp_options* opts, void* stream);
 
 /*
  * The rank proposer of TP_METHOD_LEARNED (not in the paper): an MLP 12 -> 64 -> 64 -> 1 (ReLU,

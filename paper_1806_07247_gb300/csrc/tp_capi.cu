@@ -160,6 +160,7 @@ tp_status finish(uint32_t* d_status, const Opts& o, cudaStream_t s) {
     uint32_t h = 0;
     if (d_status) TP_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
     TP_CUDA(cudaStreamSynchronize(s));
+    if (h & 2u) return TP_ERR_SINGULAR;
     return (h & 1u) ? TP_ERR_NOT_CONVERGED : TP_OK;
 }
 
@@ -513,6 +514,7 @@ const char* tp_status_string(tp_status status) {
         case TP_ERR_CUDA: return "TP_ERR_CUDA";
         case TP_ERR_NOT_CONVERGED: return "TP_ERR_NOT_CONVERGED";
         case TP_ERR_UNSUPPORTED: return "TP_ERR_UNSUPPORTED";
+        case TP_ERR_SINGULAR: return "TP_ERR_SINGULAR";
         default: return "TP_ERR_UNKNOWN";
     }
 }
@@ -653,6 +655,97 @@ tp_status tp_tsvd(const float* A, float* U, float* S, float* V, int64_t n1, int6
     TP_TRY(inv.launch(ws, true, s));
     TP_CUDA(launch_diag_scatter(tubes, (int)r, (int)n3, S, sS1, sS2, s));
     return finish(d_status, o, s);
+}
+
+tp_status tp_tinv(const float* A, float* B, int64_t n1, int64_t n2, int64_t n3,
+                  const tp_options* opts, void* stream) {
+    Opts o;
+    TP_TRY(resolve(opts, &o));
+    TP_TRY(check_dims(n1, n2, n3));
+    if (n1 != n2) return TP_ERR_SHAPE;
+    if (n1 > TP_MAX_SVD_DIM) return TP_ERR_UNSUPPORTED;
+    if (n1 == 0 || n3 == 0) return TP_OK;
+    if (!A || !B) return TP_ERR_INVALID_ARG;
+    TP_TRY(prepare());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int h = free_slices((int)n3);
+    const int64_t P = n1 * n1;
+    Workspace ws(s);
+    TP_TRY(ws.reserve(Workspace::round(4) + cbytes(P * h) + 2 * Workspace::round(sizeof(FftJob) * 2) +
+                      Workspace::round(sizeof(LaJob) * h)));
+    uint32_t* d_status = ws.take<uint32_t>(1);
+    TP_TRY(ws.check());
+    TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+    float2* spec = ws.take<float2>(P * h);
+    LaJob* d_jobs = ws.take<LaJob>(h);
+    TP_TRY(ws.check());
+    std::vector<LaJob> jobs(h);
+    for (int k = 0; k < h; ++k) {
+        jobs[k].A = jobs[k].R = spec + P * k;
+        jobs[k].n1 = jobs[k].n2 = (int)n1;
+    }
+    TP_TRY(upload(d_jobs, jobs, s));
+    TP_TRY(o.mark(0, s));
+    FftBatch fwd;
+    fwd.add(A, spec, P, (int)n3);
+    TP_TRY(fwd.launch(ws, false, s));
+    TP_TRY(o.marks(1, 3, s));
+    TP_CUDA(launch_tinv(d_jobs, h, (int)n1, d_status, s));
+    TP_TRY(o.mark(4, s));
+    FftBatch inv;
+    inv.add(B, spec, P, (int)n3);
+    TP_TRY(inv.launch(ws, true, s));
+    TP_TRY(o.mark(5, s));
+    return finish(d_status, o, s);
+}
+
+tp_status tp_tqr(const float* A, float* Q, float* R, int64_t n1, int64_t n2, int64_t n3,
+                 const tp_options* opts, void* stream) {
+    Opts o;
+    TP_TRY(resolve(opts, &o));
+    TP_TRY(check_dims(n1, n2, n3));
+    if (std::max(n1, n2) > TP_MAX_SVD_DIM) return TP_ERR_UNSUPPORTED;
+    if (n1 == 0 || n2 == 0 || n3 == 0) return TP_OK;
+    if (!A || !Q || !R) return TP_ERR_INVALID_ARG;
+    TP_TRY(prepare());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t m = std::min(n1, n2);
+    const int64_t qc = o.econ ? m : n1, rr = o.econ ? m : n1;
+    const int h = free_slices((int)n3);
+    const int64_t P = n1 * n2, PQ = n1 * qc, PR = rr * n2;
+    Workspace ws(s);
+    TP_TRY(ws.reserve(cbytes(P * h) + cbytes(PQ * h) + cbytes(PR * h) +
+                      Workspace::round(sizeof(FftJob) * 2) + Workspace::round(sizeof(FftJob) * 3) +
+                      Workspace::round(sizeof(LaJob) * h)));
+    float2* spec = ws.take<float2>(P * h);
+    float2* Qb = ws.take<float2>(PQ * h);
+    float2* Rb = ws.take<float2>(PR * h);
+    LaJob* d_jobs = ws.take<LaJob>(h);
+    TP_TRY(ws.check());
+    std::vector<LaJob> jobs(h);
+    for (int k = 0; k < h; ++k) {
+        jobs[k].A = spec + P * k;
+        jobs[k].Q = Qb + PQ * k;
+        jobs[k].R = Rb + PR * k;
+        jobs[k].n1 = (int)n1;
+        jobs[k].n2 = (int)n2;
+        jobs[k].qcols = (int)qc;
+        jobs[k].rrows = (int)rr;
+    }
+    TP_TRY(upload(d_jobs, jobs, s));
+    TP_TRY(o.mark(0, s));
+    FftBatch fwd;
+    fwd.add(A, spec, P, (int)n3);
+    TP_TRY(fwd.launch(ws, false, s));
+    TP_TRY(o.marks(1, 3, s));
+    TP_CUDA(launch_tqr(d_jobs, h, (int)n1, (int)n2, (int)qc, s));
+    TP_TRY(o.mark(4, s));
+    FftBatch inv;
+    inv.add(Q, Qb, PQ, (int)n3);
+    inv.add(R, Rb, PR, (int)n3);
+    TP_TRY(inv.launch(ws, true, s));
+    TP_TRY(o.mark(5, s));
+    return finish(nullptr, o, s);
 }
 
 static tp_status scalar_op(const float* A, double* out, int64_t n1, int64_t n2, int64_t n3,

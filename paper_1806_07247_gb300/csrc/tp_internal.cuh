@@ -158,6 +158,26 @@ size_t proposer_fit_scratch_floats(int n);
 // ---------------------------------------------------------------------------
 // Transpose (tp_tran.cu)
 // ---------------------------------------------------------------------------
+// Per-slice factorisations (tp_slice_la.cu): one CTA per independent Fourier slice.
+// ---------------------------------------------------------------------------
+struct LaJob {
+    float2* A = nullptr;  // slice (column-major, leading dimension n1); overwritten
+    float2* Q = nullptr;  // tqr: Q (n1 x qcols, leading dimension n1)
+    float2* R = nullptr;  // tqr: R (rrows x n2, leading dimension rrows); tinv: the inverse
+                          // (must equal A)
+    int32_t n1 = 0, n2 = 0, qcols = 0, rrows = 0;
+};
+
+// Shared memory one CTA may use; larger slices work in global memory.
+constexpr size_t kLaSmemLimit = 227 * 1024;
+
+// Inverse of every n x n slice (Def. 2.4); a singular slice is filled with NaN and sets bit 2
+// of *status.
+cudaError_t launch_tinv(const LaJob* d_jobs, int njobs, int n, uint32_t* status, cudaStream_t s);
+// QR of every n1 x n2 slice with the diagonal of R real and non-negative (Thm. 2.4).
+cudaError_t launch_tqr(const LaJob* d_jobs, int njobs, int n1, int n2, int qcols, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 cudaError_t launch_tran(const float* A, float* AT, int64_t n1, int64_t n2, int64_t n3,
                         cudaStream_t s);
 

@@ -22,6 +22,10 @@ low-rank-plus-noise tensors of its use case):
   tau = 2 * 0.05 * sqrt(n3) * (sqrt(n1) + sqrt(n2)) (twice the expected top
   singular value of one Fourier slice of the noise).
 * gemm(): A 2048x1024x64 and B 1024x1024x64 iid N(0,1).
+* shifted_square(): n x n x n3 with frontal slice 0 = I + G_0 and slices k > 0 = G_k,
+  G iid N(0, 1/(16 n n3)), so every Fourier slice is I plus a matrix of spectral norm
+  about 1/2 (condition number about 3): the inverse and QR workloads.
+* gaussian(): n1 x n2 x n3 iid N(0, 1) (tall shapes give well-conditioned QR slices).
 * trpca(): 240x320x100, tubal rank 10 factors iid N(0,1), 10% of positions
   (without replacement) corrupted by values uniform in [-5, 5],
   tau = 1 / sqrt(max(n1, n2) * n3).
@@ -33,7 +37,7 @@ from dataclasses import dataclass
 import numpy as np
 
 __all__ = ["normal", "small", "batched_specs", "batched_tensor", "gemm", "trpca",
-           "LowRankSpec"]
+           "LowRankSpec", "shifted_square", "gaussian"]
 
 
 def _rng(seed) -> np.random.Generator:
@@ -116,3 +120,16 @@ def trpca(seed: int = 0, n1: int = 240, n2: int = 320, n3: int = 100, r: int = 1
     val = rng.uniform(-amp, amp, size=pos.size).astype(np.float32)
     tau = 1.0 / np.sqrt(max(n1, n2) * n3)
     return {"P": P, "Q": Q, "pos": pos, "val": val, "tau": float(tau), "rank": r}
+
+
+def shifted_square(n: int, n3: int, seed: int = 0) -> np.ndarray:
+    """n x n x n3: iid N(0, 1/(16 n n3)) entries plus 1 on the diagonal of frontal slice 0."""
+    X = normal(_rng(seed), (n, n, n3), 1.0 / (4.0 * np.sqrt(n * max(n3, 1))))
+    if n > 0 and n3 > 0:
+        X[np.arange(n), np.arange(n), 0] += np.float32(1.0)
+    return X
+
+
+def gaussian(n1: int, n2: int, n3: int, seed: int = 0) -> np.ndarray:
+    """n1 x n2 x n3 iid N(0, 1)."""
+    return normal(_rng(seed), (n1, n2, n3))

@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtp.so")
 
 TP_OK, TP_ERR_INVALID_ARG, TP_ERR_SHAPE, TP_ERR_NO_MEMORY, TP_ERR_CUDA, \
-    TP_ERR_NOT_CONVERGED, TP_ERR_UNSUPPORTED = range(7)
+    TP_ERR_NOT_CONVERGED, TP_ERR_UNSUPPORTED, TP_ERR_SINGULAR = range(8)
 PRECISIONS = {"fp32": 0, "3xtf32": 1, "bf16x3": 2}
 MAX_N3 = 1024
 MAX_SVD_DIM = 512
@@ -77,6 +77,10 @@ _SIGS = {
     "tp_proposer_train": (ctypes.c_int, [ctypes.POINTER(TensorDesc), ctypes.c_int64, ctypes.c_int32,
                                          ctypes.c_double, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "tp_tinv": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int64] * 3 +
+                [ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_tqr": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 3 +
+               [ctypes.POINTER(Options), ctypes.c_void_p]),
     "tp_proposer_get": (ctypes.c_int, [ctypes.c_void_p]),
     "tp_proposer_set": (ctypes.c_int, [ctypes.c_void_p]),
 }
@@ -232,6 +236,31 @@ def tsvd(A: torch.Tensor, econ: bool = False, opts: Options | None = None, strea
     _check(lib().tp_tsvd(_ptr(A), _ptr(U), _ptr(S), _ptr(V), n1, n2, n3, ctypes.byref(o),
                          _stream(stream)), "tp_tsvd")
     return U, S, V
+
+
+def tinv(A: torch.Tensor, opts: Options | None = None, stream=None) -> torch.Tensor:
+    """Tensor inverse (Def. 2.4) of an n x n x n3 tensor; TpError(TP_ERR_SINGULAR) if a
+    Fourier slice is singular (synchronous calls)."""
+    A = _prep(A, "A")
+    n1, n2, n3 = A.shape
+    B = empty(n1, n2, n3, A.device)
+    o = opts or options()
+    _check(lib().tp_tinv(_ptr(A), _ptr(B), n1, n2, n3, ctypes.byref(o), _stream(stream)), "tp_tinv")
+    return B
+
+
+def tqr(A: torch.Tensor, econ: bool = False, opts: Options | None = None, stream=None):
+    """t-QR (Thm. 2.4); returns (Q, R)."""
+    A = _prep(A, "A")
+    n1, n2, n3 = A.shape
+    r = min(n1, n2)
+    Q = empty(n1, r if econ else n1, n3, A.device)
+    R = empty(r if econ else n1, n2, n3, A.device)
+    o = opts or options(econ=econ)
+    o.econ = int(bool(econ))
+    _check(lib().tp_tqr(_ptr(A), _ptr(Q), _ptr(R), n1, n2, n3, ctypes.byref(o), _stream(stream)),
+           "tp_tqr")
+    return Q, R
 
 
 def _scalar(fn, name, A, opts, stream, out):
