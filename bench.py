@@ -14,10 +14,14 @@ proposer is trained beforehand, untimed, on batches drawn with other seeds.
 The JSON line also carries:
   roofline      the dominant slice kernel of the step, timed live with CUDA events recorded
                 by the library at stage boundaries, against the FP32 ALU peak;
-  e2e           the same metric with pinned host inputs copied in and outputs copied back
-                inside the timed region;
+  e2e           the same metric through tp_prox_tnn_batched_host: page-locked host inputs
+                copied in and outputs copied back inside the timed region (overlapped by the
+                library chunk by chunk);
   tprod         t-product TFLOP/s on A 2048x1024x64 times B 1024x1024x64 in FP32,
                 BF16x3 and 3xTF32 slice-GEMM arithmetic;
+  factor        tensor inverse (Def. 2.4) on 128x128x302 and economy t-QR (Thm. 2.4) on
+                128x64x302 (152 independent slices each, one per SM), slices/s and the slice
+                kernel's FP32 flop rate;
   cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
 
 `--impl reference` times the FP64 oracle itself (host cores) on the same workload.
@@ -56,6 +60,7 @@ def parse():
     p.add_argument("--count", type=int, default=512)
     p.add_argument("--no-tprod", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-factor", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--train-batches", type=int, default=4,
                    help="512-tensor batches (other seeds) that label the proposer's training set")
@@ -417,6 +422,8 @@ def run_tp(args):
         line["e2e"] = e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device)
     if not args.no_tprod and rank == 0:
         line["tprod"] = tprod_leg(args, tp, synth, device)
+    if not args.no_factor and rank == 0:
+        line["factor"] = factor_leg(args, tp, synth, device)
     if rank == 0:
         rate, sl, nt, secs = oracle_sample(specs, rank, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(),
@@ -430,22 +437,20 @@ def run_tp(args):
 
 
 def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
-    """Pinned host input -> device, batched prox, device -> pinned host output, per step."""
+    """The same batch through the host-buffer entry point: every step copies the inputs from
+    page-locked host memory, runs the learned batched prox and copies the results back, the
+    library overlapping the copies with the kernels chunk by chunk."""
     import torch
-    hin = [torch.empty(Y.numel(), dtype=torch.float32, pin_memory=True) for Y in Ys]
-    hout = [torch.empty(Y.numel(), dtype=torch.float32, pin_memory=True) for Y in Ys]
+    shapes = [tuple(Y.shape) for Y in Ys]
+    _, hin = tp.pinned_tensors(shapes)
+    _, hout = tp.pinned_tensors(shapes)
     for h, Y in zip(hin, Ys):
-        h.copy_(Y.permute(2, 1, 0).reshape(-1).cpu())
-    flat_in = [Y.permute(2, 1, 0).reshape(-1) for Y in Ys]     # views of the device buffers
-    flat_out = [X.permute(2, 1, 0).reshape(-1) for X in Xs]
+        h.copy_(Y.cpu())
+    hdescs = tp.make_descs(hin, hout, taus)
     opts = tp.options(sync=False, method="learned")
 
     def step():
-        for d, h in zip(flat_in, hin):
-            d.copy_(h, non_blocking=True)
-        tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=opts, descs=descs)
-        for h, d in zip(hout, flat_out):
-            h.copy_(d, non_blocking=True)
+        tp.prox_tnn_batched_host(hin, taus, outs=hout, opts=opts, descs=hdescs)
 
     for _ in range(max(1, args.warmup)):
         step()
@@ -461,7 +466,9 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
     ms = max_over_ranks(t0.elapsed_time(t1), device)
     nb = sum(4 * Y.numel() for Y in Ys)
     return {"value": job_throughput(sum_over_ranks(slices, device), args.steps, ms), "unit": UNIT,
-            "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+            "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
+            "api": "tp_prox_tnn_batched_host (page-locked host tensors, chunked copy/compute "
+                   "overlap)"}
 
 
 BF16_PEAK_TFLOPS = 1944.2        # measured dense bf16 (MEASURED_PEAKS.json, burst)
@@ -514,6 +521,51 @@ def tprod_leg(args, tp, synth, device):
         out[prec] = {"tflops": flops / (ms / 1e3) / 1e12, "ms_per_call": ms,
                      "stages_ms": {"rfft": st[0], "gemm": st[1], "irfft": st[2]},
                      "gemm_useful_tflops": gemm_tflops, "gemm_roofline": roof}
+    return out
+
+
+def factor_leg(args, tp, synth, device):
+    """tinv on 128x128x302 and economy tqr on 128x64x302 (shifted-identity / N(0,1) inputs):
+    302 tubes give 152 independent Fourier slices, one CTA per SM.  Model flops per complex
+    slice: Gauss-Jordan 8 n^3; Householder QR plus the economy Q, 16 (n1 n2^2 - n2^3 / 3)
+    (half that on the two real slices is not credited)."""
+    import torch
+    out = {}
+    steps = max(3, min(args.steps, 10))
+    cases = {
+        "tinv": (synth.shifted_square(128, 302, 0), 8.0 * 128 ** 3,
+                 lambda A, o: tp.tinv(A, opts=o)),
+        "tqr": (synth.gaussian(128, 64, 302, 0), 16.0 * (128 * 64 ** 2 - 64 ** 3 / 3.0),
+                lambda A, o: tp.tqr(A, econ=True, opts=o)),
+    }
+    for name, (host, slice_flops, call) in cases.items():
+        A = tp.to_device(host, device)
+        n1, n2, n3 = host.shape
+        h = n3 // 2 + 1
+        for _ in range(3):
+            call(A, tp.options(sync=False, econ=(name == "tqr")))
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(tp.STAGE_EVENTS)]
+               for _ in range(steps)]
+        for s_ in evs:          # torch creates the CUDA event at its first record
+            for e in s_:
+                e.record()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for i in range(steps):
+            call(A, tp.options(sync=False, econ=(name == "tqr"), stage_events=evs[i]))
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / steps
+        seg = lambda a, b: sum(s_[a].elapsed_time(s_[b]) for s_ in evs) / steps
+        k_ms = seg(3, 4)
+        tflops = slice_flops * h / (k_ms / 1e3) / 1e12
+        out[name] = {"shape": [n1, n2, n3], "slices": h, "slices_per_s": h / (ms / 1e3),
+                     "ms_per_call": ms,
+                     "stages_ms": {"rfft": seg(0, 1), "slice_kernel": k_ms, "irfft": seg(4, 5)},
+                     "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
+                                  "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS}}
+        del A
     return out
 
 

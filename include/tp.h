@@ -247,6 +247,24 @@ typedef struct tp_tensor_desc {
 tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count,
                               const tp_options* opts, void* stream);
 
+/*
+ * tp_prox_tnn_batched on tensors in HOST memory: descs[t].in / .out are host pointers (in may
+ * equal out). The library copies the tensors to the device in chunks of about 1/8 of the
+ * data (16..256 MiB, cut at tensor boundaries), runs the batched prox on each chunk in place,
+ * and copies the results back, with the host-to-device copy of the next chunk and the
+ * device-to-host copy of the previous one overlapping the current chunk's kernels (two
+ * library-owned copy streams per device, ordered after and before `stream` by events). Runs
+ * of tensors that are contiguous in host memory move with one copy each. The host buffers
+ * should be page-locked (cudaHostAlloc / cudaHostRegister) for the copies to overlap;
+ * pageable memory works but serialises. Device memory: two chunk buffers plus the batched
+ * prox workspace of one chunk. With opts->sync == 0 the host buffers must stay valid and
+ * untouched until `stream` reaches the end of the call. stage_events [0] is recorded before
+ * the first copy and [1]..[5] after the last; sweeps_out and the other per-slice outputs
+ * are device arrays indexed as in tp_prox_tnn_batched. Arguments are validated as there.
+ */
+tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
+                                   const tp_options* opts, void* stream);
+
 tp_status tp_proposer_train(const tp_tensor_desc* descs, int64_t count, int32_t steps, double lr,
                             uint64_t seed, double* mse_out, void* stream);
 tp_status tp_proposer_get(float* host_params);

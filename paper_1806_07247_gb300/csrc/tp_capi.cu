@@ -267,8 +267,10 @@ struct ProxCapture {
     int64_t slices = 0;
 };
 
+// ext_status: a caller-owned (zeroed) status word shared by several calls; the call then
+// neither clears it nor reads it back.
 tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cudaStream_t s,
-                       ProxCapture* train = nullptr) {
+                       ProxCapture* train = nullptr, uint32_t* ext_status = nullptr) {
     const bool learned = (o.method == TP_METHOD_LEARNED) && !train;
     const bool need_feat = learned || train;
     size_t bytes = Workspace::round(sizeof(uint32_t));
@@ -304,7 +306,10 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     TP_TRY(ws.reserve(bytes));
     uint32_t* d_status = ws.take<uint32_t>(1);
     TP_TRY(ws.check());
-    TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+    if (ext_status)
+        d_status = ext_status;
+    else
+        TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
     float* feat = nullptr;
     int32_t *ell = nullptr, *flags = nullptr, *counts = nullptr, *d_order = nullptr;
     SvdJob* d_nat = nullptr;
@@ -481,6 +486,79 @@ tp_status sigma_op(const float* A, int64_t n1, int64_t n2, int64_t n3, int kind,
                                 s_out, s));
     TP_TRY(o.mark(5, s));
     return finish(d_status, o, s);
+}
+
+// Per-device streams for the host-buffer entry point's copies (created once, never destroyed).
+struct CopyStreams {
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+};
+std::mutex g_copy_mutex;
+CopyStreams g_copy[128];
+
+tp_status copy_streams(CopyStreams* out) {
+    int dev = 0;
+    TP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return TP_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_copy_mutex);
+    CopyStreams& c = g_copy[dev];
+    if (!c.h2d) TP_CUDA(cudaStreamCreateWithFlags(&c.h2d, cudaStreamNonBlocking));
+    if (!c.d2h) TP_CUDA(cudaStreamCreateWithFlags(&c.d2h, cudaStreamNonBlocking));
+    *out = c;
+    return TP_OK;
+}
+
+// Events of one host-buffer call, destroyed when it returns (the driver releases them once
+// the recorded work completes).
+struct CallEvents {
+    cudaEvent_t start = nullptr, h2d[2] = {}, comp[2] = {}, d2h[2] = {};
+    tp_status create() {
+        TP_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+        for (int b = 0; b < 2; ++b) {
+            TP_CUDA(cudaEventCreateWithFlags(&h2d[b], cudaEventDisableTiming));
+            TP_CUDA(cudaEventCreateWithFlags(&comp[b], cudaEventDisableTiming));
+            TP_CUDA(cudaEventCreateWithFlags(&d2h[b], cudaEventDisableTiming));
+        }
+        return TP_OK;
+    }
+    ~CallEvents() {
+        if (start) cudaEventDestroy(start);
+        for (int b = 0; b < 2; ++b) {
+            if (h2d[b]) cudaEventDestroy(h2d[b]);
+            if (comp[b]) cudaEventDestroy(comp[b]);
+            if (d2h[b]) cudaEventDestroy(d2h[b]);
+        }
+    }
+};
+
+// Copies [first, last) of a chunk between host and device, one cudaMemcpyAsync per run of
+// tensors that are contiguous on both sides.
+tp_status copy_runs(const tp_tensor_desc* d, const std::vector<int64_t>& bytes,
+                    const std::vector<char*>& dev, int64_t first, int64_t last, bool to_device,
+                    cudaStream_t st) {
+    int64_t t = first;
+    while (t < last) {
+        if (bytes[t] == 0) {
+            ++t;
+            continue;
+        }
+        const char* h0 = to_device ? static_cast<const char*>(static_cast<const void*>(d[t].in))
+                                   : static_cast<const char*>(static_cast<void*>(d[t].out));
+        char* dv0 = dev[t];
+        int64_t run = bytes[t], u = t + 1;
+        while (u < last && bytes[u] > 0) {
+            const char* hu = to_device ? static_cast<const char*>(static_cast<const void*>(d[u].in))
+                                       : static_cast<const char*>(static_cast<void*>(d[u].out));
+            if (hu != h0 + run || dev[u] != dv0 + run) break;
+            run += bytes[u];
+            ++u;
+        }
+        if (to_device)
+            TP_CUDA(cudaMemcpyAsync(dv0, h0, (size_t)run, cudaMemcpyHostToDevice, st));
+        else
+            TP_CUDA(cudaMemcpyAsync(const_cast<char*>(h0), dv0, (size_t)run, cudaMemcpyDeviceToHost, st));
+        t = u;
+    }
+    return TP_OK;
 }
 
 }  // namespace
@@ -869,6 +947,110 @@ tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count, const 
     TP_TRY(prepare());
     if (o.method == TP_METHOD_LEARNED && !proposer_ready()) return TP_ERR_INVALID_ARG;
     return prox_batched(descs, count, o, static_cast<cudaStream_t>(stream));
+}
+
+tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
+                                   const tp_options* opts, void* stream) {
+    Opts o;
+    TP_TRY(resolve(opts, &o));
+    TP_TRY(check_descs(descs, count));
+    for (int64_t t = 0; t < count; ++t)
+        if (descs[t].n1 > 0 && descs[t].n2 > 0 && descs[t].n3 > 0 && !descs[t].out)
+            return TP_ERR_INVALID_ARG;
+    if (count == 0) return TP_OK;
+    TP_TRY(prepare());
+    if (o.method == TP_METHOD_LEARNED && !proposer_ready()) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CopyStreams cs;
+    TP_TRY(copy_streams(&cs));
+
+    // chunks of about 1/8 of the data (16 MiB .. 256 MiB), cut at tensor boundaries
+    std::vector<int64_t> bytes(count), slices(count);
+    int64_t total = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        const tp_tensor_desc& d = descs[t];
+        const bool empty = d.n1 == 0 || d.n2 == 0 || d.n3 == 0;
+        bytes[t] = empty ? 0 : (int64_t)sizeof(float) * d.n1 * d.n2 * d.n3;
+        slices[t] = empty ? 0 : free_slices((int)d.n3);
+        total += bytes[t];
+    }
+    if (total == 0) return TP_OK;
+    const int64_t target = std::min<int64_t>(std::max<int64_t>(total / 8, 16 << 20), 256 << 20);
+    std::vector<int64_t> cut{0};
+    std::vector<int64_t> off(count, 0);  // device offset of each tensor inside its chunk's slab
+    int64_t slab = 0, acc = 0, cur = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        if (bytes[t] > 0) {
+            // keep the host pointer's alignment (mod 256) so that contiguous host tensors stay
+            // contiguous on the device and one copy moves a whole run
+            const bool follows = t > cut.back() && bytes[t - 1] > 0 &&
+                                 reinterpret_cast<const char*>(descs[t].in) ==
+                                     reinterpret_cast<const char*>(descs[t - 1].in) + bytes[t - 1];
+            const int64_t a = (int64_t)(reinterpret_cast<uintptr_t>(descs[t].in) & 255u);
+            off[t] = follows ? cur : ((cur + 255) & ~(int64_t)255) + a;
+            cur = off[t] + bytes[t];
+            acc += bytes[t];
+        }
+        if (acc >= target || t + 1 == count) {
+            slab = std::max(slab, cur);
+            cut.push_back(t + 1);
+            acc = 0;
+            cur = 0;
+        }
+    }
+    const int nchunks = (int)cut.size() - 1;
+    const int nbuf = nchunks > 1 ? 2 : 1;
+    const size_t slab_r = Workspace::round((size_t)slab + 256);
+    Workspace ws(s);
+    TP_TRY(ws.reserve(Workspace::round(4) + nbuf * slab_r));
+    uint32_t* d_status = ws.take<uint32_t>(1);
+    char* buf[2] = {nullptr, nullptr};
+    for (int b = 0; b < nbuf; ++b) buf[b] = ws.take<char>(slab_r);
+    TP_TRY(ws.check());
+    TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+    CallEvents ev;
+    TP_TRY(ev.create());
+    TP_TRY(o.mark(0, s));
+    TP_CUDA(cudaEventRecord(ev.start, s));
+    TP_CUDA(cudaStreamWaitEvent(cs.h2d, ev.start, 0));
+    TP_CUDA(cudaStreamWaitEvent(cs.d2h, ev.start, 0));
+
+    std::vector<char*> dev(count, nullptr);
+    std::vector<tp_tensor_desc> chunk;
+    int64_t slice_base = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        const int b = c & 1;
+        const int64_t first = cut[c], last = cut[c + 1];
+        for (int64_t t = first; t < last; ++t) dev[t] = buf[b] + off[t];
+        if (c >= 2) TP_CUDA(cudaStreamWaitEvent(cs.h2d, ev.d2h[b], 0));  // slab b is free again
+        TP_TRY(copy_runs(descs, bytes, dev, first, last, true, cs.h2d));
+        TP_CUDA(cudaEventRecord(ev.h2d[b], cs.h2d));
+        TP_CUDA(cudaStreamWaitEvent(s, ev.h2d[b], 0));
+        chunk.clear();
+        int64_t chunk_slices = 0;
+        for (int64_t t = first; t < last; ++t) {
+            tp_tensor_desc d = descs[t];
+            d.in = reinterpret_cast<const float*>(dev[t]);
+            d.out = reinterpret_cast<float*>(dev[t]);
+            chunk.push_back(d);
+            chunk_slices += slices[t];
+        }
+        Opts oc = o;
+        oc.sync = 0;
+        oc.events = nullptr;
+        oc.sweeps_out = o.sweeps_out ? o.sweeps_out + slice_base : nullptr;
+        oc.slice_flags_out = o.slice_flags_out ? o.slice_flags_out + slice_base : nullptr;
+        oc.sketch_width_out = o.sketch_width_out ? o.sketch_width_out + slice_base : nullptr;
+        TP_TRY(prox_batched(chunk.data(), (int64_t)chunk.size(), oc, s, nullptr, d_status));
+        slice_base += chunk_slices;
+        TP_CUDA(cudaEventRecord(ev.comp[b], s));
+        TP_CUDA(cudaStreamWaitEvent(cs.d2h, ev.comp[b], 0));
+        TP_TRY(copy_runs(descs, bytes, dev, first, last, false, cs.d2h));
+        TP_CUDA(cudaEventRecord(ev.d2h[b], cs.d2h));
+    }
+    for (int b = 0; b < nbuf; ++b) TP_CUDA(cudaStreamWaitEvent(s, ev.d2h[b], 0));
+    TP_TRY(o.marks(1, 5, s));
+    return finish(d_status, o, s);
 }
 
 }  // extern "C"

@@ -74,6 +74,8 @@ _SIGS = {
                                            ctypes.POINTER(Options), ctypes.c_void_p]),
     "tp_prox_tnn_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int64] * 3 +
                             [ctypes.c_double, ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_prox_tnn_batched_host": (ctypes.c_int, [ctypes.POINTER(TensorDesc), ctypes.c_int64,
+                                                ctypes.POINTER(Options), ctypes.c_void_p]),
     "tp_proposer_train": (ctypes.c_int, [ctypes.POINTER(TensorDesc), ctypes.c_int64, ctypes.c_int32,
                                          ctypes.c_double, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
@@ -341,6 +343,41 @@ def prox_tnn_batched(Ys, taus, outs=None, opts: Options | None = None, stream=No
     _check(lib().tp_prox_tnn_batched(d, len(Ys), ctypes.byref(o), _stream(stream)),
            "tp_prox_tnn_batched")
     return Xs
+
+
+def pinned_tensors(shapes):
+    """(slab, views): one page-locked host buffer holding column-major float32 tensors of the
+    given (n1, n2, n3) shapes back to back, and a view of each."""
+    total = sum(int(n1) * int(n2) * int(n3) for n1, n2, n3 in shapes)
+    slab = torch.empty(max(total, 1), dtype=torch.float32, pin_memory=True)
+    views, off = [], 0
+    for n1, n2, n3 in shapes:
+        n = int(n1) * int(n2) * int(n3)
+        views.append(slab[off:off + n].view(n3, n2, n1).permute(2, 1, 0))
+        off += n
+    return slab, views
+
+
+def _prep_host(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dim() != 3:
+        raise TypeError(f"{name} must be a 3-way host tensor")
+    if t.dtype == torch.float32 and is_colmajor(t):
+        return t
+    return t.to(torch.float32).permute(2, 1, 0).contiguous().permute(2, 1, 0)
+
+
+def prox_tnn_batched_host(Ys, taus, outs=None, opts: Options | None = None, stream=None,
+                          descs=None):
+    """prox_tnn over many HOST tensors (page-locked for overlap); the copies in and out and the
+    batched prox run inside the call, overlapped by chunks. Returns the host outputs."""
+    Ys = [_prep_host(Y, "Y") for Y in Ys]
+    if outs is None:
+        _, outs = pinned_tensors([tuple(Y.shape) for Y in Ys])
+    d = make_descs(Ys, outs, taus) if descs is None else descs
+    o = opts or options()
+    _check(lib().tp_prox_tnn_batched_host(d, len(Ys), ctypes.byref(o), _stream(stream)),
+           "tp_prox_tnn_batched_host")
+    return outs
 
 
 def proposer_train(Ys, taus, steps: int = 300, lr: float = 3e-3, seed: int = 0, stream=None) -> float:

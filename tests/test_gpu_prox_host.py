@@ -1,0 +1,97 @@
+"""GPU tests of tp_prox_tnn_batched_host: tensors in host memory, copied in and out by the
+library in overlapped chunks.  The results must match the device-memory batched call on the
+same tensors (the same kernels run on every slice) and the FP64 oracle within TOL_FP32."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import tproduct as O
+from tests.helpers import TOL_FP32, batched_inputs, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tp():
+    import os
+
+    from paper_1806_07247_gb300 import build, tp as _tp
+    if not os.path.exists(_tp.LIB_PATH):
+        build.build()
+    _tp.lib()
+    return _tp
+
+
+@pytest.fixture(scope="module")
+def batch():
+    # about 60 MB of tensors: several 16 MiB chunks
+    items = batched_inputs(60, seed=4)
+    return [Y for _, Y in items], [s.tau for s, _ in items]
+
+
+def _host_slab(tp, Ys):
+    slab, views = tp.pinned_tensors([Y.shape for Y in Ys])
+    for v, Y in zip(views, Ys):
+        v.copy_(torch.from_numpy(np.ascontiguousarray(Y.transpose(2, 1, 0))).permute(2, 1, 0))
+    return slab, views
+
+
+def _np(t):
+    return t.permute(2, 1, 0).contiguous().numpy().transpose(2, 1, 0)
+
+
+@pytest.mark.parametrize("method", ["jacobi", "learned"])
+def test_host_matches_device(tp, batch, method):
+    Ys, taus = batch
+    if method == "learned":
+        tp.proposer_train([tp.to_device(Y) for Y in Ys[:24]], taus[:24], steps=200, seed=1)
+    _, hin = _host_slab(tp, Ys)
+    houts = tp.prox_tnn_batched_host(hin, taus, opts=tp.options(method=method))
+    douts = tp.prox_tnn_batched([tp.to_device(Y) for Y in Ys], taus, opts=tp.options(method=method))
+    worst = max(rel(_np(h), tp.to_numpy(d)) for h, d in zip(houts, douts))
+    assert worst < 1e-6, worst
+    for i in (0, 17, 59):
+        assert rel(_np(houts[i]), O.prox_tnn(Ys[i].astype(np.float64), taus[i])) < \
+            (TOL_FP32 if method == "jacobi" else 1e-4)
+
+
+def test_host_layouts_and_aliasing(tp, batch):
+    """Separate (non-contiguous) pinned buffers, a pageable buffer, in == out, and an empty
+    tensor in the middle of the list."""
+    Ys, taus = batch
+    sel = [Y for Y in Ys[:5]]
+    ins = []
+    for i, Y in enumerate(sel):
+        t = torch.from_numpy(np.ascontiguousarray(Y.transpose(2, 1, 0))).permute(2, 1, 0)
+        ins.append(t.pin_memory() if i % 2 == 0 else t.clone())
+    empty = torch.zeros((0, 4, 3), dtype=torch.float32)
+    ins.insert(2, empty)
+    tau = [taus[0], taus[1], 0.1, taus[2], taus[3], taus[4]]
+    outs = [x for x in ins]          # fully in place
+    tp.prox_tnn_batched_host(ins, tau, outs=outs)
+    for k, Y in zip([0, 1, 3, 4, 5], sel):
+        i = k if k < 2 else k - 1
+        assert rel(_np(outs[k]), O.prox_tnn(Y.astype(np.float64), taus[i])) < TOL_FP32
+
+
+def test_host_sweeps_indexing(tp, batch):
+    """sweeps_out is indexed over the whole batch although the call runs in chunks."""
+    Ys, taus = batch
+    _, hin = _host_slab(tp, Ys)
+    slices = sum(Y.shape[2] // 2 + 1 for Y in Ys)
+    sw_h = torch.full((slices,), -1, dtype=torch.int32, device="cuda")
+    sw_d = torch.full((slices,), -1, dtype=torch.int32, device="cuda")
+    tp.prox_tnn_batched_host(hin, taus, opts=tp.options(sweeps_out=sw_h))
+    tp.prox_tnn_batched([tp.to_device(Y) for Y in Ys], taus, opts=tp.options(sweeps_out=sw_d))
+    assert torch.equal(sw_h, sw_d)
+    assert int(sw_h.min()) >= 1
+
+
+def test_host_rejects_bad_args(tp):
+    d = (tp.TensorDesc * 1)()
+    d[0].n1, d[0].n2, d[0].n3, d[0].tau = 4, 4, 4, 0.5
+    o = tp.options()
+    assert tp.lib().tp_prox_tnn_batched_host(d, 1, tp.ctypes.byref(o), None) == tp.TP_ERR_INVALID_ARG
+    d[0].n1 = -1
+    assert tp.lib().tp_prox_tnn_batched_host(d, 1, tp.ctypes.byref(o), None) == tp.TP_ERR_INVALID_ARG
+    assert tp.lib().tp_prox_tnn_batched_host(d, 0, tp.ctypes.byref(o), None) == tp.TP_OK
