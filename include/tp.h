@@ -249,18 +249,21 @@ tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count,
 
 /*
  * tp_prox_tnn_batched on tensors in HOST memory: descs[t].in / .out are host pointers (in may
- * equal out). The library copies the tensors to the device in chunks of about 1/8 of the
- * data (16..256 MiB, cut at tensor boundaries), runs the batched prox on each chunk in place,
- * and copies the results back, with the host-to-device copy of the next chunk and the
- * device-to-host copy of the previous one overlapping the current chunk's kernels (two
- * library-owned copy streams per device, ordered after and before `stream` by events). Runs
- * of tensors that are contiguous in host memory move with one copy each. The host buffers
- * should be page-locked (cudaHostAlloc / cudaHostRegister) for the copies to overlap;
- * pageable memory works but serialises. Device memory: two chunk buffers plus the batched
- * prox workspace of one chunk. With opts->sync == 0 the host buffers must stay valid and
- * untouched until `stream` reaches the end of the call. stage_events [0] is recorded before
- * the first copy and [1]..[5] after the last; sweeps_out and the other per-slice outputs
- * are device arrays indexed as in tp_prox_tnn_batched. Arguments are validated as there.
+ * equal out). The library copies the batch into one device buffer and runs the batched prox
+ * on it in place in up to 2 parts of at least 16 MiB each (cut at tensor boundaries). Each
+ * part is copied in, computed and copied back on its own: the copy in of part c+1 and the
+ * copy back of part c-1 overlap part c's kernels. Each part runs on its own library-owned
+ * compute stream, earlier parts at higher stream priority, so later parts' blocks fill the
+ * SMs that earlier parts leave idle. The copies use two more library-owned streams per
+ * device; all of it is ordered after earlier work on `stream` and before later work on it
+ * by events. Runs of tensors that are contiguous in host memory
+ * move with one copy each. The host buffers should be page-locked (cudaHostAlloc /
+ * cudaHostRegister) for the copies to overlap; pageable memory works but serialises. Device
+ * memory: the batch once plus the batched prox workspace of every part. With
+ * opts->sync == 0 the host buffers must stay valid and untouched until `stream` reaches the
+ * end of the call. stage_events [0] is recorded before the first copy and [1]..[5] after the
+ * last; sweeps_out and the other per-slice outputs are device arrays indexed as in
+ * tp_prox_tnn_batched. Arguments are validated as there.
  */
 tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
                                    const tp_options* opts, void* stream);

@@ -488,21 +488,33 @@ tp_status sigma_op(const float* A, int64_t n1, int64_t n2, int64_t n3, int kind,
     return finish(d_status, o, s);
 }
 
-// Per-device streams for the host-buffer entry point's copies (created once, never destroyed).
-struct CopyStreams {
-    cudaStream_t h2d = nullptr, d2h = nullptr;
+// Per-device streams of the host-buffer entry point (created once, never destroyed): the two
+// copy directions and one compute stream per part of the batch, part 0 at the highest stream
+// priority and each later part one level lower (as far as the device's range goes), so that
+// earlier parts finish first and their copies back overlap later parts' kernels, while the
+// later parts' blocks fill the SMs the earlier ones leave idle.
+constexpr int kHostParts = 2;
+struct SideStreams {
+    cudaStream_t h2d = nullptr, d2h = nullptr, comp[kHostParts] = {};
 };
-std::mutex g_copy_mutex;
-CopyStreams g_copy[128];
+std::mutex g_side_mutex;
+SideStreams g_side[128];
 
-tp_status copy_streams(CopyStreams* out) {
+tp_status side_streams(SideStreams* out) {
     int dev = 0;
     TP_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 128) return TP_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_copy_mutex);
-    CopyStreams& c = g_copy[dev];
+    std::lock_guard<std::mutex> lock(g_side_mutex);
+    SideStreams& c = g_side[dev];
     if (!c.h2d) TP_CUDA(cudaStreamCreateWithFlags(&c.h2d, cudaStreamNonBlocking));
     if (!c.d2h) TP_CUDA(cudaStreamCreateWithFlags(&c.d2h, cudaStreamNonBlocking));
+    if (!c.comp[0]) {
+        int least = 0, greatest = 0;
+        TP_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        for (int p = 0; p < kHostParts; ++p)
+            TP_CUDA(cudaStreamCreateWithPriority(&c.comp[p], cudaStreamNonBlocking,
+                                                 std::min(least, greatest + p)));
+    }
     *out = c;
     return TP_OK;
 }
@@ -510,23 +522,15 @@ tp_status copy_streams(CopyStreams* out) {
 // Events of one host-buffer call, destroyed when it returns (the driver releases them once
 // the recorded work completes).
 struct CallEvents {
-    cudaEvent_t start = nullptr, h2d[2] = {}, comp[2] = {}, d2h[2] = {};
-    tp_status create() {
-        TP_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-        for (int b = 0; b < 2; ++b) {
-            TP_CUDA(cudaEventCreateWithFlags(&h2d[b], cudaEventDisableTiming));
-            TP_CUDA(cudaEventCreateWithFlags(&comp[b], cudaEventDisableTiming));
-            TP_CUDA(cudaEventCreateWithFlags(&d2h[b], cudaEventDisableTiming));
-        }
+    std::vector<cudaEvent_t> ev;
+    tp_status create(size_t n) {
+        ev.assign(n, nullptr);
+        for (auto& e : ev) TP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         return TP_OK;
     }
     ~CallEvents() {
-        if (start) cudaEventDestroy(start);
-        for (int b = 0; b < 2; ++b) {
-            if (h2d[b]) cudaEventDestroy(h2d[b]);
-            if (comp[b]) cudaEventDestroy(comp[b]);
-            if (d2h[b]) cudaEventDestroy(d2h[b]);
-        }
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -961,10 +965,14 @@ tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
     TP_TRY(prepare());
     if (o.method == TP_METHOD_LEARNED && !proposer_ready()) return TP_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    CopyStreams cs;
-    TP_TRY(copy_streams(&cs));
+    SideStreams ss;
+    TP_TRY(side_streams(&ss));
 
-    // chunks of about 1/8 of the data (16 MiB .. 256 MiB), cut at tensor boundaries
+    // The batch is cut, at tensor boundaries, into up to kHostParts parts of at least 16 MiB.
+    // Part c runs on side compute stream c once its host-to-device copy has landed and is
+    // copied back as soon as its kernels are done: the copy of part c+1 and the copy back of
+    // part c-1 overlap part c's kernels.
+    constexpr int kParts = kHostParts;
     std::vector<int64_t> bytes(count), slices(count);
     int64_t total = 0;
     for (int64_t t = 0; t < count; ++t) {
@@ -975,15 +983,15 @@ tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
         total += bytes[t];
     }
     if (total == 0) return TP_OK;
-    const int64_t target = std::min<int64_t>(std::max<int64_t>(total / 8, 16 << 20), 256 << 20);
+    const int64_t target = std::max<int64_t>(total / kParts, 16 << 20);
     std::vector<int64_t> cut{0};
-    std::vector<int64_t> off(count, 0);  // device offset of each tensor inside its chunk's slab
-    int64_t slab = 0, acc = 0, cur = 0;
+    std::vector<int64_t> off(count, 0);  // device offset of each tensor in the batch buffer
+    int64_t acc = 0, cur = 0;
     for (int64_t t = 0; t < count; ++t) {
         if (bytes[t] > 0) {
-            // keep the host pointer's alignment (mod 256) so that contiguous host tensors stay
-            // contiguous on the device and one copy moves a whole run
-            const bool follows = t > cut.back() && bytes[t - 1] > 0 &&
+            // keep the host pointer's alignment (mod 256) so that tensors contiguous in host
+            // memory stay contiguous on the device and one copy moves a whole run
+            const bool follows = t > 0 && bytes[t - 1] > 0 &&
                                  reinterpret_cast<const char*>(descs[t].in) ==
                                      reinterpret_cast<const char*>(descs[t - 1].in) + bytes[t - 1];
             const int64_t a = (int64_t)(reinterpret_cast<uintptr_t>(descs[t].in) & 255u);
@@ -991,49 +999,46 @@ tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
             cur = off[t] + bytes[t];
             acc += bytes[t];
         }
-        if (acc >= target || t + 1 == count) {
-            slab = std::max(slab, cur);
+        if ((acc >= target && (int)cut.size() < kParts) || t + 1 == count) {
             cut.push_back(t + 1);
             acc = 0;
-            cur = 0;
         }
     }
-    const int nchunks = (int)cut.size() - 1;
-    const int nbuf = nchunks > 1 ? 2 : 1;
-    const size_t slab_r = Workspace::round((size_t)slab + 256);
+    const int nparts = (int)cut.size() - 1;
+    const size_t slab = Workspace::round((size_t)cur + 256);
     Workspace ws(s);
-    TP_TRY(ws.reserve(Workspace::round(4) + nbuf * slab_r));
+    TP_TRY(ws.reserve(Workspace::round(4) + slab));
     uint32_t* d_status = ws.take<uint32_t>(1);
-    char* buf[2] = {nullptr, nullptr};
-    for (int b = 0; b < nbuf; ++b) buf[b] = ws.take<char>(slab_r);
+    char* buf = ws.take<char>(slab);
     TP_TRY(ws.check());
     TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
-    CallEvents ev;
-    TP_TRY(ev.create());
+    CallEvents ce;  // [0] start, [1 + c] copied in, [1 + nparts + c] computed, [last] copied back
+    TP_TRY(ce.create(2 + 2 * (size_t)nparts));
+    cudaEvent_t ev_start = ce.ev[0], ev_back = ce.ev.back();
     TP_TRY(o.mark(0, s));
-    TP_CUDA(cudaEventRecord(ev.start, s));
-    TP_CUDA(cudaStreamWaitEvent(cs.h2d, ev.start, 0));
-    TP_CUDA(cudaStreamWaitEvent(cs.d2h, ev.start, 0));
+    TP_CUDA(cudaEventRecord(ev_start, s));
+    TP_CUDA(cudaStreamWaitEvent(ss.h2d, ev_start, 0));
+    TP_CUDA(cudaStreamWaitEvent(ss.d2h, ev_start, 0));
 
     std::vector<char*> dev(count, nullptr);
-    std::vector<tp_tensor_desc> chunk;
+    for (int64_t t = 0; t < count; ++t) dev[t] = buf + off[t];
+    std::vector<tp_tensor_desc> part;
     int64_t slice_base = 0;
-    for (int c = 0; c < nchunks; ++c) {
-        const int b = c & 1;
+    for (int c = 0; c < nparts; ++c) {
         const int64_t first = cut[c], last = cut[c + 1];
-        for (int64_t t = first; t < last; ++t) dev[t] = buf[b] + off[t];
-        if (c >= 2) TP_CUDA(cudaStreamWaitEvent(cs.h2d, ev.d2h[b], 0));  // slab b is free again
-        TP_TRY(copy_runs(descs, bytes, dev, first, last, true, cs.h2d));
-        TP_CUDA(cudaEventRecord(ev.h2d[b], cs.h2d));
-        TP_CUDA(cudaStreamWaitEvent(s, ev.h2d[b], 0));
-        chunk.clear();
-        int64_t chunk_slices = 0;
+        cudaStream_t cs = ss.comp[c];
+        cudaEvent_t ev_in = ce.ev[1 + c], ev_done = ce.ev[1 + nparts + c];
+        TP_TRY(copy_runs(descs, bytes, dev, first, last, true, ss.h2d));
+        TP_CUDA(cudaEventRecord(ev_in, ss.h2d));
+        TP_CUDA(cudaStreamWaitEvent(cs, ev_in, 0));  // ev_in follows ev_start
+        part.clear();
+        int64_t part_slices = 0;
         for (int64_t t = first; t < last; ++t) {
             tp_tensor_desc d = descs[t];
             d.in = reinterpret_cast<const float*>(dev[t]);
             d.out = reinterpret_cast<float*>(dev[t]);
-            chunk.push_back(d);
-            chunk_slices += slices[t];
+            part.push_back(d);
+            part_slices += slices[t];
         }
         Opts oc = o;
         oc.sync = 0;
@@ -1041,14 +1046,15 @@ tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
         oc.sweeps_out = o.sweeps_out ? o.sweeps_out + slice_base : nullptr;
         oc.slice_flags_out = o.slice_flags_out ? o.slice_flags_out + slice_base : nullptr;
         oc.sketch_width_out = o.sketch_width_out ? o.sketch_width_out + slice_base : nullptr;
-        TP_TRY(prox_batched(chunk.data(), (int64_t)chunk.size(), oc, s, nullptr, d_status));
-        slice_base += chunk_slices;
-        TP_CUDA(cudaEventRecord(ev.comp[b], s));
-        TP_CUDA(cudaStreamWaitEvent(cs.d2h, ev.comp[b], 0));
-        TP_TRY(copy_runs(descs, bytes, dev, first, last, false, cs.d2h));
-        TP_CUDA(cudaEventRecord(ev.d2h[b], cs.d2h));
+        TP_TRY(prox_batched(part.data(), (int64_t)part.size(), oc, cs, nullptr, d_status));
+        slice_base += part_slices;
+        TP_CUDA(cudaEventRecord(ev_done, cs));
+        TP_CUDA(cudaStreamWaitEvent(ss.d2h, ev_done, 0));
+        TP_TRY(copy_runs(descs, bytes, dev, first, last, false, ss.d2h));
     }
-    for (int b = 0; b < nbuf; ++b) TP_CUDA(cudaStreamWaitEvent(s, ev.d2h[b], 0));
+    // every part's kernels precede its copy back, so this one event covers all side streams
+    TP_CUDA(cudaEventRecord(ev_back, ss.d2h));
+    TP_CUDA(cudaStreamWaitEvent(s, ev_back, 0));
     TP_TRY(o.marks(1, 5, s));
     return finish(d_status, o, s);
 }
