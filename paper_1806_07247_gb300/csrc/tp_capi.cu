@@ -372,33 +372,35 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         TP_CUDA(launch_proposer(feat, d_nat, (int)slices, ell, s));
         TP_TRY(o.mark(2, s));
         // size classes by shared memory at sketch width 24 (a slice whose proposed width needs
-        // more than its class provides falls back): 4, 3, 2 and 1 CTAs per SM; slices beyond
-        // the last class get a launch without shared memory and fall back
+        // more than its class provides falls back): 4, 3, 2 and 1 CTAs of the sketch kernel
+        // per SM; slices beyond the last class get a launch without shared memory and fall
+        // back
         constexpr int kSizeL = 24;
-        const size_t caps[5] = {56 * 1024, 75 * 1024, 113 * 1024, 220 * 1024, 0};
-        std::vector<std::vector<int32_t>> cls(5);
+        constexpr int kClasses = 5;
+        const size_t caps[kClasses - 1] = {56 * 1024, 75 * 1024, 113 * 1024, 220 * 1024};
+        std::vector<std::vector<int32_t>> cls(kClasses);
         for (int64_t j = 0; j < slices; ++j) {
             const size_t need = sketch_smem_need(natural[j].n1, natural[j].n2, kSizeL);
-            int c = 4;
-            for (int q = 0; q < 4; ++q)
+            int c = kClasses - 1;
+            for (int q = 0; q < kClasses - 1; ++q)
                 if (need <= caps[q]) { c = q; break; }
             cls[c].push_back((int32_t)j);
         }
         std::vector<int32_t> order;
-        std::vector<size_t> start(5), smem(5, 0);
-        for (int c = 0; c < 5; ++c) {
+        std::vector<size_t> start(kClasses), smem(kClasses, 0);
+        for (int c = 0; c < kClasses; ++c) {
             std::stable_sort(cls[c].begin(), cls[c].end(), [&](int32_t a, int32_t b) {
                 return (int64_t)natural[a].n1 * natural[a].n2 > (int64_t)natural[b].n1 * natural[b].n2;
             });
             start[c] = order.size();
             for (int32_t j : cls[c]) {
                 order.push_back(j);
-                if (c < 4)
+                if (c < kClasses - 1)
                     smem[c] = std::max(smem[c], sketch_smem_need(natural[j].n1, natural[j].n2, kSizeL));
             }
         }
         TP_TRY(upload(d_order, order, s));
-        for (int c = 0; c < 5; ++c) {
+        for (int c = 0; c < kClasses; ++c) {
             if (cls[c].empty()) continue;
             SketchParams sp;
             sp.order = d_order + start[c];

@@ -137,9 +137,8 @@ struct SketchParams {
 
 __host__ __device__ inline size_t sketch_smem_need(int n1, int n2, int l) {
     const size_t nm = n1 > n2 ? n1 : n2;
-    return sizeof(float2) * (nm * l + (size_t)n1 * l + (size_t)n2 * l + (size_t)2 * l * l +
-                             (size_t)8 * n1 + n1 + n2 + 2 * kSketchMaxL) +
-           sizeof(float) * (2 * kSketchMaxL + 32) + 64;
+    return sizeof(float2) * (3 * nm * l + (size_t)3 * l * l + (size_t)n1 + n2 + 2 * kSketchMaxL) +
+           sizeof(float) * (2 * kSketchMaxL) + 64;
 }
 size_t features_smem_bytes(int n1, int n2);
 cudaError_t launch_features(const SvdJob* jobs, int njobs, int max_n1, int max_n2, float* feat,

@@ -9,8 +9,8 @@
 //   2. randomized range finder: Y = A Omega (Omega n2 x l, random +-1 / (+-1 +- i)/sqrt 2
 //      from a counter-based hash), q power iterations (Z = A^H Q, Y = A Z), each followed by
 //      shifted CholeskyQR3 orthonormalisation, Q = orth(Y);
-//   3. small SVD: Z = A^H Q (n2 x l) = B^H; one warp diagonalises the l x l Gram matrix
-//      Z^H Z = V diag(lambda) V^H by two-sided Jacobi; D = Z V, sigma_j = ||d_j||, so
+//   3. small SVD: Z = A^H Q (n2 x l) = B^H; one-sided Jacobi over the whole CTA turns Z into
+//      D = Z V with orthogonal columns, sigma_j = ||d_j||, so
 //      A ~ Q Z^H = (Q V) diag(sigma) (D / sigma)^H;
 //   4. acceptance: (a) the smallest of the l computed singular values is below tau (else the
 //      rank was underestimated); (b) every kept triplet (u, sigma, r) has
@@ -33,7 +33,8 @@ namespace tp {
 
 namespace {
 
-constexpr int kT = 256;  // threads per CTA
+constexpr int kT = 256;   // threads per CTA of the feature and training kernels
+constexpr int kTS = 256;  // threads per CTA of the sketch kernel
 constexpr int kLMax = kSketchMaxL;
 constexpr int kD = kProposerInputs;
 constexpr int kH = 64;
@@ -91,7 +92,7 @@ __device__ __forceinline__ float2 ld_a(const float2* A, int64_t idx, bool real) 
 __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, const float2* X,
                        float2* Y, int l) {
     const int nch = (l + 7) >> 3;
-    for (int t = threadIdx.x; t < n1 * nch; t += kT) {
+    for (int t = threadIdx.x; t < n1 * nch; t += (int)blockDim.x) {
         const int i = t % n1, j0 = (t / n1) * 8;
         const int jn = min(8, l - j0);
         float2 acc[8];
@@ -123,13 +124,13 @@ __device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real,
                         float2* Z, int l) {
     const int nch = (l + 7) >> 3;
     const int items = n2 * nch;
-    const int parts = max(1, min(kT / max(items, 1), 8));
+    const int parts = max(1, min((int)blockDim.x / max(items, 1), 8));
     const int span = (n1 + parts - 1) / parts;
     if (parts > 1) {
-        for (int t = threadIdx.x; t < n2 * l; t += kT) Z[t] = make_float2(0.f, 0.f);
+        for (int t = threadIdx.x; t < n2 * l; t += (int)blockDim.x) Z[t] = make_float2(0.f, 0.f);
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < items * parts; t += kT) {
+    for (int t = threadIdx.x; t < items * parts; t += (int)blockDim.x) {
         const int c = t % n2, rest = t / n2, ch = rest % nch, pr = rest / nch;
         const int j0 = ch * 8, jn = min(8, l - j0);
         const int i0 = pr * span, i1 = min(n1, i0 + span);
@@ -167,7 +168,7 @@ __device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real,
 
 // G (l x l, column-major, full Hermitian) = Y^H Y for Y n x l (ld n).
 __device__ void gram(const float2* Y, int n, int l, float2* G) {
-    for (int t = threadIdx.x; t < l * l; t += kT) {
+    for (int t = threadIdx.x; t < l * l; t += (int)blockDim.x) {
         const int a = t % l, b = t / l;
         if (a > b) continue;
         const float2* ya = Y + (size_t)n * a;
@@ -185,71 +186,72 @@ __device__ void gram(const float2* Y, int n, int l, float2* G) {
     __syncthreads();
 }
 
-// Cholesky factor of G + shift I by one warp: L (lower triangle of G, real positive
-// diagonal) overwrites the lower triangle.  Returns false on breakdown.
-__device__ bool cholesky_warp(float2* G, int l, float shift) {
-    const int lane = threadIdx.x & 31;
-    bool ok = true;
-    for (int k = 0; k < l; ++k) {
-        float d = 0.f;
-        if (lane == 0) {
-            d = G[k + l * k].x + shift;
-            for (int m = 0; m < k; ++m) {
-                const float2 v = G[k + l * m];
-                d -= fmaf(v.x, v.x, v.y * v.y);
-            }
-            d = (d > 0.f) ? sqrtf(d) : -1.f;
-            G[k + l * k] = make_float2(d, 0.f);
-        }
-        d = __shfl_sync(0xffffffffu, d, 0);
-        if (!(d > 0.f)) { ok = false; break; }
-        for (int i = k + 1 + lane; i < l; i += 32) {
-            float2 v = G[i + l * k];
-            for (int m = 0; m < k; ++m) {
-                const float2 a = G[i + l * m], b = G[k + l * m];  // a conj(b)
-                v.x -= fmaf(a.x, b.x, a.y * b.y);
-                v.y -= fmaf(a.y, b.x, -a.x * b.y);
-            }
-            const float inv = 1.f / d;
-            G[i + l * k] = make_float2(v.x * inv, v.y * inv);
-        }
-        __syncwarp();
+// C (l x l, upper triangular) with C^H (G + shift I) C = I, i.e. C = R^-1 for the Cholesky
+// factor R^H R = G + shift I: Gram-Schmidt of the unit vectors e_0..e_{l-1} in the
+// (G + shift I) inner product, each normalised vector projected out of all later ones at
+// once.  G is overwritten by M = (G + shift I) C, kept current column by column, so that
+// every step needs only dot products of length l: warp 0 normalises c_j (and m_j), then one
+// half-warp per later column k forms h = m_j^H c_k and updates c_k -= h c_j, m_k -= h m_j.
+// Returns false (uniformly) if a norm is not positive (breakdown).
+__device__ bool chol_inv(float2* G, float2* C, int l, float shift, int* s_flag) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int t = tid; t < l * l; t += kTS) {
+        const bool d = (t % l) == (t / l);
+        C[t] = make_float2(d ? 1.f : 0.f, 0.f);
+        if (d) G[t].x += shift;
     }
-    return ok;
-}
-
-// Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa): the l columns of
-// Y (n x l, ld n) are orthonormalised in place by three passes of Y <- Y R^-1 with R^H R the
-// Cholesky factorisation of the Gram matrix, the first pass shifted by
-// 11 (n l + l (l + 1)) u ||Y||_F^2 (u = 2^-24) so that it cannot break down.
-// Returns false if a pass still breaks down (the slice then goes to the Jacobi path).
-__device__ bool cholqr3(float2* Y, int n, int l, float2* G, int* s_flag) {
-    const int warp = threadIdx.x >> 5;
-    for (int pass = 0; pass < 3; ++pass) {
-        gram(Y, n, l, G);
+    __syncthreads();
+    const int hw = tid >> 4, hl = tid & 15;  // 16 half-warps; rows hl and hl + 16
+    for (int j = 0; j < l; ++j) {
         if (warp == 0) {
-            float shift = 0.f;
-            if (pass == 0) {
-                float tr = 0.f;
-                for (int j = 0; j < l; ++j) tr += G[j + l * j].x;
-                shift = 11.f * (float)(n * l + l * (l + 1)) * 5.9604645e-08f * tr;
-            }
-            const bool ok = cholesky_warp(G, l, shift);
-            if ((threadIdx.x & 31) == 0) *s_flag = ok ? 0 : 1;
+            const float2 cj = lane <= j ? C[lane + l * j] : make_float2(0.f, 0.f);
+            const float2 mj = lane < l ? G[lane + l * j] : make_float2(0.f, 0.f);
+            const float p = warp_sum(fmaf(cj.x, mj.x, cj.y * mj.y));  // c_j^H m_j (real)
+            const bool ok = p > 0.f;
+            const float inv = ok ? 1.f / sqrtf(p) : 0.f;
+            if (lane <= j) C[lane + l * j] = make_float2(cj.x * inv, cj.y * inv);
+            if (lane < l) G[lane + l * j] = make_float2(mj.x * inv, mj.y * inv);
+            if (lane == 0) *s_flag = ok ? 0 : 1;
         }
         __syncthreads();
         if (*s_flag) return false;
-        // Y <- Y L^-H, one row per thread, in place
-        for (int e = threadIdx.x; e < n; e += kT) {
-            for (int j = 0; j < l; ++j) {
-                float2 v = Y[e + (size_t)n * j];
-                for (int m = 0; m < j; ++m) {
-                    const float2 q = Y[e + (size_t)n * m], b = G[j + l * m];  // q conj(L_jm)
-                    v.x -= fmaf(q.x, b.x, q.y * b.y);
-                    v.y -= fmaf(q.y, b.x, -q.x * b.y);
+        for (int kb = j + 1; kb < l; kb += kTS / 16) {  // uniform over each warp
+            const int k = kb + hw;
+            const bool act = k < l;
+            float hr = 0.f, hi = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = hl + 16 * h;
+                if (act && m <= k) {
+                    const float2 mm = G[m + l * j], c = C[m + l * k];
+                    hr = fmaf(mm.x, c.x, fmaf(mm.y, c.y, hr));  // conj(m_j) c_k
+                    hi = fmaf(mm.x, c.y, fmaf(-mm.y, c.x, hi));
                 }
-                const float inv = 1.f / G[j + l * j].x;
-                Y[e + (size_t)n * j] = make_float2(v.x * inv, v.y * inv);
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                hr += __shfl_xor_sync(0xffffffffu, hr, o);
+                hi += __shfl_xor_sync(0xffffffffu, hi, o);
+            }
+            if (act) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int m = hl + 16 * h;
+                    if (m <= j) {
+                        const float2 cj = C[m + l * j];
+                        float2 c = C[m + l * k];
+                        c.x -= fmaf(hr, cj.x, -hi * cj.y);
+                        c.y -= fmaf(hr, cj.y, hi * cj.x);
+                        C[m + l * k] = c;
+                    }
+                    if (m < l) {
+                        const float2 mj = G[m + l * j];
+                        float2 mk = G[m + l * k];
+                        mk.x -= fmaf(hr, mj.x, -hi * mj.y);
+                        mk.y -= fmaf(hr, mj.y, hi * mj.x);
+                        G[m + l * k] = mk;
+                    }
+                }
             }
         }
         __syncthreads();
@@ -257,78 +259,205 @@ __device__ bool cholqr3(float2* Y, int n, int l, float2* G, int* s_flag) {
     return true;
 }
 
-// Eigen-decomposition G = V diag(lambda) V^H of the l x l Hermitian G by one warp: parallel
-// two-sided Jacobi (round-robin pairs, one group of 32/(pairs) lanes per pair; all row
-// rotations of a round, then all column rotations).  G is overwritten by diag(lambda) (up
-// to the tolerance); V (l x l) receives the eigenvectors.  Returns false without
-// convergence in 30 sweeps.
-__device__ bool eigh_warp(float2* G, float2* V, int l) {
-    const int lane = threadIdx.x & 31;
-    for (int t = lane; t < l * l; t += 32)
-        V[t] = make_float2((t % l) == (t / l) ? 1.f : 0.f, 0.f);
-    __syncwarp();
+// Yout (n x l) = Yin C for an upper triangular C (l x l); items of one row and 4 columns.
+__device__ void mult_upper(const float2* Yin, const float2* C, float2* Yout, int n, int l) {
+    const int nq = (l + 3) >> 2;
+    for (int t = threadIdx.x; t < n * nq; t += kTS) {
+        const int e = t % n, k0 = (t / n) * 4;
+        const int kn = min(4, l - k0);
+        float2 acc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+        for (int m = 0; m < k0 + kn; ++m) {
+            const float2 y = Yin[e + (size_t)n * m];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q < kn) {
+                    const float2 c = C[m + l * (k0 + q)];  // zero below the diagonal
+                    acc[q].x = fmaf(y.x, c.x, fmaf(-y.y, c.y, acc[q].x));
+                    acc[q].y = fmaf(y.x, c.y, fmaf(y.y, c.x, acc[q].y));
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < kn) Yout[e + (size_t)n * (k0 + q)] = acc[q];
+    }
+    __syncthreads();
+}
+
+// Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa): the l columns of
+// Y (n x l, ld n) are orthonormalised by three passes of Y <- Y R^-1 with R^H R the Cholesky
+// factorisation of the Gram matrix, the first pass shifted by 11 (n l + l (l + 1)) u ||Y||_F^2
+// (u = 2^-24) so that it cannot break down.  The passes alternate between Y and the scratch
+// S (both n x l); returns the buffer that holds the result, or nullptr if a pass still broke
+// down (the slice then goes to the Jacobi path).
+__device__ float2* orth3(float2* Y, float2* S, int n, int l, float2* G, float2* C, int* s_flag,
+                         int passes = 3) {
+    float2* cur = Y;
+    float2* oth = S;
+    for (int pass = 0; pass < passes; ++pass) {
+        gram(cur, n, l, G);
+        float shift = 0.f;
+        if (pass == 0) {
+            float tr = 0.f;
+            for (int j = 0; j < l; ++j) tr += G[j + l * j].x;
+            shift = 11.f * (float)(n * l + l * (l + 1)) * 5.9604645e-08f * tr;
+        }
+        if (!chol_inv(G, C, l, shift, s_flag)) return nullptr;
+        mult_upper(cur, C, oth, n, l);
+        float2* t = cur;
+        cur = oth;
+        oth = t;
+    }
+    return cur;
+}
+
+// Eigen-decomposition G = V diag(lambda) V^H of the l x l (l <= 32) Hermitian G by the whole
+// CTA: parallel two-sided Jacobi over the round-robin tournament.  Each round first forms the
+// rotations of its P pairs (one thread per pair), then applies all of them at once: every
+// 2 x 2 block of G (rows of pair i, columns of pair j) becomes J_i^H G_ij J_j and V <- V J.
+// Rows and columns of different pairs are disjoint, so the blocks are independent.  G ends
+// diagonal up to the tolerance.  `rot` (4 kLMax floats) and `pq` (kLMax ints) are scratch.
+// Returns false without convergence in 30 sweeps.
+__device__ bool eigh_cta(float2* G, float2* V, int l, float4* rot, int2* pq) {
+    const int tid = threadIdx.x;
+    for (int t = tid; t < l * l; t += kTS) V[t] = make_float2((t % l) == (t / l) ? 1.f : 0.f, 0.f);
+    __syncthreads();
     if (l < 2) return true;
-    const int Np = l + (l & 1), P = Np / 2, gs = 32 / P;
-    const int pi = lane / gs, sub = lane % gs;
+    const int Np = l + (l & 1), P = Np / 2;
     const float tol = 8.f * 1.1920928955078125e-07f, tol2 = tol * tol;
     for (int sweep = 0; sweep < 30; ++sweep) {
         int rotated = 0;
         for (int r = 0; r < Np - 1; ++r) {
-            int a = 0, b = 0;
-            if (pi == 0) { a = Np - 1; b = r; }
-            else { a = (r + pi) % (Np - 1); b = (r - pi + Np - 1) % (Np - 1); }
-            const bool act = pi < P && a < l && b < l;
-            const int p = act ? min(a, b) : 0, q = act ? max(a, b) : 0;
-            float c = 1.f, sr = 0.f, si = 0.f;
-            bool rot = false;
-            if (act) {
-                const float al = G[p + l * p].x, be = G[q + l * q].x;
-                const float2 g = G[p + l * q];
-                const float ag2 = fmaf(g.x, g.x, g.y * g.y);
-                rot = ag2 > (tol2 * fabsf(al)) * fabsf(be) && ag2 > 0.f;
-                if (rot) jacobi_rotation(al, be, g.x, g.y, ag2, c, sr, si);
+            if (tid < P) {
+                int a, b;
+                if (tid == 0) { a = Np - 1; b = r; }
+                else { a = (r + tid) % (Np - 1); b = (r - tid + Np - 1) % (Np - 1); }
+                const int p = min(a, b), q = max(a, b);  // q == l only for the odd-l dummy
+                float c = 1.f, sr = 0.f, si = 0.f, f = 0.f;
+                if (q < l) {
+                    const float al = G[p + l * p].x, be = G[q + l * q].x;
+                    const float2 g = G[p + l * q];
+                    const float ag2 = fmaf(g.x, g.x, g.y * g.y);
+                    if (ag2 > (tol2 * fabsf(al)) * fabsf(be) && ag2 > 0.f) {
+                        jacobi_rotation(al, be, g.x, g.y, ag2, c, sr, si);
+                        f = 1.f;
+                        rotated = 1;
+                    }
+                }
+                rot[tid] = make_float4(c, sr, si, f);
+                pq[tid] = make_int2(p, q < l ? q : -1);
             }
-            rotated |= rot;
-            __syncwarp();
-            // rows p, q: G_pk <- c G_pk - s e G_qk, G_qk <- s conj(e) G_pk + c G_qk
-            if (rot) {
-                for (int k = sub; k < l; k += gs) {
-                    const float2 x = G[p + l * k], y = G[q + l * k];
-                    G[p + l * k] = make_float2(fmaf(c, x.x, -fmaf(sr, y.x, -si * y.y)),
-                                               fmaf(c, x.y, -fmaf(sr, y.y, si * y.x)));
-                    G[q + l * k] = make_float2(fmaf(sr, x.x, fmaf(si, x.y, c * y.x)),
-                                               fmaf(sr, x.y, fmaf(-si, x.x, c * y.y)));
+            __syncthreads();
+            for (int t = tid; t < P * P + l * P; t += kTS) {
+                if (t < P * P) {
+                    const int i = t % P, j = t / P;
+                    const float4 ri = rot[i], rj = rot[j];
+                    if (ri.w == 0.f && rj.w == 0.f) continue;
+                    const int2 a = pq[i], b = pq[j];
+                    // block [[x0, x1], [y0, y1]]: rows (a.x, a.y), columns (b.x, b.y)
+                    const float2 z = make_float2(0.f, 0.f);
+                    float2 x0 = G[a.x + l * b.x];
+                    float2 x1 = b.y >= 0 ? G[a.x + l * b.y] : z;
+                    float2 y0 = a.y >= 0 ? G[a.y + l * b.x] : z;
+                    float2 y1 = (a.y >= 0 && b.y >= 0) ? G[a.y + l * b.y] : z;
+                    // rows: g_p <- c g_p - w g_q, g_q <- conj(w) g_p + c g_q   (w = sr + i si)
+                    const float c = ri.x, sr = ri.y, si = ri.z;
+                    float2 n0 = make_float2(fmaf(c, x0.x, -fmaf(sr, y0.x, -si * y0.y)),
+                                            fmaf(c, x0.y, -fmaf(sr, y0.y, si * y0.x)));
+                    float2 m0 = make_float2(fmaf(sr, x0.x, fmaf(si, x0.y, c * y0.x)),
+                                            fmaf(sr, x0.y, fmaf(-si, x0.x, c * y0.y)));
+                    float2 n1 = make_float2(fmaf(c, x1.x, -fmaf(sr, y1.x, -si * y1.y)),
+                                            fmaf(c, x1.y, -fmaf(sr, y1.y, si * y1.x)));
+                    float2 m1 = make_float2(fmaf(sr, x1.x, fmaf(si, x1.y, c * y1.x)),
+                                            fmaf(sr, x1.y, fmaf(-si, x1.x, c * y1.y)));
+                    // columns: g_p <- c g_p - conj(w) g_q, g_q <- w g_p + c g_q
+                    const float d = rj.x, tr = rj.y, ti = rj.z;
+                    x0 = make_float2(fmaf(d, n0.x, fmaf(-tr, n1.x, -ti * n1.y)),
+                                     fmaf(d, n0.y, fmaf(-tr, n1.y, ti * n1.x)));
+                    x1 = make_float2(fmaf(tr, n0.x, fmaf(-ti, n0.y, d * n1.x)),
+                                     fmaf(tr, n0.y, fmaf(ti, n0.x, d * n1.y)));
+                    y0 = make_float2(fmaf(d, m0.x, fmaf(-tr, m1.x, -ti * m1.y)),
+                                     fmaf(d, m0.y, fmaf(-tr, m1.y, ti * m1.x)));
+                    y1 = make_float2(fmaf(tr, m0.x, fmaf(-ti, m0.y, d * m1.x)),
+                                     fmaf(tr, m0.y, fmaf(ti, m0.x, d * m1.y)));
+                    G[a.x + l * b.x] = x0;
+                    if (b.y >= 0) G[a.x + l * b.y] = x1;
+                    if (a.y >= 0) G[a.y + l * b.x] = y0;
+                    if (a.y >= 0 && b.y >= 0) G[a.y + l * b.y] = y1;
+                } else {
+                    const int u = t - P * P, k = u % l, j = u / l;
+                    const float4 rj = rot[j];
+                    if (rj.w == 0.f) continue;
+                    const int2 b = pq[j];
+                    const float d = rj.x, tr = rj.y, ti = rj.z;
+                    const float2 x = V[k + l * b.x], y = V[k + l * b.y];
+                    V[k + l * b.x] = make_float2(fmaf(d, x.x, fmaf(-tr, y.x, -ti * y.y)),
+                                                 fmaf(d, x.y, fmaf(-tr, y.y, ti * y.x)));
+                    V[k + l * b.y] = make_float2(fmaf(tr, x.x, fmaf(-ti, x.y, d * y.x)),
+                                                 fmaf(tr, x.y, fmaf(ti, x.x, d * y.y)));
                 }
             }
-            __syncwarp();
-            // columns p, q of G and V: [x, y] <- [c x - s conj(e) y, s e x + c y]
-            if (rot) {
-                for (int k = sub; k < l; k += gs) {
-                    float2 x = G[k + l * p], y = G[k + l * q];
-                    G[k + l * p] = make_float2(fmaf(c, x.x, fmaf(-sr, y.x, -si * y.y)),
-                                               fmaf(c, x.y, fmaf(-sr, y.y, si * y.x)));
-                    G[k + l * q] = make_float2(fmaf(sr, x.x, fmaf(-si, x.y, c * y.x)),
-                                               fmaf(sr, x.y, fmaf(si, x.x, c * y.y)));
-                    x = V[k + l * p];
-                    y = V[k + l * q];
-                    V[k + l * p] = make_float2(fmaf(c, x.x, fmaf(-sr, y.x, -si * y.y)),
-                                               fmaf(c, x.y, fmaf(-sr, y.y, si * y.x)));
-                    V[k + l * q] = make_float2(fmaf(sr, x.x, fmaf(-si, x.y, c * y.x)),
-                                               fmaf(sr, x.y, fmaf(si, x.x, c * y.y)));
-                }
-            }
-            __syncwarp();
+            __syncthreads();
         }
-        if (!__any_sync(0xffffffffu, rotated)) return true;
+        if (!__syncthreads_or(rotated)) return true;
     }
     return false;
 }
 
-__global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
+// y (n1) = A x (x: n2, shared); partial sums over column ranges meet through shared atomics.
+__device__ void matvec_a(const float2* __restrict__ A, int n1, int n2, bool real, const float2* x,
+                         float2* y) {
+    const int parts = max(1, min(kTS / n1, 8));
+    const int span = (n2 + parts - 1) / parts;
+    for (int i = threadIdx.x; i < n1; i += kTS) y[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n1 * parts; t += kTS) {
+        const int i = t % n1, pr = t / n1;
+        const int c0 = pr * span, c1 = min(n2, c0 + span);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int c = c0; c < c1; ++c) {
+            const float2 a = ld_a(A, i + (int64_t)n1 * c, real), v = x[c];
+            acc.x = fmaf(a.x, v.x, fmaf(-a.y, v.y, acc.x));
+            acc.y = fmaf(a.x, v.y, fmaf(a.y, v.x, acc.y));
+        }
+        if (parts == 1) {
+            y[i] = acc;
+        } else {
+            atomicAdd(&y[i].x, acc.x);
+            atomicAdd(&y[i].y, acc.y);
+        }
+    }
+    __syncthreads();
+}
+
+// x (n2) = A^H y (y: n1, shared); one warp per column of A (coalesced), lanes over its rows.
+__device__ void matvec_ah(const float2* __restrict__ A, int n1, int n2, bool real, const float2* y,
+                          float2* x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = warp; c < n2; c += kTS / 32) {
+        float dr = 0.f, di = 0.f;
+        for (int i = lane; i < n1; i += 32) {
+            const float2 a = ld_a(A, i + (int64_t)n1 * c, real), v = y[i];
+            dr = fmaf(a.x, v.x, fmaf(a.y, v.y, dr));  // conj(a) v
+            di = fmaf(a.x, v.y, fmaf(-a.y, v.x, di));
+        }
+        dr = warp_sum(dr);
+        di = warp_sum(di);
+        if (lane == 0) x[c] = make_float2(dr, di);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kTS, 3) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
                                                            SketchParams P) {
     extern __shared__ float4 smem4[];
-    __shared__ int s_flag, s_eig;
-    __shared__ float s_res[8];
+    __shared__ int s_flag;
+    __shared__ float s_worst[kTS / 32];
+    __shared__ float4 s_rot[kLMax / 2];
+    __shared__ int2 s_pq[kLMax / 2];
     const int job = P.order ? P.order[blockIdx.x] : (int)blockIdx.x;
     const SvdJob J = jobs[job];
     const int n1 = J.n1, n2 = J.n2, nm = max(n1, n2);
@@ -340,73 +469,72 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
         if (tid == 0) P.flag[job] = 1;
         return;
     }
-    float2* Q = reinterpret_cast<float2*>(smem4);  // max(n1, n2) x l: Q (n1 x l), later R (n2 x l)
-    float2* U = Q + (size_t)nm * l;                 // n1 x l
-    float2* Z = U + (size_t)n1 * l;                 // n2 x l: Omega, then B^H
-    float2* V = Z + (size_t)n2 * l;                 // l x l
+    float2* B0 = reinterpret_cast<float2*>(smem4);  // three max(n1, n2) x l buffers
+    float2* B1 = B0 + (size_t)nm * l;
+    float2* B2 = B1 + (size_t)nm * l;
+    float2* V = B2 + (size_t)nm * l;                // l x l
     float2* G = V + (size_t)l * l;                  // l x l
-    float2* T = G + (size_t)l * l;                  // n1 x 8
-    float2* xv = T + (size_t)n1 * 8;                // n2
+    float2* C = G + (size_t)l * l;                  // l x l
+    float2* xv = C + (size_t)l * l;                 // n2
     float2* yv = xv + n2;                           // n1
     float2* coef = yv + n1;                         // 2 kLMax
     float* sig = reinterpret_cast<float*>(coef + 2 * kLMax);
     float* fac = sig + kLMax;
-    float* red = fac + kLMax;
     const float2* A = J.A;
 
-    // 2. range finder with power iterations; shifted CholeskyQR3 orthonormalisations
-    for (int t = tid; t < n2 * l; t += kT) Z[t] = omega(P.seed, job, t % n2, t / n2, real);
+    // 2. range finder with power iterations; shifted CholeskyQR3 orthonormalisations.  bq holds
+    // the current Q (n1 x l), bz the current Z (n2 x l), bs is scratch.
+    float2* bq = B0;
+    float2* bz = B1;
+    float2* bs = B2;
+    for (int t = tid; t < n2 * l; t += kTS) bs[t] = omega(P.seed, job, t % n2, t / n2, real);
     __syncthreads();
-    mult_a(A, n1, n2, real, Z, Q, l);
+    mult_a(A, n1, n2, real, bs, bq, l);
     __syncthreads();
-    bool ok = cholqr3(Q, n1, l, G, &s_flag);
+    float2* r = orth3(bq, bs, n1, l, G, C, &s_flag, P.power_iters > 0 ? 2 : 3);
+    bool ok = r != nullptr;
+    if (ok && r != bq) { bs = bq; bq = r; }
     for (int it = 0; ok && it < P.power_iters; ++it) {
-        mult_ah(A, n1, n2, real, Q, Z, l);
-        ok = cholqr3(Z, n2, l, G, &s_flag);
+        mult_ah(A, n1, n2, real, bq, bz, l);
+        r = orth3(bz, bs, n2, l, G, C, &s_flag, 2);
+        ok = r != nullptr;
         if (!ok) break;
-        mult_a(A, n1, n2, real, Z, Q, l);
+        if (r != bz) { bs = bz; bz = r; }
+        mult_a(A, n1, n2, real, bz, bq, l);
         __syncthreads();
-        ok = cholqr3(Q, n1, l, G, &s_flag);
+        r = orth3(bq, bs, n1, l, G, C, &s_flag);
+        ok = r != nullptr;
+        if (ok && r != bq) { bs = bq; bq = r; }
     }
+    // 3. Z = A^H Q = B^H; one-sided Jacobi Z V = D with orthogonal columns, sigma_j = ||d_j||,
+    // so A ~ Q Z^H = (Q V) diag(sigma) (D / sigma)^H
     if (ok) {
-        mult_ah(A, n1, n2, real, Q, Z, l);  // Z = A^H Q = B^H
-        // 3. B B^H = Z^H Z = V diag(lambda) V^H by one warp
-        gram(Z, n2, l, G);
-        if (warp == 0) {
-            const bool conv = eigh_warp(G, V, l);
-            if (lane == 0) s_eig = conv ? 1 : 0;
+        mult_ah(A, n1, n2, real, bq, bz, l);
+        gram(bz, n2, l, G);
+        ok = eigh_cta(G, V, l, s_rot, s_pq);
+    }
+    if (ok) {  // D = Z V over Z, by rows (a warp per row, lanes over columns)
+        for (int e = warp; e < n2; e += kTS / 32) {
+            float2 acc = make_float2(0.f, 0.f);
+            if (lane < l) {
+                for (int m = 0; m < l; ++m) {
+                    const float2 z = bz[e + (size_t)n2 * m], v = V[m + (size_t)l * lane];
+                    acc.x = fmaf(z.x, v.x, fmaf(-z.y, v.y, acc.x));
+                    acc.y = fmaf(z.x, v.y, fmaf(z.y, v.x, acc.y));
+                }
+            }
+            __syncwarp();
+            if (lane < l) bz[e + (size_t)n2 * lane] = acc;
         }
         __syncthreads();
-        ok = s_eig != 0;
     }
     float smin = 3.4e38f, smax = 0.f;
     int k = 0;
+    float2* U = bs;  // n1 x l
+    float2* R = bz;  // n2 x l: D, then D / sigma on the kept columns
+    float2* T = bq;  // n1 x l: A R for the residuals (Q is dead once U is formed)
     if (ok) {
-        // U = Q V (n1 x l); then D = Z V over Q (Q no longer needed), sigma_j = ||d_j||
-        for (int t = tid; t < n1 * l; t += kT) {
-            const int i = t % n1, j = t / n1;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int m = 0; m < l; ++m) {
-                const float2 q = Q[i + (size_t)n1 * m], v = V[m + (size_t)l * j];
-                acc.x = fmaf(q.x, v.x, fmaf(-q.y, v.y, acc.x));
-                acc.y = fmaf(q.x, v.y, fmaf(q.y, v.x, acc.y));
-            }
-            U[t] = acc;
-        }
-        __syncthreads();
-        float2* R = Q;
-        for (int t = tid; t < n2 * l; t += kT) {
-            const int c = t % n2, j = t / n2;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int m = 0; m < l; ++m) {
-                const float2 z = Z[c + (size_t)n2 * m], v = V[m + (size_t)l * j];
-                acc.x = fmaf(z.x, v.x, fmaf(-z.y, v.y, acc.x));
-                acc.y = fmaf(z.x, v.y, fmaf(z.y, v.x, acc.y));
-            }
-            R[t] = acc;
-        }
-        __syncthreads();
-        for (int j = warp; j < l; j += kT / 32) {
+        for (int j = warp; j < l; j += kTS / 32) {
             float sacc = 0.f;
             for (int e = lane; e < n2; e += 32) {
                 const float2 d = R[e + (size_t)n2 * j];
@@ -414,6 +542,17 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
             }
             sacc = warp_sum(sacc);
             if (lane == 0) sig[j] = sqrtf(sacc);
+        }
+        // U = Q V
+        for (int t = tid; t < n1 * l; t += kTS) {
+            const int i = t % n1, j = t / n1;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int m = 0; m < l; ++m) {
+                const float2 q = bq[i + (size_t)n1 * m], v = V[m + (size_t)l * j];
+                acc.x = fmaf(q.x, v.x, fmaf(-q.y, v.y, acc.x));
+                acc.y = fmaf(q.x, v.y, fmaf(q.y, v.x, acc.y));
+            }
+            U[t] = acc;
         }
         __syncthreads();
         // 4(a): the sketch must reach below tau; the kept set is decided in FP64
@@ -424,59 +563,52 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
         }
         ok = !((double)smin > J.tau);
     }
-    float2* R = Q;
     if (ok) {
-        for (int j = tid; j < l; j += kT) fac[j] = ((double)sig[j] > J.tau) ? 1.f / sig[j] : 0.f;
+        for (int j = tid; j < l; j += kTS) fac[j] = ((double)sig[j] > J.tau) ? 1.f / sig[j] : 0.f;
         __syncthreads();
-        for (int t = tid; t < n2 * l; t += kT) {
+        for (int t = tid; t < n2 * l; t += kTS) {
             const float f = fac[t / n2];
             R[t].x *= f;
             R[t].y *= f;
         }
         __syncthreads();
-        // 4(b): residuals of the kept triplets, 8 columns at a time: T = A R_chunk
+        // 4(b): residuals of the kept triplets, T = A R in one pass
+        mult_a(A, n1, n2, real, R, T, l);
+        __syncthreads();
         float worst = 0.f;
-        for (int j0 = 0; j0 < l; j0 += 8) {
-            const int jn = min(8, l - j0);
-            mult_a(A, n1, n2, real, R + (size_t)n2 * j0, T, jn);
-            if (tid < 8) s_res[tid] = 0.f;
-            __syncthreads();
-            for (int jj = 0; jj < jn; ++jj) {
-                const int j = j0 + jj;
-                if (!((double)sig[j] > J.tau)) continue;
-                float sacc = 0.f;
-                for (int e = tid; e < n1; e += kT) {
-                    const float2 a = T[e + (size_t)n1 * jj], u = U[e + (size_t)n1 * j];
-                    const float dx = a.x - sig[j] * u.x, dy = a.y - sig[j] * u.y;
-                    sacc = fmaf(dx, dx, fmaf(dy, dy, sacc));
-                }
-                sacc = warp_sum(sacc);
-                if (lane == 0) atomicAdd(&s_res[jj], sacc);
+        for (int j = warp; j < l; j += kTS / 32) {
+            if (!((double)sig[j] > J.tau)) continue;
+            float sacc = 0.f;
+            for (int e = lane; e < n1; e += 32) {
+                const float2 a = T[e + (size_t)n1 * j], u = U[e + (size_t)n1 * j];
+                const float dx = a.x - sig[j] * u.x, dy = a.y - sig[j] * u.y;
+                sacc = fmaf(dx, dx, fmaf(dy, dy, sacc));
             }
-            __syncthreads();
-            for (int jj = 0; jj < jn; ++jj) {
-                const int j = j0 + jj;
-                if ((double)sig[j] > J.tau)
-                    worst = fmaxf(worst, sqrtf(s_res[jj]) * (float)(((double)sig[j] - J.tau) / sig[j]));
-            }
-            __syncthreads();
+            sacc = warp_sum(sacc);
+            worst = fmaxf(worst, sqrtf(sacc) * (float)(((double)sig[j] - J.tau) / sig[j]));
         }
+        if (lane == 0) s_worst[warp] = worst;
+        __syncthreads();
+        worst = 0.f;
+        for (int w = 0; w < kTS / 32; ++w) worst = fmaxf(worst, s_worst[w]);
         ok = worst <= P.resid_tol * smax;
     }
     if (ok) {
         // 4(c): norm of A - U_k S_k R_k^H by two power iterations from a random start
-        for (int c = tid; c < n2; c += kT) xv[c] = omega(P.seed ^ 0x5bd1e995u, job, c, 0, real);
+        for (int c = tid; c < n2; c += kTS) xv[c] = omega(P.seed ^ 0x5bd1e995u, job, c, 0, real);
         __syncthreads();
         float est = 0.f;
         for (int it = 0; it < 2; ++it) {
+            // normalise x (every warp reduces the same shared vector)
             float nx = 0.f;
-            for (int c = tid; c < n2; c += kT) nx = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, nx));
-            nx = block_sum(nx, red);
+            for (int c = lane; c < n2; c += 32) nx = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, nx));
+            nx = warp_sum(nx);
             const float inx = nx > 0.f ? rsqrtf(nx) : 0.f;
-            for (int c = tid; c < n2; c += kT) { xv[c].x *= inx; xv[c].y *= inx; }
+            __syncthreads();
+            for (int c = tid; c < n2; c += kTS) { xv[c].x *= inx; xv[c].y *= inx; }
             __syncthreads();
             // coef_j = sigma_j (r_j^H x)   (r_j = 0 for the columns that are not kept)
-            for (int j = warp; j < l; j += kT / 32) {
+            for (int j = warp; j < l; j += kTS / 32) {
                 float dr = 0.f, di = 0.f;
                 for (int c = lane; c < n2; c += 32) {
                     const float2 rr = R[c + (size_t)n2 * j], x = xv[c];
@@ -487,16 +619,10 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
                 di = warp_sum(di);
                 if (lane == 0) coef[j] = make_float2(sig[j] * dr, sig[j] * di);
             }
-            __syncthreads();
             // y = A x - U coef
-            for (int i = tid; i < n1; i += kT) {
-                float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-                for (int c = 0; c < n2; ++c) {
-                    const float2 a = ld_a(A, i + (int64_t)n1 * c, real), x = xv[c];
-                    acc.x = fmaf(a.x, x.x, fmaf(-a.y, x.y, acc.x));
-                    acc.y = fmaf(a.x, x.y, fmaf(a.y, x.x, acc.y));
-                }
+            matvec_a(A, n1, n2, real, xv, yv);
+            for (int i = tid; i < n1; i += kTS) {
+                float2 acc = yv[i];
                 for (int j = 0; j < l; ++j) {
                     const float2 u = U[i + (size_t)n1 * j], d = coef[j];
                     acc.x -= fmaf(u.x, d.x, -u.y * d.y);
@@ -506,7 +632,7 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
             }
             __syncthreads();
             // coef_j = sigma_j (u_j^H y) for the kept columns
-            for (int j = warp; j < l; j += kT / 32) {
+            for (int j = warp; j < l; j += kTS / 32) {
                 float dr = 0.f, di = 0.f;
                 for (int i = lane; i < n1; i += 32) {
                     const float2 u = U[i + (size_t)n1 * j], y = yv[i];
@@ -516,20 +642,14 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
                 dr = warp_sum(dr);
                 di = warp_sum(di);
                 const float w = fac[j] > 0.f ? sig[j] : 0.f;
-                if (lane == 0) coef[j] = make_float2(w * dr, w * di);
+                if (lane == 0) coef[j + kLMax] = make_float2(w * dr, w * di);
             }
-            __syncthreads();
             // x = A^H y - R coef
-            for (int c = tid; c < n2; c += kT) {
-                float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-                for (int i = 0; i < n1; ++i) {
-                    const float2 a = ld_a(A, i + (int64_t)n1 * c, real), y = yv[i];
-                    acc.x = fmaf(a.x, y.x, fmaf(a.y, y.y, acc.x));
-                    acc.y = fmaf(a.x, y.y, fmaf(-a.y, y.x, acc.y));
-                }
+            matvec_ah(A, n1, n2, real, yv, xv);
+            for (int c = tid; c < n2; c += kTS) {
+                float2 acc = xv[c];
                 for (int j = 0; j < l; ++j) {
-                    const float2 rr = R[c + (size_t)n2 * j], d = coef[j];
+                    const float2 rr = R[c + (size_t)n2 * j], d = coef[j + kLMax];
                     acc.x -= fmaf(rr.x, d.x, -rr.y * d.y);
                     acc.y -= fmaf(rr.x, d.y, rr.y * d.x);
                 }
@@ -537,8 +657,8 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
             }
             __syncthreads();
             float nx2 = 0.f;
-            for (int c = tid; c < n2; c += kT) nx2 = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, nx2));
-            nx2 = block_sum(nx2, red);
+            for (int c = lane; c < n2; c += 32) nx2 = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, nx2));
+            nx2 = warp_sum(nx2);
             est = sqrtf(sqrtf(nx2));  // ||E^H E x||^(1/2) with ||x|| = 1
         }
         ok = (double)est < 0.8 * J.tau;
@@ -548,10 +668,10 @@ __global__ void __launch_bounds__(kT, 4) sketch_svt_kernel(const SvdJob* __restr
         return;
     }
     // 5. W = sum_{sigma_j > tau} (sigma_j - tau) u_j r_j^H over A
-    for (int j = tid; j < l; j += kT)
+    for (int j = tid; j < l; j += kTS)
         fac[j] = ((double)sig[j] > J.tau) ? (float)((double)sig[j] - J.tau) : 0.f;
     __syncthreads();
-    for (int t = tid; t < n1 * n2; t += kT) {
+    for (int t = tid; t < n1 * n2; t += kTS) {
         const int i = t % n1, c = t / n1;
         float2 acc = make_float2(0.f, 0.f);
         for (int j = 0; j < l; ++j) {
@@ -790,7 +910,7 @@ cudaError_t launch_sketch_svt(const SvdJob* jobs, int ncta, size_t smem, const S
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sketch_svt_kernel<<<ncta, kT, smem, s>>>(jobs, p);
+    sketch_svt_kernel<<<ncta, kTS, smem, s>>>(jobs, p);
     return cudaGetLastError();
 }
 
