@@ -487,7 +487,18 @@ __global__ void __launch_bounds__(kTS, 3) sketch_svt_kernel(const SvdJob* __rest
     float2* bq = B0;
     float2* bz = B1;
     float2* bs = B2;
-    for (int t = tid; t < n2 * l; t += kTS) bs[t] = omega(P.seed, job, t % n2, t / n2, real);
+    // Omega (n2 x l): one hash per row and group of 16 columns, two bits per entry
+    for (int t = tid; t < n2 * ((l + 15) >> 4); t += kTS) {
+        const int rr = t % n2, c0 = (t / n2) * 16;
+        const uint32_t h = mix32(P.seed ^ mix32((uint32_t)job * 0x9e3779b9u ^
+                                                mix32((uint32_t)rr * 0x632be5abu + (uint32_t)c0)));
+        for (int c = c0; c < min(l, c0 + 16); ++c) {
+            const uint32_t b = h >> (2 * (c - c0));
+            const float a = (b & 1u) ? 1.f : -1.f, bb = (b & 2u) ? 1.f : -1.f;
+            bs[rr + (size_t)n2 * c] = real ? make_float2(a, 0.f)
+                                           : make_float2(a * 0.70710678f, bb * 0.70710678f);
+        }
+    }
     __syncthreads();
     mult_a(A, n1, n2, real, bs, bq, l);
     __syncthreads();
@@ -671,18 +682,41 @@ __global__ void __launch_bounds__(kTS, 3) sketch_svt_kernel(const SvdJob* __rest
     for (int j = tid; j < l; j += kTS)
         fac[j] = ((double)sig[j] > J.tau) ? (float)((double)sig[j] - J.tau) : 0.f;
     __syncthreads();
-    for (int t = tid; t < n1 * n2; t += kTS) {
-        const int i = t % n1, c = t / n1;
-        float2 acc = make_float2(0.f, 0.f);
+    // scale the kept columns of U by sigma - tau (the others by 0) once
+    for (int t = tid; t < n1 * l; t += kTS) {
+        const float f = fac[t / n1];
+        U[t].x *= f;
+        U[t].y *= f;
+    }
+    __syncthreads();
+    // 2 x 2 output tiles: rows (i, i + 1), columns (c, c + 1)
+    const int h1 = (n1 + 1) >> 1, h2 = (n2 + 1) >> 1;
+    for (int t = tid; t < h1 * h2; t += kTS) {
+        const int i = 2 * (t % h1), c = 2 * (t / h1);
+        const bool i1 = i + 1 < n1, c1 = c + 1 < n2;
+        float2 a00 = make_float2(0.f, 0.f), a10 = a00, a01 = a00, a11 = a00;
         for (int j = 0; j < l; ++j) {
-            const float f = fac[j];
-            if (f == 0.f) continue;
-            const float2 u = U[i + (size_t)n1 * j], rr = R[c + (size_t)n2 * j];
-            acc.x = fmaf(f, fmaf(u.x, rr.x, u.y * rr.y), acc.x);  // f u conj(r)
-            acc.y = fmaf(f, fmaf(u.y, rr.x, -u.x * rr.y), acc.y);
+            if (fac[j] == 0.f) continue;
+            const float2 u0 = U[i + (size_t)n1 * j], u1 = i1 ? U[i + 1 + (size_t)n1 * j] : u0;
+            const float2 r0 = R[c + (size_t)n2 * j], r1 = c1 ? R[c + 1 + (size_t)n2 * j] : r0;
+            // u conj(r)
+            a00.x = fmaf(u0.x, r0.x, fmaf(u0.y, r0.y, a00.x));
+            a00.y = fmaf(u0.y, r0.x, fmaf(-u0.x, r0.y, a00.y));
+            a10.x = fmaf(u1.x, r0.x, fmaf(u1.y, r0.y, a10.x));
+            a10.y = fmaf(u1.y, r0.x, fmaf(-u1.x, r0.y, a10.y));
+            a01.x = fmaf(u0.x, r1.x, fmaf(u0.y, r1.y, a01.x));
+            a01.y = fmaf(u0.y, r1.x, fmaf(-u0.x, r1.y, a01.y));
+            a11.x = fmaf(u1.x, r1.x, fmaf(u1.y, r1.y, a11.x));
+            a11.y = fmaf(u1.y, r1.x, fmaf(-u1.x, r1.y, a11.y));
         }
-        if (real) acc.y = 0.f;
-        J.W[t] = acc;
+        if (real) a00.y = a10.y = a01.y = a11.y = 0.f;
+        float2* w0 = J.W + i + (size_t)n1 * c;
+        w0[0] = a00;
+        if (i1) w0[1] = a10;
+        if (c1) {
+            w0[n1] = a01;
+            if (i1) w0[n1 + 1] = a11;
+        }
     }
     if (tid == 0) {
         P.flag[job] = 0;
