@@ -49,6 +49,18 @@ cudaError_t ensure_pool() {
     return cudaSuccess;
 }
 
+int g_sms[128] = {};
+
+// Number of SMs of the current device (cached).
+tp_status sm_count(int* out) {
+    int dev = 0;
+    TP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return TP_ERR_CUDA;
+    if (!g_sms[dev]) TP_CUDA(cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev));
+    *out = g_sms[dev];
+    return TP_OK;
+}
+
 tp_status prepare() {
     TP_CUDA(ensure_pool());
     TP_CUDA(ensure_twiddles());
@@ -300,6 +312,8 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         bytes += Workspace::round(sizeof(SvdJob) * (slices + 1));        // natural-order jobs
         bytes += Workspace::round(sizeof(float) * kProposerInputs * slices);
         bytes += 4 * Workspace::round(sizeof(int32_t) * slices);  // ell, flags, counts, order
+        bytes += Workspace::round(sizeof(int32_t) * kSketchClasses * slices);  // sketch queues
+        bytes += Workspace::round(sizeof(int32_t) * 2 * kSketchClasses);       // queue counters
     }
     if (train) bytes += Workspace::round(sizeof(float) * proposer_fit_scratch_floats((int)slices));
     Workspace ws(s);
@@ -312,6 +326,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
     float* feat = nullptr;
     int32_t *ell = nullptr, *flags = nullptr, *counts = nullptr, *d_order = nullptr;
+    int32_t *d_queues = nullptr, *d_qcount = nullptr;
     SvdJob* d_nat = nullptr;
     if (need_feat) {
         d_nat = ws.take<SvdJob>(slices);
@@ -320,6 +335,8 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         flags = ws.take<int32_t>(slices);
         counts = ws.take<int32_t>(slices);
         d_order = ws.take<int32_t>(slices);
+        d_queues = ws.take<int32_t>((size_t)kSketchClasses * slices);
+        d_qcount = ws.take<int32_t>(2 * kSketchClasses);
         TP_TRY(ws.check());
     }
     FftBatch fwd, inv;
@@ -371,47 +388,41 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     if (learned) {
         TP_CUDA(launch_proposer(feat, d_nat, (int)slices, ell, s));
         TP_TRY(o.mark(2, s));
-        // size classes by shared memory at sketch width 24 (a slice whose proposed width needs
-        // more than its class provides falls back): 4, 3, 2 and 1 CTAs of the sketch kernel
-        // per SM; slices beyond the last class get a launch without shared memory and fall
-        // back
-        constexpr int kSizeL = 24;
-        constexpr int kClasses = 5;
-        const size_t caps[kClasses - 1] = {56 * 1024, 75 * 1024, 113 * 1024, 220 * 1024};
-        std::vector<std::vector<int32_t>> cls(kClasses);
-        for (int64_t j = 0; j < slices; ++j) {
-            const size_t need = sketch_smem_need(natural[j].n1, natural[j].n2, kSizeL);
-            int c = kClasses - 1;
-            for (int q = 0; q < kClasses - 1; ++q)
-                if (need <= caps[q]) { c = q; break; }
-            cls[c].push_back((int32_t)j);
-        }
-        std::vector<int32_t> order;
-        std::vector<size_t> start(kClasses), smem(kClasses, 0);
-        for (int c = 0; c < kClasses; ++c) {
-            std::stable_sort(cls[c].begin(), cls[c].end(), [&](int32_t a, int32_t b) {
-                return (int64_t)natural[a].n1 * natural[a].n2 > (int64_t)natural[b].n1 * natural[b].n2;
-            });
-            start[c] = order.size();
-            for (int32_t j : cls[c]) {
-                order.push_back(j);
-                if (c < kClasses - 1)
-                    smem[c] = std::max(smem[c], sketch_smem_need(natural[j].n1, natural[j].n2, kSizeL));
-            }
-        }
-        TP_TRY(upload(d_order, order, s));
-        for (int c = 0; c < kClasses; ++c) {
-            if (cls[c].empty()) continue;
+        // Sketch queues: the slices, largest first, binned on the device by the shared memory
+        // their proposed width needs (3, 2 and 1 CTAs of the sketch kernel per SM); one
+        // persistent launch per class works through its queue.  Slices too large for every
+        // class (or without a usable width) are flagged for the Jacobi path by the binning.
+        std::vector<int32_t> sorted(slices);
+        for (int64_t j = 0; j < slices; ++j) sorted[j] = (int32_t)j;
+        std::stable_sort(sorted.begin(), sorted.end(), [&](int32_t a, int32_t b) {
+            return (int64_t)natural[a].n1 * natural[a].n2 > (int64_t)natural[b].n1 * natural[b].n2;
+        });
+        TP_TRY(upload(d_order, sorted, s));
+        SketchCaps caps;
+        caps.n = 3;
+        caps.bytes[0] = 74 * 1024;
+        caps.bytes[1] = 112 * 1024;
+        caps.bytes[2] = 220 * 1024;
+        TP_CUDA(launch_sketch_bin(d_nat, d_order, (int)slices, ell, flags, caps, d_queues, d_qcount,
+                                  s));
+        int sms = 0;
+        TP_TRY(sm_count(&sms));
+        for (int c = 0; c < caps.n; ++c) {
+            const int per_sm = sketch_blocks_per_sm(caps.bytes[c]);
+            if (per_sm <= 0) return TP_ERR_CUDA;
             SketchParams sp;
-            sp.order = d_order + start[c];
+            sp.order = d_queues + (size_t)c * slices;
+            sp.queue_len = d_qcount + 2 * c;
+            sp.queue_next = d_qcount + 2 * c + 1;
             sp.ell = ell;
             sp.flag = flags;
             sp.count = counts;
             sp.seed = 0x9e3779b9u;
             sp.power_iters = 1;
             sp.resid_tol = 1e-5f;
-            sp.smem_bytes = (int)smem[c];
-            TP_CUDA(launch_sketch_svt(d_nat, (int)cls[c].size(), smem[c], sp, s));
+            sp.smem_bytes = (int)caps.bytes[c];
+            const int64_t grid = std::min<int64_t>(slices, (int64_t)sms * per_sm);
+            TP_CUDA(launch_sketch_svt(d_nat, (int)grid, caps.bytes[c], sp, s));
         }
         TP_TRY(o.mark(3, s));
         if (o.slice_flags_out)

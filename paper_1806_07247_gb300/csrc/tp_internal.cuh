@@ -125,7 +125,9 @@ constexpr int kProposerInputs = 12;    // features per slice
 constexpr int kProposerFloats = TP_PROPOSER_FLOATS;
 
 struct SketchParams {
-    const int32_t* order = nullptr;  // CTA -> job index (nullptr: identity)
+    const int32_t* order = nullptr;  // CTA (or queue position) -> job index (nullptr: identity)
+    const int32_t* queue_len = nullptr;  // persistent mode: number of entries of `order`
+    int32_t* queue_next = nullptr;       // persistent mode: work counter (zero at launch)
     const int32_t* ell;   // per job: sketch width (0: go to the full Jacobi SVD)
     int32_t* flag;        // per job: 0 = W written by the sketch path, 1 = needs Jacobi
     int32_t* count;       // per job: #{sigma > tau} on success (optional)
@@ -140,6 +142,18 @@ __host__ __device__ inline size_t sketch_smem_need(int n1, int n2, int l) {
     return sizeof(float2) * (3 * nm * l + (size_t)3 * l * l + (size_t)n1 + n2 + 2 * kSketchMaxL) +
            sizeof(float) * (2 * kSketchMaxL) + 64;
 }
+// Size classes of the sketch kernel's queues: shared memory bytes per CTA, increasing.
+constexpr int kSketchClasses = 4;
+struct SketchCaps {
+    int n;
+    uint32_t bytes[kSketchClasses];
+};
+// Bins the slices (in the order of `sorted`) into one queue per class; see tp_sketch.cu.
+cudaError_t launch_sketch_bin(const SvdJob* jobs, const int32_t* sorted, int n, const int32_t* ell,
+                              int32_t* flag, const SketchCaps& caps, int32_t* queues,
+                              int32_t* counts, cudaStream_t s);
+// Resident CTAs of the sketch kernel per SM at this dynamic shared memory (0 on error).
+int sketch_blocks_per_sm(size_t smem);
 size_t features_smem_bytes(int n1, int n2);
 cudaError_t launch_features(const SvdJob* jobs, int njobs, int max_n1, int max_n2, float* feat,
                             uint32_t seed, cudaStream_t s);

@@ -451,14 +451,21 @@ __device__ void matvec_ah(const float2* __restrict__ A, int n1, int n2, bool rea
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kTS, 3) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
-                                                           SketchParams P) {
-    extern __shared__ float4 smem4[];
-    __shared__ int s_flag;
-    __shared__ float s_worst[kTS / 32];
-    __shared__ float4 s_rot[kLMax / 2];
-    __shared__ int2 s_pq[kLMax / 2];
-    const int job = P.order ? P.order[blockIdx.x] : (int)blockIdx.x;
+// Shared state of one CTA of the sketch kernel besides the dynamic buffers.
+struct SketchShared {
+    int flag, item;
+    float worst[kTS / 32];
+    float4 rot[kLMax / 2];
+    int2 pq[kLMax / 2];
+};
+
+// The whole sketch SVT of one slice (steps 2-5 of the file comment) by the calling CTA.
+__device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const SketchParams& P,
+                           float4* smem4, SketchShared& sh) {
+    int& s_flag = sh.flag;
+    float* s_worst = sh.worst;
+    float4* s_rot = sh.rot;
+    int2* s_pq = sh.pq;
     const SvdJob J = jobs[job];
     const int n1 = J.n1, n2 = J.n2, nm = max(n1, n2);
     const bool real = J.real_slice != 0;
@@ -724,6 +731,85 @@ __global__ void __launch_bounds__(kTS, 3) sketch_svt_kernel(const SvdJob* __rest
     }
 }
 
+// One slice per CTA (P.queue_next == nullptr, CTA b takes P.order[b]), or a persistent grid
+// that takes slices P.order[i] from a work counter until the queue of *P.queue_len is empty;
+// the queue is ordered largest slice first, so the tail is made of small slices.
+__global__ void __launch_bounds__(kTS, 3) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
+                                                           SketchParams P) {
+    extern __shared__ float4 smem4[];
+    __shared__ SketchShared sh;
+    if (!P.queue_next) {
+        sketch_one(jobs, P.order ? P.order[blockIdx.x] : (int)blockIdx.x, P, smem4, sh);
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(P.queue_next, 1);
+        __syncthreads();
+        const int item = sh.item;
+        if (item >= *P.queue_len) break;
+        sketch_one(jobs, P.order[item], P, smem4, sh);
+        __syncthreads();  // the CTA is done with this slice's shared state
+    }
+}
+
+// Sorts the slices into the sketch kernel's queues: class c holds the slices whose shared
+// memory need at their proposed width is at most caps[c] (and above caps[c - 1]), in the
+// order of `sorted` (largest first).  Slices without a usable width, or too large for every
+// class, are flagged for the Jacobi path here.  One CTA of 1024 threads; stable compaction by
+// warp ballots and per-class running offsets.  queues: ncls lists of n entries; counts: per
+// class (length, work counter).
+__global__ void __launch_bounds__(1024) sketch_bin_kernel(const SvdJob* __restrict__ jobs,
+                                                          const int32_t* __restrict__ sorted,
+                                                          int n, const int32_t* __restrict__ ell,
+                                                          int32_t* __restrict__ flag,
+                                                          SketchCaps caps, int32_t* queues,
+                                                          int32_t* counts) {
+    __shared__ int wsum[32][kSketchClasses];
+    __shared__ int base[kSketchClasses];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ncls = caps.n;
+    if (tid < ncls) base[tid] = 0;
+    __syncthreads();
+    for (int chunk = 0; chunk < n; chunk += 1024) {
+        const int idx = chunk + tid;
+        int c = -1, job = -1;
+        if (idx < n) {
+            job = sorted[idx];
+            const SvdJob& J = jobs[job];
+            const int l = ell[job];
+            if (l > 0 && l < min(J.n1, J.n2) && l <= kLMax) {
+                const size_t need = sketch_smem_need(J.n1, J.n2, l);
+                for (int q = 0; q < ncls; ++q)
+                    if (need <= caps.bytes[q]) { c = q; break; }
+            }
+            if (c < 0) flag[job] = 1;
+        }
+        int mypos = 0;
+        for (int q = 0; q < ncls; ++q) {
+            const unsigned m = __ballot_sync(0xffffffffu, c == q);
+            if (c == q) mypos = __popc(m & ((1u << lane) - 1u));
+            if (lane == 0) wsum[warp][q] = __popc(m);
+        }
+        __syncthreads();
+        if (tid < ncls) {
+            int run = base[tid];
+            for (int w = 0; w < 32; ++w) {
+                const int t = wsum[w][tid];
+                wsum[w][tid] = run;
+                run += t;
+            }
+            base[tid] = run;
+        }
+        __syncthreads();
+        if (c >= 0) queues[(size_t)c * n + wsum[warp][c] + mypos] = job;
+        __syncthreads();
+    }
+    if (tid < ncls) {
+        counts[2 * tid] = base[tid];
+        counts[2 * tid + 1] = 0;
+    }
+}
+
 // Features of each slice for the proposer (see the file comment); one CTA per slice.
 __global__ void __launch_bounds__(kT) features_kernel(const SvdJob* __restrict__ jobs,
                                                       float* __restrict__ feat, uint32_t seed) {
@@ -934,6 +1020,26 @@ cudaError_t launch_proposer(const float* feat, const SvdJob* jobs, int njobs, in
     if (njobs <= 0) return cudaSuccess;
     mlp_infer_kernel<<<(njobs + 127) / 128, 128, 0, s>>>(feat, jobs, njobs, ell);
     return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_bin(const SvdJob* jobs, const int32_t* sorted, int n, const int32_t* ell,
+                              int32_t* flag, const SketchCaps& caps, int32_t* queues,
+                              int32_t* counts, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    sketch_bin_kernel<<<1, 1024, 0, s>>>(jobs, sorted, n, ell, flag, caps, queues, counts);
+    return cudaGetLastError();
+}
+
+int sketch_blocks_per_sm(size_t smem) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(sketch_svt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sketch_svt_kernel, kTS, smem) !=
+        cudaSuccess)
+        return 0;
+    return nb;
 }
 
 cudaError_t launch_sketch_svt(const SvdJob* jobs, int ncta, size_t smem, const SketchParams& p,
