@@ -13,8 +13,9 @@
 // computed once per device on the host in FP64 (quarter points exact) and kept in a
 // static device table; the exponent (k*t) mod n3 is advanced by integer addition.
 //
-// This direct form serves every n3; a launch whose tubes all have the same power-of-two
-// n3 <= 64 uses the register FFT kernels further below instead.
+// This direct form serves n3 > 64; a launch whose tubes all have the same power-of-two
+// n3 <= 64 uses the register FFT kernels further below, and any other launch with n3 <= 64
+// the register-resident direct kernels after them.
 #include <math.h>
 
 #include <mutex>
@@ -348,6 +349,111 @@ __global__ void __launch_bounds__(256) irfft_reg_kernel(const FftJob* __restrict
 
 bool reg_fft_size(int n3) { return n3 >= 2 && n3 <= 64 && (n3 & (n3 - 1)) == 0; }
 
+// ---------------------------------------------------------------------------------------
+// Any n3 <= 64 (launches whose tubes differ in n3): one thread per tube, the tube in
+// registers, the real DFT by its definition with every index a compile-time constant, so
+// each twiddle is an operand read straight from the constant bank.  Samples t and n3 - t are
+// paired: Re X[k] = x0 + sum_t (x_t + x_{n3-t}) cos(2 pi k t / n3) (+ (-1)^k x_{n3/2}),
+// Im X[k] = -sum_t (x_t - x_{n3-t}) sin(2 pi k t / n3), and the inverse pairs the same way.
+// A CTA's tubes belong to one job, so the switch on n3 is uniform.
+// ---------------------------------------------------------------------------------------
+constexpr int kSmallN3 = 64;
+__constant__ float2 c_twall[kSmallN3 * (kSmallN3 + 1) / 2];  // length n at n (n - 1) / 2
+
+template <int N>
+__device__ __forceinline__ void rdft_small(const float* __restrict__ x, int64_t P, float2* X) {
+    constexpr int H = (N - 1) / 2;  // pairs (t, N - t), 1 <= t <= H
+    constexpr int O = N * (N - 1) / 2;
+    float s[H + 1], d[H + 1];
+    const float x0 = __ldg(x);
+    float xm = 0.f;
+#pragma unroll
+    for (int t = 1; t <= H; ++t) {
+        const float a = __ldg(x + P * t), b = __ldg(x + P * (N - t));
+        s[t] = a + b;
+        d[t] = a - b;
+    }
+    if (N % 2 == 0 && N > 1) xm = __ldg(x + P * (N / 2));
+#pragma unroll
+    for (int k = 0; k <= N / 2; ++k) {
+        float re = x0, im = 0.f;
+        if (N % 2 == 0 && N > 1) re += (k % 2 == 0) ? xm : -xm;
+#pragma unroll
+        for (int t = 1; t <= H; ++t) {
+            const float2 w = c_twall[O + (k * t) % N];
+            re = fmaf(s[t], w.x, re);
+            im = fmaf(-d[t], w.y, im);
+        }
+        if (k == 0 || 2 * k == N) im = 0.f;
+        X[P * k] = make_float2(re, im);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void irdft_small(const float2* __restrict__ X, int64_t P, float* x) {
+    constexpr int H = (N - 1) / 2;  // frequencies 1..H appear twice (k and N - k)
+    constexpr int O = N * (N - 1) / 2;
+    float re[H + 1], im[H + 1];
+    const float r0 = __ldg(X).x;
+    float rm = 0.f;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        const float2 v = __ldg(X + P * k);
+        re[k] = 2.f * v.x;
+        im[k] = 2.f * v.y;
+    }
+    if (N % 2 == 0 && N > 1) rm = __ldg(X + P * (N / 2)).x;
+    const float sc = 1.f / (float)N;
+#pragma unroll
+    for (int t = 0; t <= N / 2; ++t) {
+        float a = r0, b = 0.f;
+        if (N % 2 == 0 && N > 1) a += (t % 2 == 0) ? rm : -rm;
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            const float2 w = c_twall[O + (k * t) % N];
+            a = fmaf(re[k], w.x, a);
+            b = fmaf(im[k], w.y, b);
+        }
+        x[P * t] = (a - b) * sc;
+        if (t > 0 && 2 * t != N) x[P * (N - t)] = (a + b) * sc;
+    }
+}
+
+#define TP_SMALL_CASES(M) \
+    M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16) \
+    M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) \
+    M(31) M(32) M(33) M(34) M(35) M(36) M(37) M(38) M(39) M(40) M(41) M(42) M(43) M(44) \
+    M(45) M(46) M(47) M(48) M(49) M(50) M(51) M(52) M(53) M(54) M(55) M(56) M(57) M(58) \
+    M(59) M(60) M(61) M(62) M(63) M(64)
+
+__global__ void __launch_bounds__(256) rfft_small_kernel(const FftJob* __restrict__ jobs, int njobs) {
+    const FftJob J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int64_t p = (int64_t)(blockIdx.x - J.tile_begin) * 256 + threadIdx.x;
+    if (p >= J.P) return;
+    const float* x = J.x + p;
+    float2* X = J.X + p;
+    switch (J.n3) {
+#define TP_FWD(n) case n: rdft_small<n>(x, J.P, X); break;
+        TP_SMALL_CASES(TP_FWD)
+#undef TP_FWD
+        default: break;
+    }
+}
+
+__global__ void __launch_bounds__(256) irfft_small_kernel(const FftJob* __restrict__ jobs, int njobs) {
+    const FftJob J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int64_t p = (int64_t)(blockIdx.x - J.tile_begin) * 256 + threadIdx.x;
+    if (p >= J.P) return;
+    const float2* X = J.X + p;
+    float* x = const_cast<float*>(J.x) + p;
+    switch (J.n3) {
+#define TP_INV(n) case n: irdft_small<n>(X, J.P, x); break;
+        TP_SMALL_CASES(TP_INV)
+#undef TP_INV
+        default: break;
+    }
+}
+
 std::mutex g_tw_mutex;
 bool g_tw_ready[128] = {};
 
@@ -384,6 +490,9 @@ cudaError_t ensure_twiddles() {
     if (err != cudaSuccess) return err;
     err = cudaMemcpyToSymbol(c_tw64, host.data() + tw_offset(64), sizeof(float2) * 64);
     if (err != cudaSuccess) return err;
+    err = cudaMemcpyToSymbol(c_twall, host.data(),
+                             sizeof(float2) * (size_t)kSmallN3 * (kSmallN3 + 1) / 2);
+    if (err != cudaSuccess) return err;
     // the largest dynamic shared memory any launch of these kernels asks for
     const int fwd = (int)fft_smem_bytes(TP_MAX_N3, false), inv = (int)fft_smem_bytes(TP_MAX_N3, true);
     int mf = fwd, mi = inv;
@@ -402,7 +511,7 @@ cudaError_t ensure_twiddles() {
 }
 
 int fft_tiles(int64_t P, int max_n3, int uniform_n3) {
-    const int tp = reg_fft_size(uniform_n3) ? 256 : tubes_per_cta(max_n3);
+    const int tp = (reg_fft_size(uniform_n3) || max_n3 <= kSmallN3) ? 256 : tubes_per_cta(max_n3);
     return (int)((P + tp - 1) / tp);
 }
 
@@ -426,6 +535,10 @@ cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int ma
                         int uniform_n3, bool vec_ok, cudaStream_t s) {
     if (total_tiles <= 0) return cudaSuccess;
     if (reg_fft_size(uniform_n3)) return launch_reg<false>(d_jobs, njobs, total_tiles, uniform_n3, s);
+    if (max_n3 <= kSmallN3) {
+        rfft_small_kernel<<<total_tiles, 256, 0, s>>>(d_jobs, njobs);
+        return cudaGetLastError();
+    }
     int tp = tubes_per_cta(max_n3);
     size_t smem = fft_smem_bytes(max_n3, false);
     if (vec_ok) rfft_kernel<true><<<total_tiles, kFftThreads, smem, s>>>(d_jobs, njobs, tp);
@@ -437,6 +550,10 @@ cudaError_t launch_irfft(const FftJob* d_jobs, int njobs, int total_tiles, int m
                          int uniform_n3, bool vec_ok, cudaStream_t s) {
     if (total_tiles <= 0) return cudaSuccess;
     if (reg_fft_size(uniform_n3)) return launch_reg<true>(d_jobs, njobs, total_tiles, uniform_n3, s);
+    if (max_n3 <= kSmallN3) {
+        irfft_small_kernel<<<total_tiles, 256, 0, s>>>(d_jobs, njobs);
+        return cudaGetLastError();
+    }
     int tp = tubes_per_cta(max_n3);
     size_t smem = fft_smem_bytes(max_n3, true);
     if (vec_ok) irfft_kernel<true><<<total_tiles, kFftThreads, smem, s>>>(d_jobs, njobs, tp);
