@@ -102,7 +102,7 @@ typedef struct tp_options {
  * TP_METHOD_JACOBI:  one-sided Jacobi SVD of every slice (the plain FP32 path).
  * TP_METHOD_LEARNED: not in the paper. A trained proposer (tp_proposer_train) predicts
  *   k = #{sigma > tau} of each slice from cheap sketch features; a randomized range finder of
- *   width k + 8 with one power iteration and a small Jacobi SVD gives the top singular
+ *   width k + 4 with one power iteration and a small Jacobi SVD gives the top singular
  *   triplets; the slice is accepted only if the smallest computed singular value is below
  *   tau, the kept triplets' residuals ||A r - sigma u|| (times their weight (sigma - tau)/sigma
  *   in the result) are below 1e-5 sigma_max and the

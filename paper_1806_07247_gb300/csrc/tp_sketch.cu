@@ -5,7 +5,7 @@
 // Per slice A (n1 x n2 complex, column-major, in place in the half spectrum):
 //   1. a tiny MLP (12 -> 64 -> 64 -> 1, ReLU) reads cheap sketch features -- log ||A||_F / tau,
 //      the diagonal of the QR factor of an 8-column sketch A Omega_8 over tau, log n1, log n2,
-//      log min(n1, n2) -- and predicts k = #{sigma > tau}; the sketch width is l = k + 8;
+//      log min(n1, n2) -- and predicts k = #{sigma > tau}; the sketch width is l = k + 4;
 //   2. randomized range finder: Y = A Omega (Omega n2 x l, random +-1 / (+-1 +- i)/sqrt 2
 //      from a counter-based hash), q power iterations (Z = A^H Q, Y = A Z), each followed by
 //      shifted CholeskyQR3 orthonormalisation, Q = orth(Y);
@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(kT) features_kernel(const SvdJob* __restrict__
     }
 }
 
-// Proposer inference: one thread per slice, ell = clamp(ceil(k_hat) + 8).
+// Proposer inference: one thread per slice, ell = clamp(ceil(k_hat) + 4).
 __global__ void mlp_infer_kernel(const float* __restrict__ feat, const SvdJob* __restrict__ jobs,
                                  int n, int32_t* __restrict__ ell) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -912,7 +912,7 @@ __global__ void mlp_infer_kernel(const float* __restrict__ feat, const SvdJob* _
         out = fmaf(w[kW3 + a], fmaxf(v, 0.f), out);
     }
     const int r = min(jobs[s].n1, jobs[s].n2);
-    int l = (int)ceilf(fmaxf(out, 0.f)) + 8;
+    int l = (int)ceilf(fmaxf(out, 0.f)) + 4;
     l = min(l, kLMax);
     ell[s] = (l >= r) ? 0 : l;  // 0: sketching cannot help, full Jacobi
 }
