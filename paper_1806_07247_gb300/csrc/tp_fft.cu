@@ -365,6 +365,7 @@ __device__ __forceinline__ void rdft_small(const float* __restrict__ x, int64_t 
     constexpr int H = (N - 1) / 2;  // pairs (t, N - t), 1 <= t <= H
     constexpr int O = N * (N - 1) / 2;
     float s[H + 1], d[H + 1];
+    int e[H + 1];  // (k t) mod N for the current k
     const float x0 = __ldg(x);
     float xm = 0.f;
 #pragma unroll
@@ -372,17 +373,20 @@ __device__ __forceinline__ void rdft_small(const float* __restrict__ x, int64_t 
         const float a = __ldg(x + P * t), b = __ldg(x + P * (N - t));
         s[t] = a + b;
         d[t] = a - b;
+        e[t] = 0;
     }
     if (N % 2 == 0 && N > 1) xm = __ldg(x + P * (N / 2));
-#pragma unroll
-    for (int k = 0; k <= N / 2; ++k) {
+#pragma unroll 1
+    for (int k = 0; k <= N / 2; ++k) {  // rolled: the body stays small in the instruction cache
         float re = x0, im = 0.f;
-        if (N % 2 == 0 && N > 1) re += (k % 2 == 0) ? xm : -xm;
+        if (N % 2 == 0 && N > 1) re += (k & 1) ? -xm : xm;
 #pragma unroll
         for (int t = 1; t <= H; ++t) {
-            const float2 w = c_twall[O + (k * t) % N];
+            const float2 w = c_twall[O + e[t]];  // the same index across the warp
             re = fmaf(s[t], w.x, re);
             im = fmaf(-d[t], w.y, im);
+            e[t] += t;
+            if (e[t] >= N) e[t] -= N;
         }
         if (k == 0 || 2 * k == N) im = 0.f;
         X[P * k] = make_float2(re, im);
@@ -394,6 +398,7 @@ __device__ __forceinline__ void irdft_small(const float2* __restrict__ X, int64_
     constexpr int H = (N - 1) / 2;  // frequencies 1..H appear twice (k and N - k)
     constexpr int O = N * (N - 1) / 2;
     float re[H + 1], im[H + 1];
+    int e[H + 1];  // (k t) mod N for the current t
     const float r0 = __ldg(X).x;
     float rm = 0.f;
 #pragma unroll
@@ -401,18 +406,21 @@ __device__ __forceinline__ void irdft_small(const float2* __restrict__ X, int64_
         const float2 v = __ldg(X + P * k);
         re[k] = 2.f * v.x;
         im[k] = 2.f * v.y;
+        e[k] = 0;
     }
     if (N % 2 == 0 && N > 1) rm = __ldg(X + P * (N / 2)).x;
     const float sc = 1.f / (float)N;
-#pragma unroll
+#pragma unroll 1
     for (int t = 0; t <= N / 2; ++t) {
         float a = r0, b = 0.f;
-        if (N % 2 == 0 && N > 1) a += (t % 2 == 0) ? rm : -rm;
+        if (N % 2 == 0 && N > 1) a += (t & 1) ? -rm : rm;
 #pragma unroll
         for (int k = 1; k <= H; ++k) {
-            const float2 w = c_twall[O + (k * t) % N];
+            const float2 w = c_twall[O + e[k]];
             a = fmaf(re[k], w.x, a);
             b = fmaf(im[k], w.y, b);
+            e[k] += k;
+            if (e[k] >= N) e[k] -= N;
         }
         x[P * t] = (a - b) * sc;
         if (t > 0 && 2 * t != N) x[P * (N - t)] = (a + b) * sc;
