@@ -389,7 +389,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         TP_CUDA(launch_proposer(feat, d_nat, (int)slices, ell, s));
         TP_TRY(o.mark(2, s));
         // Sketch queues: the slices, largest first, binned on the device by the shared memory
-        // their proposed width needs (3, 2 and 1 CTAs of the sketch kernel per SM); one
+        // their proposed width needs (4, 3, 2 and 1 CTAs of the sketch kernel per SM); one
         // persistent launch per class works through its queue.  Slices too large for every
         // class (or without a usable width) are flagged for the Jacobi path by the binning.
         std::vector<int32_t> sorted(slices);
@@ -399,10 +399,11 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         });
         TP_TRY(upload(d_order, sorted, s));
         SketchCaps caps;
-        caps.n = 3;
-        caps.bytes[0] = 74 * 1024;
-        caps.bytes[1] = 112 * 1024;
-        caps.bytes[2] = 220 * 1024;
+        caps.n = 4;
+        caps.bytes[0] = 55 * 1024;
+        caps.bytes[1] = 74 * 1024;
+        caps.bytes[2] = 112 * 1024;
+        caps.bytes[3] = 220 * 1024;
         TP_CUDA(launch_sketch_bin(d_nat, d_order, (int)slices, ell, flags, caps, d_queues, d_qcount,
                                   s));
         int sms = 0;

@@ -88,22 +88,22 @@ __device__ __forceinline__ float2 ld_a(const float2* A, int64_t idx, bool real) 
 }
 
 // Y (n1 x l, ld n1) = A X (X: n2 x l, ld n2, shared).  A work item is one row of Y and a
-// chunk of 8 of its columns; all threads of the CTA share the items.
+// chunk of 4 of its columns; all threads of the CTA share the items.
 __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, const float2* X,
                        float2* Y, int l) {
-    const int nch = (l + 7) >> 3;
+    const int nch = (l + 3) >> 2;
     for (int t = threadIdx.x; t < n1 * nch; t += (int)blockDim.x) {
-        const int i = t % n1, j0 = (t / n1) * 8;
-        const int jn = min(8, l - j0);
-        float2 acc[8];
+        const int i = t % n1, j0 = (t / n1) * 4;
+        const int jn = min(4, l - j0);
+        float2 acc[4];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) acc[jj] = make_float2(0.f, 0.f);
+        for (int jj = 0; jj < 4; ++jj) acc[jj] = make_float2(0.f, 0.f);
         const float2* x = X + (size_t)n2 * j0;
 #pragma unroll 4
         for (int c = 0; c < n2; ++c) {
             const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
+            for (int jj = 0; jj < 4; ++jj) {
                 if (jj < jn) {
                     const float2 xv = x[c + (size_t)n2 * jj];
                     acc[jj].x = fmaf(a.x, xv.x, fmaf(-a.y, xv.y, acc[jj].x));
@@ -112,17 +112,17 @@ __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, 
             }
         }
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
+        for (int jj = 0; jj < 4; ++jj)
             if (jj < jn) Y[i + (size_t)n1 * (j0 + jj)] = acc[jj];
     }
 }
 
 // Z (n2 x l, ld n2) = A^H Y (Y: n1 x l, ld n1, shared).  A work item is one column of A, a
-// chunk of 8 columns of Y and (when items are fewer than threads) a range of rows; partial
+// chunk of 4 columns of Y and (when items are fewer than threads) a range of rows; partial
 // sums over row ranges meet in Z through shared-memory atomics.
 __device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real, const float2* Y,
                         float2* Z, int l) {
-    const int nch = (l + 7) >> 3;
+    const int nch = (l + 3) >> 2;
     const int items = n2 * nch;
     const int parts = max(1, min((int)blockDim.x / max(items, 1), 8));
     const int span = (n1 + parts - 1) / parts;
@@ -132,17 +132,17 @@ __device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real,
     }
     for (int t = threadIdx.x; t < items * parts; t += (int)blockDim.x) {
         const int c = t % n2, rest = t / n2, ch = rest % nch, pr = rest / nch;
-        const int j0 = ch * 8, jn = min(8, l - j0);
+        const int j0 = ch * 4, jn = min(4, l - j0);
         const int i0 = pr * span, i1 = min(n1, i0 + span);
-        float2 acc[8];
+        float2 acc[4];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) acc[jj] = make_float2(0.f, 0.f);
+        for (int jj = 0; jj < 4; ++jj) acc[jj] = make_float2(0.f, 0.f);
         const float2* y = Y + (size_t)n1 * j0;
 #pragma unroll 4
         for (int i = i0; i < i1; ++i) {
             const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
+            for (int jj = 0; jj < 4; ++jj) {
                 if (jj < jn) {
                     const float2 yv = y[i + (size_t)n1 * jj];
                     acc[jj].x = fmaf(a.x, yv.x, fmaf(a.y, yv.y, acc[jj].x));  // conj(a) y
@@ -151,7 +151,7 @@ __device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real,
             }
         }
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
+        for (int jj = 0; jj < 4; ++jj) {
             if (jj < jn) {
                 float2* z = Z + c + (size_t)n2 * (j0 + jj);
                 if (parts == 1) {
@@ -734,7 +734,7 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
 // One slice per CTA (P.queue_next == nullptr, CTA b takes P.order[b]), or a persistent grid
 // that takes slices P.order[i] from a work counter until the queue of *P.queue_len is empty;
 // the queue is ordered largest slice first, so the tail is made of small slices.
-__global__ void __launch_bounds__(kTS, 3) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kTS, 4) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
                                                            SketchParams P) {
     extern __shared__ float4 smem4[];
     __shared__ SketchShared sh;
