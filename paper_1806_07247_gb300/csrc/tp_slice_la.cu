@@ -101,6 +101,8 @@ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 // Slice inverse.  Shared memory: [n*n matrix if in_smem][rowk n][rowold n][colk n]
 // [perm n ints][reduction 32 floats + 32 ints].
 // ---------------------------------------------------------------------------------------
+// R: rows per lane, n <= 32 R.
+template <int R>
 __global__ void __launch_bounds__(512, 1) tinv_kernel(const LaJob* __restrict__ jobs, int in_smem,
                                                     uint32_t* status) {
     extern __shared__ float4 la_smem[];
@@ -151,20 +153,38 @@ __global__ void __launch_bounds__(512, 1) tinv_kernel(const LaJob* __restrict__ 
             colk[i] = M[src + (size_t)n * k];
         }
         __syncthreads();
-        // every element is written by the one thread that reads it
+        // Every element is written by the thread that reads it.  Lane `lane` owns rows
+        // lane + 32 m; their multipliers f_i (column k after the exchange) stay in registers.
+        float2 f[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const int i = lane + 32 * m;
+            f[m] = i < n ? colk[i] : make_float2(0.f, 0.f);
+        }
         for (int j = warp; j < n; j += nw) {
-            const float2 r = rowk[j];
+            const float2 r = rowk[j], ro = rowold[j];
             float2* col = M + (size_t)n * j;
-            for (int i = lane; i < n; i += 32) {
-                if (i == k) {
-                    col[i] = r;
-                    continue;
+            if (j == k) {  // the pivot column becomes -f_i / pivot (r = 1 / pivot here)
+#pragma unroll
+                for (int m = 0; m < R; ++m) {
+                    const int i = lane + 32 * m;
+                    if (i < n)
+                        col[i] = (i == k) ? r
+                                          : make_float2(-fmaf(f[m].x, r.x, -f[m].y * r.y),
+                                                        -fmaf(f[m].x, r.y, f[m].y * r.x));
                 }
-                float2 old = (i == p) ? rowold[j] : col[i];
-                if (j == k) old = make_float2(0.0f, 0.0f);
-                const float2 f = colk[i];
-                col[i] = make_float2(old.x - fmaf(f.x, r.x, -f.y * r.y),
-                                     old.y - fmaf(f.x, r.y, f.y * r.x));
+            } else {  // a_ij <- a'_ij - f_i r_j, row k <- r, row p takes the old row k
+#pragma unroll
+                for (int m = 0; m < R; ++m) {
+                    const int i = lane + 32 * m;
+                    if (i < n) {
+                        float2 a = col[i];
+                        if (i == p) a = ro;
+                        const float2 v = make_float2(fmaf(-f[m].x, r.x, fmaf(f[m].y, r.y, a.x)),
+                                                     fmaf(-f[m].x, r.y, fmaf(-f[m].y, r.x, a.y)));
+                        col[i] = (i == k) ? r : v;
+                    }
+                }
             }
         }
         __syncthreads();
@@ -336,9 +356,19 @@ cudaError_t launch_tinv(const LaJob* d_jobs, int njobs, int n, uint32_t* status,
     if (njobs <= 0) return cudaSuccess;
     const bool in_smem = tinv_smem_bytes(n, true) <= kLaSmemLimit;
     const size_t smem = tinv_smem_bytes(n, in_smem);
-    cudaError_t e = set_smem(reinterpret_cast<const void*>(tinv_kernel), smem);
-    if (e != cudaSuccess) return e;
-    tinv_kernel<<<njobs, la_threads(n, n), smem, s>>>(d_jobs, in_smem ? 1 : 0, status);
+    const int rows = (n + 31) / 32;
+#define TP_TINV_LAUNCH(R)                                                                      \
+    do {                                                                                       \
+        cudaError_t e = set_smem(reinterpret_cast<const void*>(tinv_kernel<R>), smem);          \
+        if (e != cudaSuccess) return e;                                                        \
+        tinv_kernel<R><<<njobs, la_threads(n, n), smem, s>>>(d_jobs, in_smem ? 1 : 0, status); \
+    } while (0)
+    if (rows <= 1) TP_TINV_LAUNCH(1);
+    else if (rows <= 2) TP_TINV_LAUNCH(2);
+    else if (rows <= 4) TP_TINV_LAUNCH(4);
+    else if (rows <= 8) TP_TINV_LAUNCH(8);
+    else TP_TINV_LAUNCH(16);
+#undef TP_TINV_LAUNCH
     return cudaGetLastError();
 }
 
