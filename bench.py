@@ -19,6 +19,10 @@ The JSON line also carries:
                 library chunk by chunk);
   tprod         t-product TFLOP/s on A 2048x1024x64 times B 1024x1024x64 in FP32,
                 BF16x3 and 3xTF32 slice-GEMM arithmetic;
+  trpca         the synthetic TRPCA-style loop: 50 ADMM iterations on a 240x320x100 tensor
+                (tubal rank 10, unit RMS, 10% of entries corrupted by U[-5, 5]), each one
+                prox_tnn call at tau = 1/mu (library) plus two elementwise updates; plain
+                Jacobi vs learned (proposer trained on the iterates of another draw);
   factor        tensor inverse (Def. 2.4) on 128x128x302 and economy t-QR (Thm. 2.4) on
                 128x64x302 (152 independent slices each, one per SM), slices/s and the slice
                 kernel's FP32 flop rate;
@@ -61,6 +65,7 @@ def parse():
     p.add_argument("--no-tprod", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-factor", action="store_true")
+    p.add_argument("--no-trpca", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--train-batches", type=int, default=4,
                    help="512-tensor batches (other seeds) that label the proposer's training set")
@@ -426,6 +431,8 @@ def run_tp(args):
         line["tprod"] = tprod_leg(args, tp, synth, device)
     if not args.no_factor and rank == 0:
         line["factor"] = factor_leg(args, tp, synth, device)
+    if not args.no_trpca and rank == 0:
+        line["trpca"] = trpca_leg(args, tp, synth, device)
     if rank == 0:
         rate, sl, nt, secs = oracle_sample(specs, rank, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(),
@@ -568,6 +575,85 @@ def factor_leg(args, tp, synth, device):
                      "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
                                   "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS}}
         del A
+    return out
+
+
+def trpca_problem(tp, synth, seed, device):
+    """L0 = P * Q (240x320x100, rank 10) at unit RMS; X = L0 with 10% of its entries (linear
+    column-major positions) shifted by U[-5, 5]."""
+    import torch
+    g = synth.trpca(seed)
+    L0 = tp.tprod(tp.to_device(g["P"], device), tp.to_device(g["Q"], device))
+    L0.mul_(1.0 / float(L0.pow(2).mean().sqrt()))
+    X = L0.clone()
+    flat = X.permute(2, 1, 0).reshape(-1)           # column-major element order, a view
+    flat[torch.from_numpy(g["pos"]).to(device)] += torch.from_numpy(g["val"]).to(device)
+    return L0, X, g["tau"]
+
+
+def trpca_admm(tp, X, lam, method, iters=50, record=None):
+    """ADMM for min ||L||_* + lam ||E||_1 s.t. L + E = X with the tensor nuclear norm of
+    Def. 2.9: L <- prox_tnn(X - E - Y/mu, 1/mu) (the library call), E <- soft(X - L - Y/mu,
+    lam/mu), Y <- Y + mu (L + E - X), mu <- min(1.1 mu, 1e10), mu0 = 1e-3."""
+    import torch
+    n1, n2, n3 = X.shape
+    L = tp.empty(n1, n2, n3, X.device)
+    E = torch.zeros_like(X)
+    Y = torch.zeros_like(X)
+    T = tp.empty(n1, n2, n3, X.device)
+    mu = 1e-3
+    flags = torch.zeros((n3 // 2 + 1,), dtype=torch.int32, device=X.device)
+    fb = torch.zeros((), dtype=torch.int64, device=X.device)
+    opts = tp.options(sync=False, method=method,
+                      slice_flags_out=flags if method == "learned" else None)
+    for _ in range(iters):
+        torch.sub(X, E, out=T)
+        T.sub_(Y, alpha=1.0 / mu)
+        if record is not None:
+            record.append((T.clone(), 1.0 / mu))
+        tp.prox_tnn(T, 1.0 / mu, out=L, opts=opts)
+        if method == "learned":
+            fb += flags.sum()
+        torch.sub(X, L, out=T)
+        T.sub_(Y, alpha=1.0 / mu)
+        E.copy_(torch.sign(T) * torch.clamp(T.abs() - lam / mu, min=0.0))
+        Y.add_(L + E - X, alpha=mu)
+        mu = min(1.1 * mu, 1e10)
+    return L, int(fb) / (iters * (n3 // 2 + 1))
+
+
+def trpca_leg(args, tp, synth, device):
+    import torch
+    L0, X, lam = trpca_problem(tp, synth, 0, device)
+    n1, n2, n3 = X.shape
+    h = n3 // 2 + 1
+    iters = 50
+    out = {"workload": "240x320x100, rank 10 at unit RMS, 10% corrupted by U[-5,5]; 50 ADMM "
+                       "iterations, mu0 = 1e-3, rho = 1.1, lambda = 1/sqrt(320*100)",
+           "slices_per_call": h, "iterations": iters}
+    # proposer for this loop: plain-path iterates of another draw label its training set
+    _, Xt, _ = trpca_problem(tp, synth, 1, device)
+    rec = []
+    trpca_admm(tp, Xt, lam, "jacobi", iters, record=rec)
+    t0 = time.time()
+    mse = tp.proposer_train([r[0] for r in rec], [r[1] for r in rec], steps=300, seed=2)
+    out["train"] = {"slices": len(rec) * h, "mse": mse, "seconds": time.time() - t0}
+    del rec, Xt
+    for method in ("jacobi", "learned"):
+        trpca_admm(tp, X, lam, method, 3)          # warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        L, fbf = trpca_admm(tp, X, lam, method, iters)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        err = float((L - L0).norm() / L0.norm())
+        out[method] = {"ms": ms, "ms_per_iteration": ms / iters,
+                       "slices_per_s": iters * h / (ms / 1e3), "L_rel_err": err}
+        if method == "learned":
+            out[method]["fallback_fraction"] = fbf
+    out["learned_vs_plain"] = out["jacobi"]["ms"] / out["learned"]["ms"]
     return out
 
 

@@ -420,6 +420,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             sp.count = counts;
             sp.seed = 0x9e3779b9u;
             sp.power_iters = 1;
+            sp.retries = 2;
             sp.resid_tol = 1e-5f;
             sp.smem_bytes = (int)caps.bytes[c];
             const int64_t grid = std::min<int64_t>(slices, (int64_t)sms * per_sm);

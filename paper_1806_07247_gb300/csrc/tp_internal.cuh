@@ -133,6 +133,7 @@ struct SketchParams {
     int32_t* count;       // per job: #{sigma > tau} on success (optional)
     uint32_t seed;
     int power_iters;
+    int retries = 0;      // extra attempts with two more power iterations each (check a passed)
     float resid_tol;
     int smem_bytes;       // dynamic shared memory of the launch
 };

@@ -469,26 +469,37 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     const SvdJob J = jobs[job];
     const int n1 = J.n1, n2 = J.n2, nm = max(n1, n2);
     const bool real = J.real_slice != 0;
-    const int l = P.ell[job];
+    int l = P.ell[job];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (l <= 0 || l >= min(n1, n2) || l > kLMax ||
         sketch_smem_need(n1, n2, l) > (size_t)P.smem_bytes) {
         if (tid == 0) P.flag[job] = 1;
         return;
     }
+    const float2* A = J.A;
+
+    // Steps 2-4 run up to 1 + P.retries times.  A slice whose sketch reached below tau (check
+    // a) but failed the residual or deflation check is sketched again with two more power
+    // iterations; one whose sketch did not reach below tau (the rank was underestimated) is
+    // sketched again 4 columns wider, if that still fits the CTA's shared memory.  Any other
+    // failure leaves the slice to the Jacobi path.
+    float2 *U = nullptr, *R = nullptr, *V = nullptr, *G = nullptr, *C = nullptr;
+    float2 *xv = nullptr, *yv = nullptr, *coef = nullptr;
+    float *sig = nullptr, *fac = nullptr;
+    int k = 0, q = P.power_iters;
+    for (int attempt = 0;; ++attempt) {
     float2* B0 = reinterpret_cast<float2*>(smem4);  // three max(n1, n2) x l buffers
     float2* B1 = B0 + (size_t)nm * l;
     float2* B2 = B1 + (size_t)nm * l;
-    float2* V = B2 + (size_t)nm * l;                // l x l
-    float2* G = V + (size_t)l * l;                  // l x l
-    float2* C = G + (size_t)l * l;                  // l x l
-    float2* xv = C + (size_t)l * l;                 // n2
-    float2* yv = xv + n2;                           // n1
-    float2* coef = yv + n1;                         // 2 kLMax
-    float* sig = reinterpret_cast<float*>(coef + 2 * kLMax);
-    float* fac = sig + kLMax;
-    const float2* A = J.A;
-
+    V = B2 + (size_t)nm * l;                        // l x l
+    G = V + (size_t)l * l;                          // l x l
+    C = G + (size_t)l * l;                          // l x l
+    xv = C + (size_t)l * l;                         // n2
+    yv = xv + n2;                                   // n1
+    coef = yv + n1;                                 // 2 kLMax
+    sig = reinterpret_cast<float*>(coef + 2 * kLMax);
+    fac = sig + kLMax;
+    bool below = false;
     // 2. range finder with power iterations; shifted CholeskyQR3 orthonormalisations.  bq holds
     // the current Q (n1 x l), bz the current Z (n2 x l), bs is scratch.
     float2* bq = B0;
@@ -509,10 +520,10 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     __syncthreads();
     mult_a(A, n1, n2, real, bs, bq, l);
     __syncthreads();
-    float2* r = orth3(bq, bs, n1, l, G, C, &s_flag, P.power_iters > 0 ? 2 : 3);
+    float2* r = orth3(bq, bs, n1, l, G, C, &s_flag, q > 0 ? 2 : 3);
     bool ok = r != nullptr;
     if (ok && r != bq) { bs = bq; bq = r; }
-    for (int it = 0; ok && it < P.power_iters; ++it) {
+    for (int it = 0; ok && it < q; ++it) {
         mult_ah(A, n1, n2, real, bq, bz, l);
         r = orth3(bz, bs, n2, l, G, C, &s_flag, 2);
         ok = r != nullptr;
@@ -547,9 +558,9 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         __syncthreads();
     }
     float smin = 3.4e38f, smax = 0.f;
-    int k = 0;
-    float2* U = bs;  // n1 x l
-    float2* R = bz;  // n2 x l: D, then D / sigma on the kept columns
+    k = 0;
+    U = bs;  // n1 x l
+    R = bz;  // n2 x l: D, then D / sigma on the kept columns
     float2* T = bq;  // n1 x l: A R for the residuals (Q is dead once U is formed)
     if (ok) {
         for (int j = warp; j < l; j += kTS / 32) {
@@ -580,6 +591,7 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
             k += ((double)sig[j] > J.tau);
         }
         ok = !((double)smin > J.tau);
+        below = ok;
     }
     if (ok) {
         for (int j = tid; j < l; j += kTS) fac[j] = ((double)sig[j] > J.tau) ? 1.f / sig[j] : 0.f;
@@ -681,9 +693,21 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         }
         ok = (double)est < 0.8 * J.tau;
     }
-    if (!ok) {
+    if (ok) break;
+    bool again = attempt < P.retries;
+    if (again && below) {
+        q += 2;
+    } else if (again) {
+        const int l2 = l + 4;
+        again = l2 < min(n1, n2) && l2 <= kLMax &&
+                sketch_smem_need(n1, n2, l2) <= (size_t)P.smem_bytes;
+        if (again) l = l2;
+    }
+    if (!again) {
         if (tid == 0) P.flag[job] = 1;
         return;
+    }
+    __syncthreads();  // the next attempt rewrites the shared buffers
     }
     // 5. W = sum_{sigma_j > tau} (sigma_j - tau) u_j r_j^H over A
     for (int j = tid; j < l; j += kTS)
