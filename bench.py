@@ -234,6 +234,24 @@ def oracle_sample(specs, seed, seconds, max_items=None):
     return done_slices / t_total, done_slices, done, t_total
 
 
+def oracle_single_core(seed, seconds):
+    """The same oracle sample with every BLAS/LAPACK/OpenMP pool at one thread (a child
+    process, since the pools are sized when numpy loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "from paper_1806_07247_gb300 import synth; "
+            "r = bench.oracle_sample(synth.batched_specs(512, %d), %d, %f); "
+            "print(json.dumps(r))" % (ROOT, seed, seed, seconds))
+    try:
+        res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                             text=True, timeout=max(60.0, 10 * seconds))
+        rate, sl, nt, secs = json.loads(res.stdout.strip().splitlines()[-1])
+        return {"value": rate, "unit": UNIT, "cores": 1,
+                "sample": f"tensors 0-{nt - 1} ({sl} free slices, {secs:.1f} s)"}
+    except Exception as e:  # the bench line must still print
+        return {"value": None, "error": str(e)[:200]}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -438,7 +456,8 @@ def run_tp(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(),
                                 "kind": "oracle",
                                 "sample": f"FP64 oracle prox_tnn on tensors 0-{nt - 1} of the batch "
-                                          f"({sl} free slices, {secs:.1f} s); numpy/LAPACK threads"}
+                                          f"({sl} free slices, {secs:.1f} s); numpy/LAPACK threads",
+                                "single_core": oracle_single_core(rank, args.cpu_seconds / 3)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -481,7 +500,7 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
 
 
 BF16_PEAK_TFLOPS = 1944.2        # measured dense bf16 (MEASURED_PEAKS.json, burst)
-TF32_PEAK_TFLOPS = BF16_PEAK_TFLOPS * 1.1 / 2.25   # nominal tf32 : bf16 ratio
+TF32_PEAK_TFLOPS = 1051.2   # measured: torch.matmul 8192^3 FP32 with TF32 allowed, this GB300 pool
 
 
 def tprod_leg(args, tp, synth, device):
