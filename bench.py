@@ -401,6 +401,7 @@ def run_tp(args):
     for Xl, Xp in zip(Xs, X_plain):
         d = float(torch.linalg.vector_norm(Xl - Xp) / torch.linalg.vector_norm(Xp).clamp_min(1e-30))
         dev = max(dev, d)
+    plan = plan_leg(args, tp, Ys, Xs, taus, descs, slices) if world == 1 else None
     ms_max = learned["ms"]
     value = job_throughput(slices_all, args.steps, ms_max)
     st = learned["stages"]
@@ -440,6 +441,7 @@ def run_tp(args):
                         "sketch_width_mean": float(learned["widths"][fb == 0].mean()) if (fb == 0).any() else 0.0,
                         "vs_plain": value / plain_value},
             "plain": plain_line,
+            "plan": plan,
             "dft_gbs": {"rfft": dft_gbs, "irfft": idft_gbs}}
 
     line["clocks"] = learned["clocks"]
@@ -462,6 +464,35 @@ def run_tp(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def plan_leg(args, tp, Ys, Xs, taus, descs, slices):
+    """The learned step recorded once as a CUDA graph (tp_prox_plan) and replayed: device time
+    per step, and host time per call against the direct batched call."""
+    import torch
+    direct_opts = tp.options(sync=False, method="learned")
+    plan = tp.ProxPlan(Ys, taus, outs=Xs, opts=tp.options(sync=False, method="learned"))
+    for _ in range(max(1, args.warmup)):
+        plan.run()
+    torch.cuda.synchronize()
+
+    def timed(call):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        h0 = time.perf_counter()
+        for _ in range(args.steps):
+            call()
+        host = (time.perf_counter() - h0) / args.steps
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps, host * 1e6
+
+    ms, host_us = timed(plan.run)
+    _, direct_us = timed(lambda: tp.prox_tnn_batched(Ys, taus, outs=Xs, opts=direct_opts,
+                                                     descs=descs))
+    plan.close()
+    return {"ms_per_step": ms, "value": slices / (ms / 1e3), "unit": UNIT,
+            "host_us_per_call": host_us, "direct_host_us_per_call": direct_us}
 
 
 def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):

@@ -268,6 +268,24 @@ tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count,
 tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
                                    const tp_options* opts, void* stream);
 
+/*
+ * Replayable batched prox (not in the paper): tp_prox_plan_create records the whole launch
+ * sequence of tp_prox_tnn_batched on `descs` (DFT, slice SVT launches, inverse DFT; plain or
+ * learned per opts->method) into a CUDA graph, with the job tables uploaded from page-locked
+ * copies the plan owns; tp_prox_plan_run replays it on `stream` with no host-side planning,
+ * allocation or table upload. The tensors are those of `descs` at creation: their contents
+ * may change between runs, their addresses and shapes may not. The learned method reads the
+ * device's current proposer at every run (it must exist at creation). opts->sync applies to
+ * every run (TP_ERR_NOT_CONVERGED reported as in tp_prox_tnn_batched); stage_events must be
+ * NULL. Workspace comes from the graph's own stream-ordered allocations at every replay.
+ * Destroy a plan only when no run of it is pending.
+ */
+typedef struct tp_prox_plan tp_prox_plan;
+tp_status tp_prox_plan_create(const tp_tensor_desc* descs, int64_t count, const tp_options* opts,
+                              tp_prox_plan** plan);
+tp_status tp_prox_plan_run(tp_prox_plan* plan, void* stream);
+tp_status tp_prox_plan_destroy(tp_prox_plan* plan);
+
 tp_status tp_proposer_train(const tp_tensor_desc* descs, int64_t count, int32_t steps, double lr,
                             uint64_t seed, double* mse_out, void* stream);
 tp_status tp_proposer_get(float* host_params);

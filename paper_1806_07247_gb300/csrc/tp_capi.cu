@@ -1,8 +1,10 @@
 // extern "C" entry points of libtp: argument checks, workspace planning and the launch
 // sequence of each operation (DFT of the tubes -> per-slice kernel -> inverse DFT).
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -159,11 +161,68 @@ tp_status check_dims(int64_t n1, int64_t n2, int64_t n3) {
 }
 
 // Upload a host array into the workspace (pageable copy; the source may be freed on return).
+// Page-locked host copies of the tables a captured call uploads: a CUDA graph's copy nodes
+// read their source at every replay, so the source must live as long as the graph.
+struct HostArena {
+    std::vector<void*> blocks;
+    ~HostArena() {
+        for (void* b : blocks) cudaFreeHost(b);
+    }
+};
+thread_local HostArena* t_arena = nullptr;  // set while a plan's launch sequence is captured
+
+// Page-locked staging for the job tables of ordinary calls.  A copy from pageable memory
+// waits for a driver staging buffer, i.e. for the stream to drain the work queued before
+// it, which would tie every call's host-side planning to the GPU finishing the previous
+// call.  Each upload takes a free page-locked block, copies the table into it and records an
+// event after its copy; the block is free again once that event has completed.
+struct StageBlock {
+    char* p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+};
+std::mutex g_stage_mutex;
+std::vector<StageBlock> g_stage[128];
+
+tp_status stage_copy(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    TP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return TP_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_stage_mutex);
+    std::vector<StageBlock>& pool = g_stage[dev];
+    StageBlock* pick = nullptr;
+    for (StageBlock& b : pool) {
+        if (b.busy && cudaEventQuery(b.done) == cudaSuccess) b.busy = false;
+        if (!b.busy && b.cap >= bytes && (!pick || b.cap < pick->cap)) pick = &b;
+    }
+    if (!pick) {
+        StageBlock b;
+        b.cap = std::max<size_t>(bytes, (size_t)256 << 10);
+        TP_CUDA(cudaMallocHost(reinterpret_cast<void**>(&b.p), b.cap));
+        TP_CUDA(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+        pool.push_back(b);
+        pick = &pool.back();
+    }
+    memcpy(pick->p, src, bytes);
+    TP_CUDA(cudaMemcpyAsync(dst, pick->p, bytes, cudaMemcpyHostToDevice, s));
+    TP_CUDA(cudaEventRecord(pick->done, s));
+    pick->busy = true;
+    return TP_OK;
+}
+
 template <class T>
 tp_status upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
     if (src.empty()) return TP_OK;
-    return from_cuda(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(),
-                                     cudaMemcpyHostToDevice, s));
+    const size_t bytes = sizeof(T) * src.size();
+    if (t_arena) {  // captured: the copy's source must outlive the graph
+        void* h = nullptr;
+        TP_CUDA(cudaMallocHost(&h, bytes));
+        t_arena->blocks.push_back(h);
+        memcpy(h, src.data(), bytes);
+        return from_cuda(cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, s));
+    }
+    return stage_copy(dst, src.data(), bytes, s);
 }
 
 tp_status finish(uint32_t* d_status, const Opts& o, cudaStream_t s) {
@@ -910,6 +969,73 @@ static tp_status check_descs(const tp_tensor_desc* descs, int64_t count) {
         if (!d.in) return TP_ERR_INVALID_ARG;
         if (std::max(d.n1, d.n2) > TP_MAX_SVD_DIM) return TP_ERR_UNSUPPORTED;
     }
+    return TP_OK;
+}
+
+struct tp_prox_plan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t* d_status = nullptr;
+    HostArena arena;
+    int sync = 1;
+    ~tp_prox_plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (d_status) cudaFree(d_status);
+    }
+};
+
+tp_status tp_prox_plan_create(const tp_tensor_desc* descs, int64_t count, const tp_options* opts,
+                              tp_prox_plan** plan) {
+    if (!plan) return TP_ERR_INVALID_ARG;
+    *plan = nullptr;
+    Opts o;
+    TP_TRY(resolve(opts, &o));
+    TP_TRY(check_descs(descs, count));
+    for (int64_t t = 0; t < count; ++t)
+        if (descs[t].n1 > 0 && descs[t].n2 > 0 && descs[t].n3 > 0 && !descs[t].out)
+            return TP_ERR_INVALID_ARG;
+    if (o.events) return TP_ERR_INVALID_ARG;  // stage events cannot be replayed
+    TP_TRY(prepare());
+    if (o.method == TP_METHOD_LEARNED && !proposer_ready()) return TP_ERR_INVALID_ARG;
+    std::unique_ptr<tp_prox_plan> p(new tp_prox_plan());
+    p->sync = o.sync;
+    TP_CUDA(cudaMalloc(&p->d_status, sizeof(uint32_t)));
+    cudaStream_t cap = nullptr;
+    TP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    Opts oc = o;
+    oc.sync = 0;
+    tp_status st = from_cuda(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+    if (st == TP_OK) {
+        t_arena = &p->arena;
+        st = from_cuda(cudaMemsetAsync(p->d_status, 0, sizeof(uint32_t), cap));
+        if (st == TP_OK) st = prox_batched(descs, count, oc, cap, nullptr, p->d_status);
+        t_arena = nullptr;
+        cudaGraph_t g = nullptr;
+        const tp_status end = from_cuda(cudaStreamEndCapture(cap, &g));
+        p->graph = g;
+        if (st == TP_OK) st = end;
+    }
+    if (st == TP_OK) st = from_cuda(cudaGraphInstantiate(&p->exec, p->graph, 0));
+    cudaStreamDestroy(cap);
+    if (st != TP_OK) return st;
+    *plan = p.release();
+    return TP_OK;
+}
+
+tp_status tp_prox_plan_run(tp_prox_plan* plan, void* stream) {
+    if (!plan || !plan->exec) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TP_CUDA(cudaGraphLaunch(plan->exec, s));
+    if (!plan->sync) return TP_OK;
+    uint32_t h = 0;
+    TP_CUDA(cudaMemcpyAsync(&h, plan->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    TP_CUDA(cudaStreamSynchronize(s));
+    return (h & 1u) ? TP_ERR_NOT_CONVERGED : TP_OK;
+}
+
+tp_status tp_prox_plan_destroy(tp_prox_plan* plan) {
+    delete plan;
     return TP_OK;
 }
 

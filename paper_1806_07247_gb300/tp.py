@@ -83,6 +83,10 @@ _SIGS = {
                 [ctypes.POINTER(Options), ctypes.c_void_p]),
     "tp_tqr": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64] * 3 +
                [ctypes.POINTER(Options), ctypes.c_void_p]),
+    "tp_prox_plan_create": (ctypes.c_int, [ctypes.POINTER(TensorDesc), ctypes.c_int64,
+                                           ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_void_p)]),
+    "tp_prox_plan_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "tp_prox_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "tp_proposer_get": (ctypes.c_int, [ctypes.c_void_p]),
     "tp_proposer_set": (ctypes.c_int, [ctypes.c_void_p]),
 }
@@ -378,6 +382,36 @@ def prox_tnn_batched_host(Ys, taus, outs=None, opts: Options | None = None, stre
     _check(lib().tp_prox_tnn_batched_host(d, len(Ys), ctypes.byref(o), _stream(stream)),
            "tp_prox_tnn_batched_host")
     return outs
+
+
+class ProxPlan:
+    """A recorded batched prox_tnn (tp_prox_plan_create): run() replays it as one CUDA graph on
+    the same tensors (whose contents may change between runs)."""
+
+    def __init__(self, Ys, taus, outs=None, opts: Options | None = None):
+        self.Ys = [_prep(Y, "Y") for Y in Ys]
+        self.Xs = [empty(*Y.shape, device=Y.device) for Y in self.Ys] if outs is None else outs
+        self._descs = make_descs(self.Ys, self.Xs, taus)
+        o = opts or options()
+        h = ctypes.c_void_p()
+        _check(lib().tp_prox_plan_create(self._descs, len(self.Ys), ctypes.byref(o),
+                                         ctypes.byref(h)), "tp_prox_plan_create")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib().tp_prox_plan_run(self._h, _stream(stream)), "tp_prox_plan_run")
+        return self.Xs
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().tp_prox_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def proposer_train(Ys, taus, steps: int = 300, lr: float = 3e-3, seed: int = 0, stream=None) -> float:

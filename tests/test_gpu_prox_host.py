@@ -95,3 +95,39 @@ def test_host_rejects_bad_args(tp):
     d[0].n1 = -1
     assert tp.lib().tp_prox_tnn_batched_host(d, 1, tp.ctypes.byref(o), None) == tp.TP_ERR_INVALID_ARG
     assert tp.lib().tp_prox_tnn_batched_host(d, 0, tp.ctypes.byref(o), None) == tp.TP_OK
+
+
+# ----------------------------------------------------------------------------- replayable plans
+@pytest.mark.parametrize("method", ["jacobi", "learned"])
+def test_plan_replays_the_batched_call(tp, batch, method):
+    """A recorded plan gives the batched call's result, follows new input contents, and
+    reports through the same status path."""
+    Ys, taus = batch
+    Ys, taus = Ys[:24], taus[:24]
+    if method == "learned":
+        tp.proposer_train([tp.to_device(Y) for Y in Ys], taus, steps=200, seed=1)
+    dY = [tp.to_device(Y) for Y in Ys]
+    plan = tp.ProxPlan(dY, taus, opts=tp.options(method=method))
+    ref = tp.prox_tnn_batched(dY, taus, opts=tp.options(method=method))
+    for _ in range(2):
+        out = plan.run()
+        worst = max(rel(tp.to_numpy(a), tp.to_numpy(b)) for a, b in zip(out, ref))
+        assert worst < 1e-6, worst
+    # new contents in the same tensors
+    for Y in dY:
+        Y.mul_(0.5)
+    out = plan.run()
+    for i in (0, 11, 23):
+        assert rel(tp.to_numpy(out[i]), O.prox_tnn(0.5 * Ys[i].astype(np.float64), taus[i])) < \
+            (TOL_FP32 if method == "jacobi" else 1e-4)
+    plan.close()
+
+
+def test_plan_rejects_stage_events(tp):
+    Y = tp.to_device(np.ones((4, 4, 3), dtype=np.float32, order="F"))
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(tp.STAGE_EVENTS)]
+    for e in evs:
+        e.record()
+    with pytest.raises(tp.TpError) as e:
+        tp.ProxPlan([Y], [0.1], opts=tp.options(stage_events=evs))
+    assert e.value.status == tp.TP_ERR_INVALID_ARG
