@@ -373,6 +373,8 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         bytes += 4 * Workspace::round(sizeof(int32_t) * slices);  // ell, flags, counts, order
         bytes += Workspace::round(sizeof(int32_t) * kSketchClasses * slices);  // sketch queues
         bytes += Workspace::round(sizeof(int32_t) * 2 * kSketchClasses);       // queue counters
+        bytes += 3 * Workspace::round(sizeof(int32_t) * slices);  // extra power its, 2 retry lists
+        bytes += Workspace::round(sizeof(int32_t) * 4);           // retry list lengths, counters
     }
     if (train) bytes += Workspace::round(sizeof(float) * proposer_fit_scratch_floats((int)slices));
     Workspace ws(s);
@@ -386,6 +388,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     float* feat = nullptr;
     int32_t *ell = nullptr, *flags = nullptr, *counts = nullptr, *d_order = nullptr;
     int32_t *d_queues = nullptr, *d_qcount = nullptr;
+    int32_t *d_extra = nullptr, *d_retry = nullptr, *d_rcount = nullptr;
     SvdJob* d_nat = nullptr;
     if (need_feat) {
         d_nat = ws.take<SvdJob>(slices);
@@ -396,6 +399,9 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         d_order = ws.take<int32_t>(slices);
         d_queues = ws.take<int32_t>((size_t)kSketchClasses * slices);
         d_qcount = ws.take<int32_t>(2 * kSketchClasses);
+        d_extra = ws.take<int32_t>(slices);
+        d_retry = ws.take<int32_t>(2 * (size_t)slices);
+        d_rcount = ws.take<int32_t>(4);
         TP_TRY(ws.check());
     }
     FftBatch fwd, inv;
@@ -467,28 +473,53 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
                                   s));
         int sms = 0;
         TP_TRY(sm_count(&sms));
-        for (int c = 0; c < caps.n; ++c) {
-            const int per_sm = sketch_blocks_per_sm(caps.bytes[c]);
-            if (per_sm <= 0) return TP_ERR_CUDA;
+        // retries: two rounds over lists of the slices that failed a check but are worth
+        // another attempt (more power iterations or a wider sketch), in the largest class
+        constexpr int kRetryRounds = 2;
+        constexpr int kRetryMinDim = 96;
+        const size_t retry_smem = caps.bytes[caps.n - 1];
+        TP_CUDA(cudaMemsetAsync(d_extra, 0, sizeof(int32_t) * slices, s));
+        TP_CUDA(cudaMemsetAsync(d_rcount, 0, sizeof(int32_t) * 4, s));
+        auto base = [&]() {
             SketchParams sp;
-            sp.order = d_queues + (size_t)c * slices;
-            sp.queue_len = d_qcount + 2 * c;
-            sp.queue_next = d_qcount + 2 * c + 1;
             sp.ell = ell;
             sp.flag = flags;
             sp.count = counts;
             sp.seed = 0x9e3779b9u;
             sp.power_iters = 1;
-            sp.retries = 2;
+            sp.extra_power = d_extra;
             sp.resid_tol = 1e-5f;
+            return sp;
+        };
+        for (int c = 0; c < caps.n; ++c) {
+            const int per_sm = sketch_blocks_per_sm(caps.bytes[c]);
+            if (per_sm <= 0) return TP_ERR_CUDA;
+            SketchParams sp = base();
+            sp.order = d_queues + (size_t)c * slices;
+            sp.queue_len = d_qcount + 2 * c;
+            sp.queue_next = d_qcount + 2 * c + 1;
             sp.smem_bytes = (int)caps.bytes[c];
             const int64_t grid = std::min<int64_t>(slices, (int64_t)sms * per_sm);
             TP_CUDA(launch_sketch_svt(d_nat, (int)grid, caps.bytes[c], sp, s));
         }
+        const int retry_per_sm = sketch_blocks_per_sm(retry_smem);
+        if (retry_per_sm <= 0) return TP_ERR_CUDA;
+        for (int round = 0; round < kRetryRounds; ++round) {
+            int32_t* list = d_retry + (size_t)(round & 1) * slices;
+            TP_CUDA(launch_sketch_collect(d_nat, (int)slices, flags, ell, d_extra, kRetryMinDim,
+                                          (int)retry_smem, list, d_rcount + round, s));
+            SketchParams sp = base();
+            sp.retry_launch = 1;
+            sp.order = list;
+            sp.queue_len = d_rcount + round;
+            sp.queue_next = d_rcount + 2 + round;
+            sp.smem_bytes = (int)retry_smem;
+            const int64_t grid = std::min<int64_t>(slices, (int64_t)sms * retry_per_sm);
+            TP_CUDA(launch_sketch_svt(d_nat, (int)grid, retry_smem, sp, s));
+        }
         TP_TRY(o.mark(3, s));
         if (o.slice_flags_out)
-            TP_CUDA(cudaMemcpyAsync(o.slice_flags_out, flags, sizeof(int32_t) * slices,
-                                    cudaMemcpyDeviceToDevice, s));
+            TP_CUDA(launch_flags01(flags, o.slice_flags_out, (int)slices, s));
         if (o.sketch_width_out)
             TP_CUDA(cudaMemcpyAsync(o.sketch_width_out, ell, sizeof(int32_t) * slices,
                                     cudaMemcpyDeviceToDevice, s));

@@ -128,12 +128,14 @@ struct SketchParams {
     const int32_t* order = nullptr;  // CTA (or queue position) -> job index (nullptr: identity)
     const int32_t* queue_len = nullptr;  // persistent mode: number of entries of `order`
     int32_t* queue_next = nullptr;       // persistent mode: work counter (zero at launch)
-    const int32_t* ell;   // per job: sketch width (0: go to the full Jacobi SVD)
+    int32_t* ell;         // per job: sketch width (0: go to the full Jacobi SVD); a wider
+                          // retry raises it
     int32_t* flag;        // per job: 0 = W written by the sketch path, 1 = needs Jacobi
     int32_t* count;       // per job: #{sigma > tau} on success (optional)
     uint32_t seed;
     int power_iters;
-    int retries = 0;      // extra attempts with two more power iterations each (check a passed)
+    int32_t* extra_power = nullptr;  // per job: extra power iterations of a retry
+    int retry_launch = 0;            // 1: `order` is a retry list (per-slice power iterations)
     float resid_tol;
     int smem_bytes;       // dynamic shared memory of the launch
 };
@@ -153,6 +155,12 @@ struct SketchCaps {
 cudaError_t launch_sketch_bin(const SvdJob* jobs, const int32_t* sorted, int n, const int32_t* ell,
                               int32_t* flag, const SketchCaps& caps, int32_t* queues,
                               int32_t* counts, cudaStream_t s);
+// Queues the failed slices worth another sketch (see tp_sketch.cu) into `list`.
+cudaError_t launch_sketch_collect(const SvdJob* jobs, int n, int32_t* flag, int32_t* ell,
+                                  int32_t* extra, int min_dim, int smem, int32_t* list,
+                                  int32_t* len, cudaStream_t s);
+// out[j] = (flags[j] != 0): the per-slice fallback flags as 0 / 1.
+cudaError_t launch_flags01(const int32_t* flags, int32_t* out, int n, cudaStream_t s);
 // Resident CTAs of the sketch kernel per SM at this dynamic shared memory (0 on error).
 int sketch_blocks_per_sm(size_t smem);
 size_t features_smem_bytes(int n1, int n2);

@@ -460,6 +460,9 @@ struct SketchShared {
 };
 
 // The whole sketch SVT of one slice (steps 2-5 of the file comment) by the calling CTA.
+// RETRY: the slice comes from a retry list and takes its extra power iterations from
+// P.extra_power (a first attempt uses P.power_iters alone, a block-uniform loop bound).
+template <bool RETRY>
 __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const SketchParams& P,
                            float4* smem4, SketchShared& sh) {
     int& s_flag = sh.flag;
@@ -469,37 +472,29 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     const SvdJob J = jobs[job];
     const int n1 = J.n1, n2 = J.n2, nm = max(n1, n2);
     const bool real = J.real_slice != 0;
-    int l = P.ell[job];
+    const int l = P.ell[job];
+    // power iterations: a first attempt reads the launch parameter wherever it needs it
+    const int q_retry = RETRY ? P.power_iters + P.extra_power[job] : 0;
+#define TP_SKETCH_Q (RETRY ? q_retry : P.power_iters)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (l <= 0 || l >= min(n1, n2) || l > kLMax ||
         sketch_smem_need(n1, n2, l) > (size_t)P.smem_bytes) {
         if (tid == 0) P.flag[job] = 1;
         return;
     }
-    const float2* A = J.A;
-
-    // Steps 2-4 run up to 1 + P.retries times.  A slice whose sketch reached below tau (check
-    // a) but failed the residual or deflation check is sketched again with two more power
-    // iterations; one whose sketch did not reach below tau (the rank was underestimated) is
-    // sketched again 4 columns wider, if that still fits the CTA's shared memory.  Any other
-    // failure leaves the slice to the Jacobi path.
-    float2 *U = nullptr, *R = nullptr, *V = nullptr, *G = nullptr, *C = nullptr;
-    float2 *xv = nullptr, *yv = nullptr, *coef = nullptr;
-    float *sig = nullptr, *fac = nullptr;
-    int k = 0, q = P.power_iters;
-    for (int attempt = 0;; ++attempt) {
     float2* B0 = reinterpret_cast<float2*>(smem4);  // three max(n1, n2) x l buffers
     float2* B1 = B0 + (size_t)nm * l;
     float2* B2 = B1 + (size_t)nm * l;
-    V = B2 + (size_t)nm * l;                        // l x l
-    G = V + (size_t)l * l;                          // l x l
-    C = G + (size_t)l * l;                          // l x l
-    xv = C + (size_t)l * l;                         // n2
-    yv = xv + n2;                                   // n1
-    coef = yv + n1;                                 // 2 kLMax
-    sig = reinterpret_cast<float*>(coef + 2 * kLMax);
-    fac = sig + kLMax;
-    bool below = false;
+    float2* V = B2 + (size_t)nm * l;                // l x l
+    float2* G = V + (size_t)l * l;                  // l x l
+    float2* C = G + (size_t)l * l;                  // l x l
+    float2* xv = C + (size_t)l * l;                 // n2
+    float2* yv = xv + n2;                           // n1
+    float2* coef = yv + n1;                         // 2 kLMax
+    float* sig = reinterpret_cast<float*>(coef + 2 * kLMax);
+    float* fac = sig + kLMax;
+    const float2* A = J.A;
+
     // 2. range finder with power iterations; shifted CholeskyQR3 orthonormalisations.  bq holds
     // the current Q (n1 x l), bz the current Z (n2 x l), bs is scratch.
     float2* bq = B0;
@@ -520,10 +515,10 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     __syncthreads();
     mult_a(A, n1, n2, real, bs, bq, l);
     __syncthreads();
-    float2* r = orth3(bq, bs, n1, l, G, C, &s_flag, q > 0 ? 2 : 3);
+    float2* r = orth3(bq, bs, n1, l, G, C, &s_flag, TP_SKETCH_Q > 0 ? 2 : 3);
     bool ok = r != nullptr;
     if (ok && r != bq) { bs = bq; bq = r; }
-    for (int it = 0; ok && it < q; ++it) {
+    for (int it = 0; ok && it < TP_SKETCH_Q; ++it) {
         mult_ah(A, n1, n2, real, bq, bz, l);
         r = orth3(bz, bs, n2, l, G, C, &s_flag, 2);
         ok = r != nullptr;
@@ -558,9 +553,10 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         __syncthreads();
     }
     float smin = 3.4e38f, smax = 0.f;
-    k = 0;
-    U = bs;  // n1 x l
-    R = bz;  // n2 x l: D, then D / sigma on the kept columns
+    int k = 0;
+
+    float2* U = bs;  // n1 x l
+    float2* R = bz;  // n2 x l: D, then D / sigma on the kept columns
     float2* T = bq;  // n1 x l: A R for the residuals (Q is dead once U is formed)
     if (ok) {
         for (int j = warp; j < l; j += kTS / 32) {
@@ -591,7 +587,10 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
             k += ((double)sig[j] > J.tau);
         }
         ok = !((double)smin > J.tau);
-        below = ok;
+        if (!ok) {  // the rank was underestimated
+            if (tid == 0) P.flag[job] = 3;
+            return;
+        }
     }
     if (ok) {
         for (int j = tid; j < l; j += kTS) fac[j] = ((double)sig[j] > J.tau) ? 1.f / sig[j] : 0.f;
@@ -693,21 +692,10 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         }
         ok = (double)est < 0.8 * J.tau;
     }
-    if (ok) break;
-    bool again = attempt < P.retries;
-    if (again && below) {
-        q += 2;
-    } else if (again) {
-        const int l2 = l + 4;
-        again = l2 < min(n1, n2) && l2 <= kLMax &&
-                sketch_smem_need(n1, n2, l2) <= (size_t)P.smem_bytes;
-        if (again) l = l2;
-    }
-    if (!again) {
+    if (!ok) {
         if (tid == 0) P.flag[job] = 1;
         return;
-    }
-    __syncthreads();  // the next attempt rewrites the shared buffers
+#undef TP_SKETCH_Q
     }
     // 5. W = sum_{sigma_j > tau} (sigma_j - tau) u_j r_j^H over A
     for (int j = tid; j < l; j += kTS)
@@ -758,12 +746,13 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
 // One slice per CTA (P.queue_next == nullptr, CTA b takes P.order[b]), or a persistent grid
 // that takes slices P.order[i] from a work counter until the queue of *P.queue_len is empty;
 // the queue is ordered largest slice first, so the tail is made of small slices.
+template <bool RETRY>
 __global__ void __launch_bounds__(kTS, 4) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
                                                            SketchParams P) {
     extern __shared__ float4 smem4[];
     __shared__ SketchShared sh;
     if (!P.queue_next) {
-        sketch_one(jobs, P.order ? P.order[blockIdx.x] : (int)blockIdx.x, P, smem4, sh);
+        sketch_one<RETRY>(jobs, P.order ? P.order[blockIdx.x] : (int)blockIdx.x, P, smem4, sh);
         return;
     }
     for (;;) {
@@ -771,7 +760,7 @@ __global__ void __launch_bounds__(kTS, 4) sketch_svt_kernel(const SvdJob* __rest
         __syncthreads();
         const int item = sh.item;
         if (item >= *P.queue_len) break;
-        sketch_one(jobs, P.order[item], P, smem4, sh);
+        sketch_one<RETRY>(jobs, P.order[item], P, smem4, sh);
         __syncthreads();  // the CTA is done with this slice's shared state
     }
 }
@@ -1046,6 +1035,53 @@ cudaError_t launch_proposer(const float* feat, const SvdJob* jobs, int njobs, in
     return cudaGetLastError();
 }
 
+// Between sketch rounds: every slice that failed (flag 1 or 3) and has min(n1, n2) >=
+// min_dim (its Jacobi SVD would cost much more than another sketch) is queued for another
+// attempt -- with two more power iterations if its sketch reached below tau (flag 1), or 4
+// columns wider if the rank was underestimated (flag 3) and the wider sketch fits `smem`;
+// it is marked 2 (pending).  Any other failed slice is marked 4 (left to the Jacobi path).
+__global__ void __launch_bounds__(1024) sketch_collect_kernel(const SvdJob* __restrict__ jobs,
+                                                              int n, int32_t* __restrict__ flag,
+                                                              int32_t* __restrict__ ell,
+                                                              int32_t* __restrict__ extra,
+                                                              int min_dim, int smem,
+                                                              int32_t* list, int32_t* len) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int f = flag[j];
+        if (f != 1 && f != 3) continue;
+        const int n1 = jobs[j].n1, n2 = jobs[j].n2, l = ell[j];
+        bool again = min(n1, n2) >= min_dim;
+        if (again && f == 1) {
+            extra[j] += 2;
+        } else if (again) {
+            again = l + 4 < min(n1, n2) && l + 4 <= kLMax &&
+                    sketch_smem_need(n1, n2, l + 4) <= (size_t)smem;
+            if (again) ell[j] = l + 4;
+        }
+        flag[j] = again ? 2 : 4;
+        if (again) list[atomicAdd(len, 1)] = j;
+    }
+}
+
+cudaError_t launch_sketch_collect(const SvdJob* jobs, int n, int32_t* flag, int32_t* ell,
+                                  int32_t* extra, int min_dim, int smem, int32_t* list,
+                                  int32_t* len, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    sketch_collect_kernel<<<1, 1024, 0, s>>>(jobs, n, flag, ell, extra, min_dim, smem, list, len);
+    return cudaGetLastError();
+}
+
+__global__ void flags01_kernel(const int32_t* __restrict__ in, int32_t* __restrict__ out, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = in[j] != 0 ? 1 : 0;
+}
+
+cudaError_t launch_flags01(const int32_t* flags, int32_t* out, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    flags01_kernel<<<(n + 255) / 256, 256, 0, s>>>(flags, out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sketch_bin(const SvdJob* jobs, const int32_t* sorted, int n, const int32_t* ell,
                               int32_t* flag, const SketchCaps& caps, int32_t* queues,
                               int32_t* counts, cudaStream_t s) {
@@ -1054,13 +1090,16 @@ cudaError_t launch_sketch_bin(const SvdJob* jobs, const int32_t* sorted, int n, 
     return cudaGetLastError();
 }
 
+// Both instantiations have the same resources; the first stands for them.
 int sketch_blocks_per_sm(size_t smem) {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(sketch_svt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return 0;
+    for (const void* fn : {reinterpret_cast<const void*>(sketch_svt_kernel<false>),
+                           reinterpret_cast<const void*>(sketch_svt_kernel<true>)})
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+            return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sketch_svt_kernel, kTS, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sketch_svt_kernel<false>, kTS, smem) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -1069,12 +1108,14 @@ int sketch_blocks_per_sm(size_t smem) {
 cudaError_t launch_sketch_svt(const SvdJob* jobs, int ncta, size_t smem, const SketchParams& p,
                               cudaStream_t s) {
     if (ncta <= 0) return cudaSuccess;
+    const void* fn = p.retry_launch ? reinterpret_cast<const void*>(sketch_svt_kernel<true>)
+                                    : reinterpret_cast<const void*>(sketch_svt_kernel<false>);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sketch_svt_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sketch_svt_kernel<<<ncta, kTS, smem, s>>>(jobs, p);
+    if (p.retry_launch) sketch_svt_kernel<true><<<ncta, kTS, smem, s>>>(jobs, p);
+    else sketch_svt_kernel<false><<<ncta, kTS, smem, s>>>(jobs, p);
     return cudaGetLastError();
 }
 
