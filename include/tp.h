@@ -91,8 +91,9 @@ typedef struct tp_options {
     int32_t* slice_flags_out; /* optional DEVICE array, one int per directly computed slice
                             (same indexing as sweeps_out): with TP_METHOD_LEARNED, 0 if the
                             sketch path finished the slice, 1 if it fell back to Jacobi */
-    int32_t* sketch_width_out; /* optional DEVICE array, same indexing: the sketch width the
-                            proposer chose (0: the slice went straight to Jacobi) */
+    int32_t* sketch_width_out; /* optional DEVICE array, same indexing: the sketch width of
+                            the slice's last attempt (the proposer's choice, 4 more after a
+                            wider retry; 0: the slice went straight to Jacobi) */
 } tp_options;
 
 #define TP_STAGE_EVENTS 6
@@ -106,8 +107,10 @@ typedef struct tp_options {
  *   triplets; the slice is accepted only if the smallest computed singular value is below
  *   tau, the kept triplets' residuals ||A r - sigma u|| (times their weight (sigma - tau)/sigma
  *   in the result) are below 1e-5 sigma_max and the
- *   deflated matrix's norm is estimated below 0.8 tau; every other slice is recomputed by
- *   the Jacobi path. Error target 1e-4 relative (Frobenius) against the exact prox.
+ *   deflated matrix's norm is estimated below 0.8 tau. A slice with min(n1, n2) >= 96 that
+ *   fails is sketched again (up to twice) with two more power iterations, or 4 columns wider
+ *   if the rank was underestimated; every other failed slice is recomputed by the Jacobi
+ *   path. Error target 1e-4 relative (Frobenius) against the exact prox.
  */
 #define TP_METHOD_JACOBI 0
 #define TP_METHOD_LEARNED 1
