@@ -432,7 +432,9 @@ def run_tp(args):
                        "Jacobi fallback", "tensors": len(specs), "free_slices": slices,
                        "seed": rank, "input_bytes": nbytes,
                        "l2": "inputs larger than L2 (%.2f GB in + out per step)" % (2 * nbytes / 1e9)},
-            "gpu_launches": (5 + groups) * args.steps,
+            # per step: DFT, features, MLP, binning, 4 sketch classes, 2 x (collect + retry),
+            # the Jacobi groups, inverse DFT
+            "gpu_launches": (13 + groups) * args.steps,
             "roofline": roof,
             "stages_ms": st,
             "learned": {"fallback_fraction": float((fb == 1).mean()),
