@@ -495,7 +495,9 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     float* fac = sig + kLMax;
     const float2* A = J.A;
 
-    // 2. range finder with power iterations; shifted CholeskyQR3 orthonormalisations.  bq holds
+    // 2. range finder with power iterations; shifted CholeskyQR orthonormalisations of two
+    // passes (shifted, then plain: after the shifted pass the basis is well conditioned, so one
+    // plain pass leaves it orthonormal to working accuracy, which check (b) confirms).  bq holds
     // the current Q (n1 x l), bz the current Z (n2 x l), bs is scratch.
     float2* bq = B0;
     float2* bz = B1;
@@ -526,7 +528,7 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         if (r != bz) { bs = bz; bz = r; }
         mult_a(A, n1, n2, real, bz, bq, l);
         __syncthreads();
-        r = orth3(bq, bs, n1, l, G, C, &s_flag);
+        r = orth3(bq, bs, n1, l, G, C, &s_flag, 2);
         ok = r != nullptr;
         if (ok && r != bq) { bs = bq; bq = r; }
     }
