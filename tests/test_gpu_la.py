@@ -145,3 +145,30 @@ def test_tqr_real_slices_and_empty(tp):
     for shape in [(0, 3, 2), (3, 0, 2), (3, 3, 0)]:
         Q, R = tp.tqr(tp.to_device(np.zeros(shape, dtype=np.float32, order="F")))
         assert Q.numel() == 0 or R.numel() == 0
+
+
+# ----------------------------------------------------------------------------- limits
+@pytest.mark.parametrize("n,n3", [(512, 2), (300, 3), (4, 1024), (33, 1)])
+def test_tinv_limits(tp, n, n3):
+    """The largest slice (n = TP_MAX_SVD_DIM, 16 rows per lane, global-memory path), a slice
+    just past the shared-memory path, the longest tubes (n3 = TP_MAX_N3, 513 slices)."""
+    A = synth.shifted_square(n, n3, seed=n + n3)
+    B = tp.to_numpy(tp.tinv(tp.to_device(A)))
+    assert rel(B, O.tinv_fourier(A.astype(np.float64))) < TOL_FP32
+
+
+@pytest.mark.parametrize("econ", [False, True])
+@pytest.mark.parametrize("n1,n2,n3", [(512, 128, 2), (96, 512, 2), (6, 4, 1024)])
+def test_tqr_limits(tp, n1, n2, n3, econ):
+    A = synth.gaussian(n1, n2, n3, seed=n1 + n2) if n1 >= 2 * n2 else None
+    if A is None:  # wide or small: a well-conditioned leading block
+        A = synth.gaussian(n1, n2, n3, seed=n1 + n2) * np.float32(0.05)
+        m = min(n1, n2)
+        A[:m, :m, :] += synth.shifted_square(m, n3, seed=7)
+        A = np.asfortranarray(A)
+    Q, R = tp.tqr(tp.to_device(A), econ=econ)
+    Q, R = tp.to_numpy(Q), tp.to_numpy(R)
+    m = min(n1, n2)
+    Qo, Ro = O.tqr(A.astype(np.float64))
+    assert rel(R, Ro[:R.shape[0]]) < TOL_FP32
+    assert rel(Q[:, :m], Qo[:, :m]) < TOL_FP32
