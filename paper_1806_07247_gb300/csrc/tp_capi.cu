@@ -374,7 +374,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         bytes += Workspace::round(sizeof(int32_t) * kSketchClasses * slices);  // sketch queues
         bytes += Workspace::round(sizeof(int32_t) * 2 * kSketchClasses);       // queue counters
         bytes += 3 * Workspace::round(sizeof(int32_t) * slices);  // extra power its, 2 retry lists
-        bytes += Workspace::round(sizeof(int32_t) * 4);           // retry list lengths, counters
+        bytes += Workspace::round(sizeof(int32_t) * 2 * kSketchRetryRounds);  // retry counters
     }
     if (train) bytes += Workspace::round(sizeof(float) * proposer_fit_scratch_floats((int)slices));
     Workspace ws(s);
@@ -401,7 +401,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         d_qcount = ws.take<int32_t>(2 * kSketchClasses);
         d_extra = ws.take<int32_t>(slices);
         d_retry = ws.take<int32_t>(2 * (size_t)slices);
-        d_rcount = ws.take<int32_t>(4);
+        d_rcount = ws.take<int32_t>(2 * kSketchRetryRounds);
         TP_TRY(ws.check());
     }
     FftBatch fwd, inv;
@@ -475,16 +475,17 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         TP_TRY(sm_count(&sms));
         // retries: two rounds over lists of the slices that failed a check but are worth
         // another attempt (more power iterations or a wider sketch), in the largest class
-        constexpr int kRetryRounds = 2;
+        constexpr int kRetryRounds = kSketchRetryRounds;
         constexpr int kRetryMinDim = 96;
         const size_t retry_smem = caps.bytes[caps.n - 1];
         TP_CUDA(cudaMemsetAsync(d_extra, 0, sizeof(int32_t) * slices, s));
-        TP_CUDA(cudaMemsetAsync(d_rcount, 0, sizeof(int32_t) * 4, s));
+        TP_CUDA(cudaMemsetAsync(d_rcount, 0, sizeof(int32_t) * 2 * kRetryRounds, s));
         auto base = [&]() {
             SketchParams sp;
             sp.ell = ell;
             sp.flag = flags;
             sp.count = counts;
+            sp.njobs = (int)slices;
             sp.seed = 0x9e3779b9u;
             sp.power_iters = 1;
             sp.extra_power = d_extra;
@@ -507,12 +508,12 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         for (int round = 0; round < kRetryRounds; ++round) {
             int32_t* list = d_retry + (size_t)(round & 1) * slices;
             TP_CUDA(launch_sketch_collect(d_nat, (int)slices, flags, ell, d_extra, kRetryMinDim,
-                                          (int)retry_smem, list, d_rcount + round, s));
+                                          (int)retry_smem, list, d_rcount + 2 * round, s));
             SketchParams sp = base();
             sp.retry_launch = 1;
             sp.order = list;
-            sp.queue_len = d_rcount + round;
-            sp.queue_next = d_rcount + 2 + round;
+            sp.queue_len = d_rcount + 2 * round;       // round r: length, then work counter
+            sp.queue_next = d_rcount + 2 * round + 1;
             sp.smem_bytes = (int)retry_smem;
             const int64_t grid = std::min<int64_t>(slices, (int64_t)sms * retry_per_sm);
             TP_CUDA(launch_sketch_svt(d_nat, (int)grid, retry_smem, sp, s));

@@ -134,6 +134,7 @@ struct SketchParams {
     int32_t* count;       // per job: #{sigma > tau} on success (optional)
     uint32_t seed;
     int power_iters;
+    int njobs = 0;                   // jobs in the launch's job array (bounds queue entries)
     int32_t* extra_power = nullptr;  // per job: extra power iterations of a retry
     int retry_launch = 0;            // 1: `order` is a retry list (per-slice power iterations)
     float resid_tol;
@@ -145,6 +146,8 @@ __host__ __device__ inline size_t sketch_smem_need(int n1, int n2, int l) {
     return sizeof(float2) * (3 * nm * l + (size_t)3 * l * l + (size_t)n1 + n2 + 2 * kSketchMaxL) +
            sizeof(float) * (2 * kSketchMaxL) + 64;
 }
+// Retry rounds of the sketch path (each: collect the failed slices, sketch them again).
+constexpr int kSketchRetryRounds = 4;
 // Size classes of the sketch kernel's queues: shared memory bytes per CTA, increasing.
 constexpr int kSketchClasses = 4;
 struct SketchCaps {

@@ -762,7 +762,8 @@ __global__ void __launch_bounds__(kTS, 4) sketch_svt_kernel(const SvdJob* __rest
         __syncthreads();
         const int item = sh.item;
         if (item >= *P.queue_len) break;
-        sketch_one<RETRY>(jobs, P.order[item], P, smem4, sh);
+        const int job = P.order[item];
+        if (job >= 0 && job < P.njobs) sketch_one<RETRY>(jobs, job, P, smem4, sh);
         __syncthreads();  // the CTA is done with this slice's shared state
     }
 }
