@@ -26,6 +26,12 @@ The JSON line also carries:
   factor        tensor inverse (Def. 2.4) on 128x128x302 and economy t-QR (Thm. 2.4) on
                 128x64x302 (152 independent slices each, one per SM), slices/s and the slice
                 kernel's FP32 flop rate;
+  plain.autotuned  the plain path again after tp_autotune_jacobi chose the Jacobi CTA shape
+                by timing its candidates on this batch (the shape stays set for the learned
+                step, whose fallback slices use it; the other legs run at the default);
+  stream        a bounded sample of the mixed call stream (prox_tnn and tprod calls on
+                tensors up to 512x512x256): every call on its own in FP32 with Jacobi, against
+                windows of calls as replayed learned batched plans plus BF16x3 tprod;
   cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
 
 `--impl reference` times the FP64 oracle itself (host cores) on the same workload.
@@ -66,6 +72,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-factor", action="store_true")
     p.add_argument("--no-trpca", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-stream", action="store_true")
+    p.add_argument("--stream-calls", type=int, default=48)
+    p.add_argument("--stream-window", type=int, default=16)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--train-batches", type=int, default=4,
                    help="512-tensor batches (other seeds) that label the proposer's training set")
@@ -159,9 +169,11 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- workload
-def svd_launch_groups(shapes):
-    """Kernel instantiations one batched prox call launches (mirrors the library's
-    slice planner: lanes per column pair, float4 pairs per lane, shared or global)."""
+def svd_launch_groups(shapes, shape=None):
+    """Kernel launches of the Jacobi stage of one batched prox call (mirrors the library's
+    slice planner under a Jacobi CTA shape: lanes per column pair, float4 pairs per lane,
+    shared or global memory, and the CTA size when launches are split by it)."""
+    shape = shape or {"target_lane_pairs": 5, "max_warps": 32, "split_launches": 0}
     groups = set()
     for n1, n2 in shapes:
         m, n = max(n1, n2), min(n1, n2)
@@ -170,7 +182,7 @@ def svd_launch_groups(shapes):
             e2 = (m + 2 * cand - 1) // (2 * cand)
             if e2 > 8:
                 continue
-            score = (2 * cand * e2 - m) / m + 0.03 * abs(e2 - 5.0)
+            score = (2 * cand * e2 - m) / m + 0.03 * abs(e2 - shape["target_lane_pairs"])
             if score < best:
                 best, lp = score, cand
         e2 = (m + 2 * lp - 1) // (2 * lp)
@@ -178,8 +190,21 @@ def svd_launch_groups(shapes):
         ld = 2 * lp * e2
         aux = (6 * n * 4 + 256 + (m + 1) * 4 + 20 * m + 15) & ~15
         in_smem = n * ld * 8 + aux <= 227 * 1024 - 1024
-        groups.add((in_smem, lp, maxe2))
+        threads = 0
+        if shape["split_launches"]:
+            pairs, spw = (n + 1) // 2, 32 // lp
+            wmax = min(shape["max_warps"], 16 if maxe2 >= 8 else 32)
+            passes = -(-pairs // (wmax * spw))
+            threads = 32 * max(2, -(-pairs // (passes * spw)))
+        groups.add((in_smem, lp, maxe2, threads))
     return len(groups)
+
+
+# Kernel launches of one learned batched prox call besides the Jacobi groups: the tube DFT,
+# features, proposer MLP, binning, one persistent sketch launch per size class, a collect and
+# a sketch launch per retry round, the inverse DFT.
+SKETCH_CLASSES, SKETCH_RETRY_ROUNDS = 4, 4
+LEARNED_FIXED_LAUNCHES = 4 + SKETCH_CLASSES + 2 * SKETCH_RETRY_ROUNDS + 1
 
 
 def make_batch(tp, synth, count, seed, device):
@@ -364,7 +389,6 @@ def run_tp(args):
     specs, Ys, taus, slices, nbytes, shapes = make_batch(tp, synth, args.count, rank, device)
     Xs = [tp.empty(*Y.shape, device=device) for Y in Ys]
     descs = tp.make_descs(Ys, Xs, taus)
-    groups = svd_launch_groups([(a, b) for a, b, _ in shapes])
     spec_bytes = sum(8 * a * b * (c // 2 + 1) for a, b, c in shapes)
 
     # --- plain FP32 path (one-sided Jacobi on every slice)
@@ -382,6 +406,29 @@ def run_tp(args):
                                "frac": jflops / (jt / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
                                "model": "sum over slices of sweeps*n(n-1)/2*40*m flops",
                                "sweeps_mean": float(plain["sweeps"].mean())}}
+
+    # --- autotuned plain path: the Jacobi CTA shape chosen by timing the candidates on this
+    # batch's own Fourier slices; the chosen shape stays set for the learned step's fallback
+    shape = None
+    if not args.no_autotune:
+        t_at = time.perf_counter()
+        shape, tune_def_ms, tune_best_ms = tp.autotune_jacobi(Ys, taus, reps=2)
+        t_at = time.perf_counter() - t_at
+        tuned = time_prox(tp, args, Ys, Xs, taus, descs, "jacobi", world, barrier, device)
+        tuned_value = job_throughput(slices_all, args.steps, tuned["ms"])
+        tdev = 0.0
+        for Xt, Xp in zip(Xs, X_plain):
+            d = float(torch.linalg.vector_norm(Xt - Xp) /
+                      torch.linalg.vector_norm(Xp).clamp_min(1e-30))
+            tdev = max(tdev, d)
+        tj = jacobi_model_flops(shapes, tuned["sweeps"]) / (tuned["stages"]["jacobi_svt"] / 1e3) / 1e12
+        plain_line["autotuned"] = {
+            "shape": shape, "tune_seconds": t_at,
+            "tune_ms_per_pass": {"default": tune_def_ms, "chosen": tune_best_ms},
+            "value": tuned_value, "ms_per_step": tuned["ms"] / args.steps,
+            "stages_ms": tuned["stages"], "max_rel_dev_vs_default": tdev,
+            "jacobi_tflops": tj, "jacobi_frac": tj / FP32_PEAK_TFLOPS}
+    best_plain = max(plain_value, plain_line["autotuned"]["value"]) if shape else plain_value
 
     # --- learned path: proposer trained (untimed) on separately seeded batches
     t_train = time.perf_counter()
@@ -408,6 +455,7 @@ def run_tp(args):
     sk_flops = sketch_model_flops(shapes, learned["widths"])
     sk_tflops = sk_flops / (st["sketch_svt"] / 1e3) / 1e12
     fb = learned["flags"]
+    groups = svd_launch_groups([(a, b) for a, b, _ in shapes], shape)
     dominant = "sketch_svt" if st["sketch_svt"] >= st["jacobi_svt"] else "jacobi_svt"
     if dominant == "sketch_svt":
         roof = {"kernel": "sketch_svt_kernel (randomized range finder + small Jacobi SVD + SVT)",
@@ -432,21 +480,21 @@ def run_tp(args):
                        "Jacobi fallback", "tensors": len(specs), "free_slices": slices,
                        "seed": rank, "input_bytes": nbytes,
                        "l2": "inputs larger than L2 (%.2f GB in + out per step)" % (2 * nbytes / 1e9)},
-            # per step: DFT, features, MLP, binning, 4 sketch classes, 2 x (collect + retry),
-            # the Jacobi groups, inverse DFT
-            "gpu_launches": (13 + groups) * args.steps,
+            "gpu_launches": (LEARNED_FIXED_LAUNCHES + groups) * args.steps,
             "roofline": roof,
             "stages_ms": st,
             "learned": {"fallback_fraction": float((fb == 1).mean()),
                         "max_rel_dev_vs_plain": dev, "train_slices": train_slices,
                         "train_mse": mse, "train_seconds": t_train,
                         "sketch_width_mean": float(learned["widths"][fb == 0].mean()) if (fb == 0).any() else 0.0,
-                        "vs_plain": value / plain_value},
+                        "vs_plain": value / best_plain},
             "plain": plain_line,
             "plan": plan,
             "dft_gbs": {"rfft": dft_gbs, "irfft": idft_gbs}}
 
     line["clocks"] = learned["clocks"]
+    if shape:
+        tp.jacobi_shape_set(None)  # the other legs run at the default shape
     if not args.no_e2e:
         line["e2e"] = e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device)
     if not args.no_tprod and rank == 0:
@@ -455,6 +503,11 @@ def run_tp(args):
         line["factor"] = factor_leg(args, tp, synth, device)
     if not args.no_trpca and rank == 0:
         line["trpca"] = trpca_leg(args, tp, synth, device)
+    if not args.no_stream and rank == 0:
+        try:
+            line["stream"] = stream_leg(args, tp, synth, device)
+        except tp.TpError as e:  # reported in the line; the measured legs above stand
+            line["stream"] = {"error": str(e)}
     if rank == 0:
         rate, sl, nt, secs = oracle_sample(specs, rank, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(),
@@ -721,6 +774,132 @@ def trpca_leg(args, tp, synth, device):
         if method == "learned":
             out[method]["fallback_fraction"] = fbf
     out["learned_vs_plain"] = out["jacobi"]["ms"] / out["learned"]["ms"]
+    return out
+
+
+def stream_leg(args, tp, synth, device):
+    """A bounded sample of the mixed call stream: the first `stream_calls` calls of the seeded
+    stream (prox_tnn or tprod by a fair coin; n1, n2 up to 512, n3 up to 256, every operand a
+    rank-4..40 t-product plus N(0, 0.02^2) noise), run two ways on the same tensors:
+      plain     every call on its own in stream order: tp_prox_tnn (Jacobi, FP32) and
+                tp_tprod (FP32 slice GEMMs);
+      combined  the stream in windows of `stream_window` consecutive calls: the window's prox
+                calls as one replayed batched plan (CUDA graph) with the learned method, its
+                tprod calls with BF16x3 tensor-core slice GEMMs.
+    Operand data is drawn on the device (seeded torch generator; sizes from the generator
+    module) and formed with the library's t-product, untimed. The proposer is retrained on the
+    plain path's labels for prox calls of another draw of the stream."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(20180619)
+
+    def randn(n1, n2, n3, std=1.0):
+        return (torch.randn(n3, n2, n1, generator=gen, device=device) * std).permute(2, 1, 0)
+
+    def low_rank(sp):
+        X = tp.tprod(randn(sp.n1, sp.r, sp.n3), randn(sp.r, sp.n2, sp.n3))
+        X.add_(randn(sp.n1, sp.n2, sp.n3, sp.noise))
+        return X
+
+    # proposer for these sizes and ranks
+    t0 = time.time()
+    tcalls = [c for c in synth.stream_specs(8 * args.stream_calls, seed=1) if c.op == "prox"][:24]
+    tY = [low_rank(c.a) for c in tcalls]
+    mse = tp.proposer_train(tY, [c.a.tau for c in tcalls], steps=300, seed=3)
+    train = {"tensors": len(tY), "slices": sum(Y.shape[2] // 2 + 1 for Y in tY), "mse": mse,
+             "seconds": time.time() - t0}
+    del tY
+
+    calls = synth.stream_specs(args.stream_calls, seed=0)
+    data = []
+    for c in calls:
+        if c.op == "prox":
+            Y = low_rank(c.a)
+            data.append({"Y": Y, "Xp": tp.empty(*Y.shape, device=device),
+                         "Xc": tp.empty(*Y.shape, device=device)})
+        else:
+            A, B = low_rank(c.a), low_rank(c.b)
+            data.append({"A": A, "B": B, "Cp": tp.empty(c.a.n1, c.b.n2, c.a.n3, device=device),
+                         "Cc": tp.empty(c.a.n1, c.b.n2, c.a.n3, device=device)})
+    torch.cuda.synchronize()
+    prox_idx = [i for i, c in enumerate(calls) if c.op == "prox"]
+    tprod_idx = [i for i, c in enumerate(calls) if c.op == "tprod"]
+    prox_slices = sum(calls[i].a.n3 // 2 + 1 for i in prox_idx)
+    tprod_flops = 0.0
+    for i in tprod_idx:
+        a, b = calls[i].a, calls[i].b
+        h = a.n3 // 2 + 1
+        nreal = 2 if a.n3 % 2 == 0 else 1
+        tprod_flops += (2.0 * nreal + 8.0 * (h - nreal)) * a.n1 * a.n2 * b.n2
+
+    o_plain_p = tp.options(sync=False)
+    o_plain_t = tp.options(sync=False)
+    o_tc = tp.options(precision="bf16x3", sync=False)
+
+    def plain_pass():
+        for i, c in enumerate(calls):
+            d = data[i]
+            if c.op == "prox":
+                tp.prox_tnn(d["Y"], c.a.tau, out=d["Xp"], opts=o_plain_p)
+            else:
+                tp.tprod(d["A"], d["B"], out=d["Cp"], opts=o_plain_t)
+
+    W = args.stream_window
+    windows, flags = [], []
+    for w0 in range(0, len(calls), W):
+        w = range(w0, min(w0 + W, len(calls)))
+        px = [i for i in w if calls[i].op == "prox"]
+        plan = None
+        if px:
+            f = torch.zeros(sum(calls[i].a.n3 // 2 + 1 for i in px), dtype=torch.int32,
+                            device=device)
+            flags.append(f)
+            plan = tp.ProxPlan([data[i]["Y"] for i in px], [calls[i].a.tau for i in px],
+                               outs=[data[i]["Xc"] for i in px],
+                               opts=tp.options(sync=False, method="learned", slice_flags_out=f))
+        windows.append((plan, [i for i in w if calls[i].op == "tprod"]))
+
+    def combined_pass():
+        for plan, tps in windows:
+            if plan is not None:
+                plan.run()
+            for i in tps:
+                tp.tprod(data[i]["A"], data[i]["B"], out=data[i]["Cc"], opts=o_tc)
+
+    reps = 2
+    out = {"workload": f"first {len(calls)} calls of the seeded mixed stream (prox_tnn or tprod "
+                       "by a fair coin; n1,n2~U{16..512}, n3~U{4..256}, l~U{16..512}, tubal rank "
+                       "r~U{4..40} + N(0,0.02^2) noise, tau = 2x noise level)",
+           "calls": len(calls), "prox_calls": len(prox_idx), "tprod_calls": len(tprod_idx),
+           "prox_slices": prox_slices, "tprod_flops": tprod_flops, "window": W,
+           "proposer_train": train}
+    for name, fn in (("plain", plain_pass), ("combined", combined_pass)):
+        fn()  # warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[name] = {"ms_per_pass": ms, "calls_per_s": len(calls) / (ms / 1e3)}
+    fl = torch.cat(flags).cpu() if flags else torch.zeros(0)
+    out["combined"]["prox_fallback_fraction"] = float((fl == 1).float().mean()) if fl.numel() else 0.0
+    out["combined"]["api"] = ("tp_prox_plan_run (learned) per window + tp_tprod BF16x3; "
+                              f"{sum(1 for p, _ in windows if p is not None)} plans")
+    out["plain"]["api"] = "tp_prox_tnn (Jacobi) and tp_tprod (FP32), one call each"
+    out["speedup"] = out["plain"]["ms_per_pass"] / out["combined"]["ms_per_pass"]
+
+    def reldev(x, y):
+        return float(torch.linalg.vector_norm(x - y) / torch.linalg.vector_norm(y).clamp_min(1e-30))
+
+    out["max_rel_dev_vs_plain"] = {
+        "prox": max((reldev(data[i]["Xc"], data[i]["Xp"]) for i in prox_idx), default=0.0),
+        "tprod": max((reldev(data[i]["Cc"], data[i]["Cp"]) for i in tprod_idx), default=0.0)}
+    for plan, _ in windows:
+        if plan is not None:
+            plan.close()
     return out
 
 

@@ -295,6 +295,46 @@ tp_status tp_proposer_get(float* host_params);
 tp_status tp_proposer_set(const float* host_params);
 
 /*
+ * CTA shape of the one-sided Jacobi kernel (not in the paper; the method is Algorithm 3,
+ * step 2, or the singular values of Eq. 14 and 17). The kernel runs one CTA per Fourier
+ * slice; each column pair of a sweep round is rotated by a group of 8, 16 or 32 lanes, and a
+ * round's n/2 disjoint pairs are spread over the CTA's warps in as few passes as its warp
+ * count allows. A shape sets:
+ *   target_lane_pairs: lanes per pair are chosen so that each lane holds about this many
+ *     float4 pairs of the two columns, balanced against zero padding (1..8; default 5);
+ *   max_warps: warps per CTA at most (2..32; default 32; 16 when a lane holds more than
+ *     4 pairs, the kernel's register limit);
+ *   split_launches: 1 launches slices whose CTA sizes differ separately; 0 (default) launches
+ *     all slices of one kernel instantiation together at the largest CTA size among them.
+ * The current device's shape applies to the Jacobi launches of tp_prox_tnn, tp_prox_tnn_batched,
+ * tp_prox_tnn_batched_host, plans created while it is set, tp_proposer_train, tp_tnn, tp_tsn
+ * and tp_tubalrank; tp_tsvd and tp_prox_tnn_noalloc always use the default. Results under
+ * different shapes differ only by rounding order.
+ *
+ * tp_jacobi_shape_get / tp_jacobi_shape_set: read or replace the current device's shape (HOST
+ *   struct; set(NULL) restores the default; an out-of-range field gives TP_ERR_INVALID_ARG).
+ *   Not safe to call while another host thread launches work on the same device.
+ * tp_autotune_jacobi: the autotuner. It computes the Fourier slices of `descs` (the tensors are
+ *   read, never written; rules of tp_prox_tnn_batched) and times the batched prox's Jacobi
+ *   launches on them under 18 candidate shapes (target_lane_pairs 3, 5, 7 x max_warps 8, 16,
+ *   32 x split_launches 0, 1), each once untimed and then `reps` (1..100) times with CUDA events
+ *   on `stream`, and makes the fastest the current device's shape (the default wins ties).
+ *   *chosen (HOST, required) receives it; ms_out (HOST, optional, 2 doubles) receives the
+ *   default shape's and the chosen shape's time per pass over the batch in milliseconds.
+ *   Synchronous. Device memory: the batch's half spectra twice plus the Jacobi workspace.
+ *   A batch without any non-empty tensor gives TP_ERR_INVALID_ARG.
+ */
+typedef struct tp_jacobi_shape {
+    int32_t target_lane_pairs;
+    int32_t max_warps;
+    int32_t split_launches;
+} tp_jacobi_shape;
+tp_status tp_jacobi_shape_get(tp_jacobi_shape* shape);
+tp_status tp_jacobi_shape_set(const tp_jacobi_shape* shape);
+tp_status tp_autotune_jacobi(const tp_tensor_desc* descs, int64_t count, int32_t reps,
+                             tp_jacobi_shape* chosen, double* ms_out, void* stream);
+
+/*
  * tp_prox_tnn without any device allocation. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory while they run -- for instance code
  * that must not trigger the implicit synchronisation or the latency of an allocator call

@@ -244,20 +244,36 @@ struct SvdBatch {
     };
     std::vector<Item> items;
 
+    SvdJob* d_jobs = nullptr;
+
     tp_status launch(Workspace& ws, int mode, const Opts& o, uint32_t* d_status, cudaStream_t s) {
         if (items.empty()) return TP_OK;
-        auto key = [](const Item& a) {
-            return (a.cfg.in_smem ? 0 : 1000000) + a.cfg.lp * 100 + a.cfg.maxe;
-        };
+        TP_TRY(upload_jobs(ws, s));
+        return run(mode, o, d_status, s);
+    }
+
+    int64_t key(const Item& a) const {
+        return (int64_t)a.cfg.group * 10000000 + (a.cfg.in_smem ? 0 : 1000000) +
+               a.cfg.lp * 100 + a.cfg.maxe;
+    }
+
+    // Sort the jobs into launch groups (largest first within a group) and upload them.
+    tp_status upload_jobs(Workspace& ws, cudaStream_t s) {
+        if (items.empty()) return TP_OK;
         std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
             if (key(a) != key(b)) return key(a) < key(b);
             return a.cost > b.cost;
         });
         std::vector<SvdJob> jobs(items.size());
         for (size_t i = 0; i < items.size(); ++i) jobs[i] = items[i].job;
-        SvdJob* d_jobs = ws.take<SvdJob>(jobs.size());
+        d_jobs = ws.take<SvdJob>(jobs.size());
         TP_TRY(ws.check());
-        TP_TRY(upload(d_jobs, jobs, s));
+        return upload(d_jobs, jobs, s);
+    }
+
+    // One launch per group of uploaded jobs.
+    tp_status run(int mode, const Opts& o, uint32_t* d_status, cudaStream_t s) const {
+        if (items.empty()) return TP_OK;
         SvdParams p;
         p.mode = mode;
         p.max_sweeps = o.max_sweeps;
@@ -348,13 +364,14 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     int64_t slices = 0;
     std::vector<SvdConfig> cfg(count);
     std::vector<int64_t> work(count, 0);
+    const JacobiShape shape = jacobi_shape_current();
     int64_t nfft = 0;
     int max_n1 = 1, max_n2 = 1;
     for (int64_t t = 0; t < count; ++t) {
         const int64_t n1 = d[t].n1, n2 = d[t].n2, n3 = d[t].n3;
         if (n1 == 0 || n2 == 0 || n3 == 0) continue;
         const int h = free_slices((int)n3);
-        if (!svd_plan((int)n1, (int)n2, SVD_PROX, &cfg[t])) return TP_ERR_UNSUPPORTED;
+        if (!svd_plan((int)n1, (int)n2, SVD_PROX, &cfg[t], &shape)) return TP_ERR_UNSUPPORTED;
         work[t] = cfg[t].work_elems;
         bytes += cbytes(n1 * n2 * h);
         if (work[t] > 0) bytes += cbytes(work[t] * h);
@@ -548,7 +565,8 @@ tp_status sigma_op(const float* A, int64_t n1, int64_t n2, int64_t n3, int kind,
     const int h = free_slices((int)n3);
     const int64_t r = std::min(n1, n2), P = n1 * n2;
     SvdConfig cfg;
-    if (!svd_plan((int)n1, (int)n2, SVD_SIGMA, &cfg)) return TP_ERR_UNSUPPORTED;
+    const JacobiShape shape = jacobi_shape_current();
+    if (!svd_plan((int)n1, (int)n2, SVD_SIGMA, &cfg, &shape)) return TP_ERR_UNSUPPORTED;
     const int64_t work = cfg.work_elems;
     size_t bytes = Workspace::round(4) + cbytes(P * h) + (work ? cbytes(work * h) : 0) +
                    Workspace::round(sizeof(float) * r * h) + 2 * Workspace::round(sizeof(FftJob)) +
@@ -1104,6 +1122,163 @@ tp_status tp_proposer_set(const float* host_params) {
     for (int i = 0; i < kProposerFloats; ++i)
         if (!isfinite(host_params[i])) return TP_ERR_INVALID_ARG;
     TP_CUDA(proposer_set(host_params));
+    return TP_OK;
+}
+
+static tp_status shape_in(const tp_jacobi_shape* in, JacobiShape* out) {
+    out->target_e2 = in->target_lane_pairs;
+    out->max_warps = in->max_warps;
+    out->split = in->split_launches;
+    return jacobi_shape_valid(*out) ? TP_OK : TP_ERR_INVALID_ARG;
+}
+
+static void shape_out(const JacobiShape& in, tp_jacobi_shape* out) {
+    out->target_lane_pairs = in.target_e2;
+    out->max_warps = in.max_warps;
+    out->split_launches = in.split;
+}
+
+tp_status tp_jacobi_shape_get(tp_jacobi_shape* shape) {
+    if (!shape) return TP_ERR_INVALID_ARG;
+    int dev = 0;
+    TP_CUDA(cudaGetDevice(&dev));
+    shape_out(jacobi_shape_current(), shape);
+    return TP_OK;
+}
+
+tp_status tp_jacobi_shape_set(const tp_jacobi_shape* shape) {
+    JacobiShape sh;
+    if (shape) TP_TRY(shape_in(shape, &sh));
+    int dev = 0;
+    TP_CUDA(cudaGetDevice(&dev));
+    jacobi_shape_store(sh);
+    return TP_OK;
+}
+
+// Times the batched Jacobi prox launches on the batch's own Fourier slices under every
+// candidate shape and keeps the fastest.  The slices are computed once; each candidate reads
+// them and writes its thresholded slices to a second buffer, so every candidate sees the
+// same input.
+tp_status tp_autotune_jacobi(const tp_tensor_desc* descs, int64_t count, int32_t reps,
+                             tp_jacobi_shape* chosen, double* ms_out, void* stream) {
+    TP_TRY(check_descs(descs, count));
+    if (reps < 1 || reps > 100 || !chosen) return TP_ERR_INVALID_ARG;
+    int64_t slices = 0, nfft = 0;
+    size_t spec_bytes = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        const tp_tensor_desc& d = descs[t];
+        if (d.n1 == 0 || d.n2 == 0 || d.n3 == 0) continue;
+        const int h = free_slices((int)d.n3);
+        spec_bytes += cbytes(d.n1 * d.n2 * h);
+        slices += h;
+        ++nfft;
+    }
+    if (slices == 0) return TP_ERR_INVALID_ARG;
+    TP_TRY(prepare());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    Workspace ws(s);
+    TP_TRY(ws.reserve(Workspace::round(sizeof(uint32_t)) + 2 * spec_bytes +
+                      Workspace::round(sizeof(FftJob) * (nfft + 1))));
+    uint32_t* d_status = ws.take<uint32_t>(1);
+    std::vector<float2*> spec(count, nullptr), outs(count, nullptr);
+    FftBatch fwd;
+    for (int64_t t = 0; t < count; ++t) {
+        const tp_tensor_desc& d = descs[t];
+        if (d.n1 == 0 || d.n2 == 0 || d.n3 == 0) continue;
+        const int64_t P = d.n1 * d.n2;
+        const int h = free_slices((int)d.n3);
+        spec[t] = ws.take<float2>(P * h);
+        outs[t] = ws.take<float2>(P * h);
+        fwd.add(d.in, spec[t], P, (int)d.n3);
+    }
+    TP_TRY(ws.check());
+    TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+    TP_TRY(fwd.launch(ws, false, s));
+
+    std::vector<JacobiShape> cands;
+    cands.push_back(JacobiShape());  // the default first: it wins ties
+    for (int split : {0, 1})
+        for (int e2 : {3, 5, 7})
+            for (int w : {8, 16, 32}) {
+                JacobiShape c;
+                c.target_e2 = e2;
+                c.max_warps = w;
+                c.split = split;
+                if (c.target_e2 == 5 && c.max_warps == 32 && c.split == 0) continue;
+                cands.push_back(c);
+            }
+
+    struct Ev {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Ev() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    TP_CUDA(cudaEventCreate(&ev.a));
+    TP_CUDA(cudaEventCreate(&ev.b));
+    Opts o;  // default sweep cap and tolerance, no per-slice outputs
+    double best_ms = 0.0, default_ms = 0.0;
+    size_t best = 0;
+    for (size_t c = 0; c < cands.size(); ++c) {
+        SvdBatch svd;
+        std::vector<SvdConfig> cfg(count);
+        size_t bytes = Workspace::round(sizeof(SvdJob) * (slices + 1));
+        for (int64_t t = 0; t < count; ++t) {
+            const tp_tensor_desc& d = descs[t];
+            if (!spec[t]) continue;
+            if (!svd_plan((int)d.n1, (int)d.n2, SVD_PROX, &cfg[t], &cands[c]))
+                return TP_ERR_UNSUPPORTED;
+            if (cfg[t].work_elems > 0) bytes += cbytes(cfg[t].work_elems * free_slices((int)d.n3));
+        }
+        Workspace cw(s);
+        TP_TRY(cw.reserve(bytes));
+        for (int64_t t = 0; t < count; ++t) {
+            const tp_tensor_desc& d = descs[t];
+            if (!spec[t]) continue;
+            const int h = free_slices((int)d.n3);
+            const int64_t P = d.n1 * d.n2;
+            float2* wk = cfg[t].work_elems > 0 ? cw.take<float2>(cfg[t].work_elems * h) : nullptr;
+            for (int k = 0; k < h; ++k) {
+                SvdBatch::Item it{};
+                SvdJob& j = it.job;
+                j.A = spec[t] + P * k;
+                j.W = outs[t] + P * k;
+                j.work = wk ? wk + cfg[t].work_elems * k : nullptr;
+                j.n1 = (int)d.n1;
+                j.n2 = (int)d.n2;
+                j.real_slice = is_real_slice(k, (int)d.n3) ? 1 : 0;
+                j.tau = d.tau;
+                it.cfg = cfg[t];
+                const int64_t m = std::max(d.n1, d.n2), n = std::min(d.n1, d.n2);
+                it.cost = m * n * n;
+                svd.items.push_back(it);
+            }
+        }
+        TP_TRY(cw.check());
+        TP_TRY(svd.upload_jobs(cw, s));
+        TP_TRY(svd.run(SVD_PROX, o, d_status, s));  // untimed: first launch of each kernel
+        TP_CUDA(cudaEventRecord(ev.a, s));
+        for (int r = 0; r < reps; ++r) TP_TRY(svd.run(SVD_PROX, o, d_status, s));
+        TP_CUDA(cudaEventRecord(ev.b, s));
+        TP_CUDA(cudaEventSynchronize(ev.b));
+        float ms = 0.f;
+        TP_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+        const double per = (double)ms / reps;
+        if (c == 0) default_ms = best_ms = per;
+        else if (per < best_ms) {
+            best_ms = per;
+            best = c;
+        }
+    }
+    TP_CUDA(cudaStreamSynchronize(s));
+    jacobi_shape_store(cands[best]);
+    shape_out(cands[best], chosen);
+    if (ms_out) {
+        ms_out[0] = default_ms;
+        ms_out[1] = best_ms;
+    }
     return TP_OK;
 }
 

@@ -93,7 +93,23 @@ struct SvdConfig {
     int lp, maxe, smem_bytes, threads;
     bool in_smem;
     int64_t work_elems;  // global scratch elements (float2) per slice
+    int group = 0;       // > 0: slices launch only with slices of the same group (CTA size)
 };
+
+// CTA shape policy of the Jacobi kernel (tp_jacobi_shape of tp.h): lanes per column pair are
+// picked so that each lane holds about `target_e2` float4 pairs, the CTA has at most
+// `max_warps` warps (the pairs of a round are spread over passes of that many warps), and
+// with `split` set, slices whose CTA sizes differ are launched separately instead of sharing
+// the largest CTA of their kernel instantiation.  The default reproduces the fixed choice.
+struct JacobiShape {
+    int target_e2 = 5;
+    int max_warps = 32;
+    int split = 0;
+};
+bool jacobi_shape_valid(const JacobiShape& sh);
+// The current device's shape (the default until tp_jacobi_shape_set / tp_autotune_jacobi).
+JacobiShape jacobi_shape_current();
+void jacobi_shape_store(const JacobiShape& sh);
 
 struct SvdParams {
     int mode;
@@ -103,8 +119,8 @@ struct SvdParams {
     uint32_t* status;    // device status word (bit 0: not converged)
 };
 
-// Which launch configuration a slice of size n1 x n2 needs.
-bool svd_plan(int n1, int n2, int mode, SvdConfig* cfg);
+// Which launch configuration a slice of size n1 x n2 needs under `shape` (NULL: default).
+bool svd_plan(int n1, int n2, int mode, SvdConfig* cfg, const JacobiShape* shape = nullptr);
 cudaError_t launch_svd(const SvdLaunch& L, const SvdParams& p, cudaStream_t s);
 
 // Reductions over the sorted singular values of one tensor (tnn, tsn, tubal rank).

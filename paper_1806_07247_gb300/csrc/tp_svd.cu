@@ -40,6 +40,9 @@
 // column by column, re-reading the original column g_c of the slice.
 #include <math.h>
 
+#include <algorithm>
+#include <atomic>
+
 #include "tp_internal.cuh"
 #include "tp_rotation.cuh"
 
@@ -647,16 +650,54 @@ __global__ void diag_scatter_kernel(const float* __restrict__ tubes, int r, int 
 
 }  // namespace
 
-bool svd_plan(int n1, int n2, int mode, SvdConfig* cfg) {
+bool jacobi_shape_valid(const JacobiShape& sh) {
+    return sh.target_e2 >= 1 && sh.target_e2 <= 8 && sh.max_warps >= 2 && sh.max_warps <= 32 &&
+           (sh.split == 0 || sh.split == 1);
+}
+
+namespace {
+// Per-device shape, packed as target_e2 | max_warps << 8 | split << 16 (0 = default).
+std::atomic<uint32_t> g_shape[128];
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return -1;
+    return dev;
+}
+}  // namespace
+
+JacobiShape jacobi_shape_current() {
+    JacobiShape sh;
+    const int dev = current_device();
+    if (dev < 0) return sh;
+    const uint32_t v = g_shape[dev].load(std::memory_order_relaxed);
+    if (v == 0) return sh;
+    sh.target_e2 = (int)(v & 0xff);
+    sh.max_warps = (int)((v >> 8) & 0xff);
+    sh.split = (int)((v >> 16) & 0xff);
+    return sh;
+}
+
+void jacobi_shape_store(const JacobiShape& sh) {
+    const int dev = current_device();
+    if (dev < 0) return;
+    const uint32_t v = (uint32_t)sh.target_e2 | ((uint32_t)sh.max_warps << 8) |
+                       ((uint32_t)sh.split << 16);
+    g_shape[dev].store(v, std::memory_order_relaxed);
+}
+
+bool svd_plan(int n1, int n2, int mode, SvdConfig* cfg, const JacobiShape* shape) {
+    const JacobiShape sh = shape ? *shape : JacobiShape();
     const int m = n1 > n2 ? n1 : n2, n = n1 > n2 ? n2 : n1;
     if (m > TP_MAX_SVD_DIM || n < 0 || m < 1) return false;
-    // lanes per column pair: little zero padding, about 4-6 float4 pairs per lane
+    // lanes per column pair: little zero padding, about target_e2 float4 pairs per lane
     int lp = 32;
     double best = 1e30;
     for (int cand : {8, 16, 32}) {
         const int e2 = col_e2(m, cand);
         if (e2 > 8) continue;
-        const double score = (double)(col_ld(m, cand) - m) / m + 0.03 * fabs(e2 - 5.0);
+        const double score =
+            (double)(col_ld(m, cand) - m) / m + 0.03 * fabs(e2 - (double)sh.target_e2);
         if (score < best) { best = score; lp = cand; }
     }
     const int e2 = col_e2(m, lp);
@@ -671,12 +712,14 @@ bool svd_plan(int n1, int n2, int mode, SvdConfig* cfg) {
     cfg->in_smem = sm;
     cfg->smem_bytes = sm ? (int)(gbytes + aux) : aux;
     // pair slots: the pairs of a round split evenly over as few passes as the warp cap allows
+    // (the kernels' launch bounds: 512 threads with 8 float4 pairs per lane, else 1024)
     const int pairs = (n + 1) / 2, spw = 32 / lp;
-    const int wmax = maxe2 >= 8 ? 16 : 32;
+    const int wmax = std::min(sh.max_warps, maxe2 >= 8 ? 16 : 32);
     const int passes = (pairs + wmax * spw - 1) / (wmax * spw);
     int warps = (pairs + passes * spw - 1) / (passes * spw);
     warps = warps < 2 ? 2 : warps;
     cfg->threads = 32 * warps;
+    cfg->group = sh.split ? cfg->threads : 0;
     int64_t w = 0;
     if (!sm) w += (int64_t)n * ld;
     if (mode == SVD_FULL) w += (int64_t)n * n;

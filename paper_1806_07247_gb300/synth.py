@@ -26,6 +26,10 @@ low-rank-plus-noise tensors of its use case):
   G iid N(0, 1/(16 n n3)), so every Fourier slice is I plus a matrix of spectral norm
   about 1/2 (condition number about 3): the inverse and QR workloads.
 * gaussian(): n1 x n2 x n3 iid N(0, 1) (tall shapes give well-conditioned QR slices).
+* stream_specs(): the mixed call stream: each call is prox_tnn or tprod by a fair coin,
+  n1, n2 uniform in {16..512}, n3 uniform in {4..256}, tprod's third size l uniform in
+  {16..512}, tubal rank r uniform in {4..40}, noise N(0, 0.02^2), tau = 2 nu as for
+  batched() (every operand is a rank-r t-product of N(0,1) factors plus noise).
 * trpca(): 240x320x100, tubal rank 10 factors iid N(0,1), 10% of positions
   (without replacement) corrupted by values uniform in [-5, 5],
   tau = 1 / sqrt(max(n1, n2) * n3).
@@ -37,7 +41,7 @@ from dataclasses import dataclass
 import numpy as np
 
 __all__ = ["normal", "small", "batched_specs", "batched_tensor", "gemm", "trpca",
-           "LowRankSpec", "shifted_square", "gaussian"]
+           "LowRankSpec", "shifted_square", "gaussian", "StreamCall", "stream_specs"]
 
 
 def _rng(seed) -> np.random.Generator:
@@ -98,6 +102,33 @@ def batched_tensor(spec: LowRankSpec, index: int, seed: int = 0) -> dict:
     Q = normal(rng, (spec.r, spec.n2, spec.n3))
     E = normal(rng, (spec.n1, spec.n2, spec.n3), spec.noise)
     return {"P": P, "Q": Q, "E": E, "tau": spec.tau, "rank": spec.r}
+
+
+@dataclass(frozen=True)
+class StreamCall:
+    op: str          # "prox" (prox_tnn of a) or "tprod" (a * b)
+    a: LowRankSpec   # n1 x n2 x n3
+    b: LowRankSpec | None  # tprod: n2 x l x n3
+
+
+def stream_specs(count: int = 2000, seed: int = 0, n_lo: int = 16, n_hi: int = 512,
+                 n3_lo: int = 4, n3_hi: int = 256, r_lo: int = 4, r_hi: int = 40,
+                 noise: float = 0.02) -> list[StreamCall]:
+    """Sizes, ranks and thresholds of the mixed call stream (no tensor data)."""
+    rng = _rng(seed)
+    out = []
+    for _ in range(count):
+        op = "prox" if rng.integers(0, 2) == 0 else "tprod"
+        n1, n2, l = (int(v) for v in rng.integers(n_lo, n_hi + 1, size=3))
+        n3 = int(rng.integers(n3_lo, n3_hi + 1))
+        ra, rb = (int(v) for v in rng.integers(r_lo, r_hi + 1, size=2))
+
+        def spec(p, q, r):
+            nu = noise * np.sqrt(n3) * (np.sqrt(p) + np.sqrt(q))
+            return LowRankSpec(p, q, n3, r, noise, float(2.0 * nu))
+
+        out.append(StreamCall(op, spec(n1, n2, ra), spec(n2, l, rb) if op == "tprod" else None))
+    return out
 
 
 def gemm(seed: int = 0, n1: int = 2048, n2: int = 1024, l: int = 1024, n3: int = 64) -> dict:

@@ -46,6 +46,11 @@ class Options(ctypes.Structure):
 STAGE_EVENTS = 6
 
 
+class JacobiShape(ctypes.Structure):
+    _fields_ = [("target_lane_pairs", ctypes.c_int32), ("max_warps", ctypes.c_int32),
+                ("split_launches", ctypes.c_int32)]
+
+
 class TensorDesc(ctypes.Structure):
     _fields_ = [("inp", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n1", ctypes.c_int64),
                 ("n2", ctypes.c_int64), ("n3", ctypes.c_int64), ("tau", ctypes.c_double)]
@@ -87,6 +92,11 @@ _SIGS = {
                                            ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_void_p)]),
     "tp_prox_plan_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "tp_prox_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "tp_jacobi_shape_get": (ctypes.c_int, [ctypes.POINTER(JacobiShape)]),
+    "tp_jacobi_shape_set": (ctypes.c_int, [ctypes.POINTER(JacobiShape)]),
+    "tp_autotune_jacobi": (ctypes.c_int, [ctypes.POINTER(TensorDesc), ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.POINTER(JacobiShape),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "tp_proposer_get": (ctypes.c_int, [ctypes.c_void_p]),
     "tp_proposer_set": (ctypes.c_int, [ctypes.c_void_p]),
 }
@@ -435,6 +445,41 @@ def proposer_set(params: np.ndarray) -> None:
     params = np.ascontiguousarray(params, dtype=np.float32)
     assert params.size == PROPOSER_FLOATS
     _check(lib().tp_proposer_set(params.ctypes.data), "tp_proposer_set")
+
+
+def _shape_dict(sh: JacobiShape) -> dict:
+    return {"target_lane_pairs": sh.target_lane_pairs, "max_warps": sh.max_warps,
+            "split_launches": sh.split_launches}
+
+
+def jacobi_shape_get() -> dict:
+    """The current device's Jacobi CTA shape (tp_jacobi_shape_get)."""
+    sh = JacobiShape()
+    _check(lib().tp_jacobi_shape_get(ctypes.byref(sh)), "tp_jacobi_shape_get")
+    return _shape_dict(sh)
+
+
+def jacobi_shape_set(shape: dict | None) -> None:
+    """Replace the current device's Jacobi CTA shape; None restores the default."""
+    if shape is None:
+        _check(lib().tp_jacobi_shape_set(None), "tp_jacobi_shape_set")
+        return
+    sh = JacobiShape(int(shape["target_lane_pairs"]), int(shape["max_warps"]),
+                     int(shape["split_launches"]))
+    _check(lib().tp_jacobi_shape_set(ctypes.byref(sh)), "tp_jacobi_shape_set")
+
+
+def autotune_jacobi(Ys, taus, reps: int = 2, stream=None):
+    """Time the batched prox's Jacobi launches on these tensors' Fourier slices under each
+    candidate CTA shape and keep the fastest (tp_autotune_jacobi). Returns (shape, default_ms,
+    chosen_ms)."""
+    Ys = [_prep(Y, "Y") for Y in Ys]
+    d = make_descs(Ys, Ys, taus)
+    sh = JacobiShape()
+    ms = (ctypes.c_double * 2)()
+    _check(lib().tp_autotune_jacobi(d, len(Ys), int(reps), ctypes.byref(sh), ms, _stream(stream)),
+           "tp_autotune_jacobi")
+    return _shape_dict(sh), ms[0], ms[1]
 
 
 def exported_symbols():

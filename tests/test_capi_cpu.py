@@ -83,3 +83,25 @@ def test_limits_and_bad_options_rejected(L):
     assert L.tp_prox_tnn_batched(d, 1, None, None) == tp.TP_ERR_UNSUPPORTED
     # null pointer for a non-empty tensor
     assert L.tp_tran(None, None, 2, 2, 2, None) == tp.TP_ERR_INVALID_ARG
+
+
+def test_jacobi_shape_and_autotune_argument_checks(L):
+    from paper_1806_07247_gb300 import tp
+    # every field out of range is rejected before the device is touched
+    for bad in [(0, 32, 0), (9, 32, 0), (5, 1, 0), (5, 33, 0), (5, 16, 2), (5, 16, -1)]:
+        sh = tp.JacobiShape(*bad)
+        assert L.tp_jacobi_shape_set(ctypes.byref(sh)) == tp.TP_ERR_INVALID_ARG, bad
+    assert L.tp_jacobi_shape_get(None) == tp.TP_ERR_INVALID_ARG
+    d = (tp.TensorDesc * 1)()
+    d[0].inp, d[0].out, d[0].n1, d[0].n2, d[0].n3, d[0].tau = 16, 16, 8, 8, 4, 0.1
+    sh = tp.JacobiShape()
+    ms = (ctypes.c_double * 2)()
+    assert L.tp_autotune_jacobi(d, 1, 0, ctypes.byref(sh), ms, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_autotune_jacobi(d, 1, 101, ctypes.byref(sh), ms, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_autotune_jacobi(d, 1, 2, None, ms, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_autotune_jacobi(None, -1, 2, ctypes.byref(sh), ms, None) == tp.TP_ERR_INVALID_ARG
+    # a batch of empty tensors has nothing to time
+    d[0].n3 = 0
+    assert L.tp_autotune_jacobi(d, 1, 2, ctypes.byref(sh), ms, None) == tp.TP_ERR_INVALID_ARG
+    d[0].n3, d[0].n1 = 4, tp.MAX_SVD_DIM + 1
+    assert L.tp_autotune_jacobi(d, 1, 2, ctypes.byref(sh), ms, None) == tp.TP_ERR_UNSUPPORTED

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import tproduct as O
-from tests.helpers import TOL_FP32, batched_inputs, median_sigma, randn, rel
+from tests.helpers import TOL_FP32, batched_inputs, low_rank, median_sigma, randn, rel
 
 pytestmark = pytest.mark.gpu
 TOL_LEARNED = 1e-4
@@ -84,3 +84,26 @@ def test_learned_prox_falls_back_on_full_rank_inputs(tp):
     for Y, tau, out in zip(Ys, taus, outs):
         assert rel(tp.to_numpy(out), O.prox_tnn(Y, tau)) < TOL_FP32
     assert (flags.cpu().numpy() == 1).all()
+
+
+def test_learned_prox_on_large_slices(tp):
+    # slices of the mixed call stream's sizes (up to 512, ranks up to 40): the sketch path
+    # takes those whose width fits a size class, the rest fall back to the global-memory
+    # Jacobi; every output must still be the prox of Algorithm 3 within the mixed-form bound
+    import torch
+
+    from paper_1806_07247_gb300 import synth
+    _train(tp)
+    specs = []
+    for (n1, n2, n3), r in zip([(512, 300, 3), (300, 512, 4), (480, 440, 2), (512, 512, 1),
+                                (350, 260, 5)], [8, 20, 36, 6, 12]):
+        nu = 0.02 * np.sqrt(n3) * (np.sqrt(n1) + np.sqrt(n2))
+        specs.append(synth.LowRankSpec(n1, n2, n3, r, 0.02, float(2.0 * nu)))
+    Xs = [low_rank(synth.batched_tensor(s, i, seed=5)) for i, s in enumerate(specs)]
+    nsl = sum(s.n3 // 2 + 1 for s in specs)
+    flags = torch.full((nsl,), -1, dtype=torch.int32, device="cuda")
+    outs = tp.prox_tnn_batched([tp.to_device(X) for X in Xs], [s.tau for s in specs],
+                               opts=tp.options(method="learned", slice_flags_out=flags))
+    for s, X, out in zip(specs, Xs, outs):
+        assert rel(tp.to_numpy(out), O.prox_tnn(X, s.tau)) < TOL_LEARNED, s
+    assert set(np.unique(flags.cpu().numpy())) <= {0, 1}
