@@ -169,6 +169,13 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- workload
+# DRAM traffic of the sketch stage (dram__bytes_read.sum + dram__bytes_write.sum over the four
+# class launches of one call) per byte of half spectrum, from an ncu capture of the 160-tensor
+# batch of the same workload: 278.2 MB for 178.9 MB of spectrum.  The traffic of a batch is
+# taken in proportion to its half-spectrum bytes.
+SKETCH_DRAM_PER_SPEC_BYTE = 278.2 / 178.9
+
+
 def svd_launch_groups(shapes, shape=None):
     """Kernel launches of the Jacobi stage of one batched prox call (mirrors the library's
     slice planner under a Jacobi CTA shape: lanes per column pair, float4 pairs per lane,
@@ -460,7 +467,11 @@ def run_tp(args):
     if dominant == "sketch_svt":
         roof = {"kernel": "sketch_svt_kernel (randomized range finder + small Jacobi SVD + SVT)",
                 "bound": "alu", "achieved": sk_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": sk_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": sk_tflops / FP32_PEAK_TFLOPS,
+                "traffic": SKETCH_DRAM_PER_SPEC_BYTE * spec_bytes,
+                "traffic_note": "DRAM bytes of the sketch stage per step, scaled by half-spectrum "
+                                "bytes from an ncu capture of the 160-tensor batch (algorithmic: "
+                                "read and write each slice once, %.0f MB)" % (2 * spec_bytes / 1e6),
                 "model": "per sketched slice 8*n1*n2*(6*l+4) flops (l = sketch width)"}
     else:
         fl = jacobi_model_flops(shapes, learned["sweeps"] * (fb == 1))
