@@ -255,11 +255,11 @@ tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count,
  * equal out). The library copies the batch into one device buffer and runs the batched prox
  * on it in place in up to 2 parts of at least 16 MiB each (cut at tensor boundaries). Each
  * part is copied in, computed and copied back on its own: the copy in of part c+1 and the
- * copy back of part c-1 overlap part c's kernels. Each part runs on its own library-owned
- * compute stream, earlier parts at higher stream priority, so later parts' blocks fill the
- * SMs that earlier parts leave idle. The copies use two more library-owned streams per
- * device; all of it is ordered after earlier work on `stream` and before later work on it
- * by events. Runs of tensors that are contiguous in host memory
+ * copy back of part c-1 overlap part c's kernels. The parts' kernels run in order on one
+ * library-owned compute stream per device and the copies on two more library-owned streams;
+ * all of it is ordered after earlier work on `stream` and before later work on it by events.
+ * Calls issued on different streams overlap one another's copies and kernels: the library's
+ * stream-ordered allocations never make one caller stream wait for another. Runs of tensors that are contiguous in host memory
  * move with one copy each. The host buffers should be page-locked (cudaHostAlloc /
  * cudaHostRegister) for the copies to overlap; pageable memory works but serialises. Device
  * memory: the batch once plus the batched prox workspace of every part. With

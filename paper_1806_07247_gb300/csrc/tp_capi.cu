@@ -33,6 +33,13 @@ tp_status from_cuda(cudaError_t e) {
 std::mutex g_pool_mutex;
 bool g_pool_ready[128] = {};
 
+// 1: let cudaMallocAsync reuse a block freed on another stream by making the allocating stream
+// wait for that stream (the pool's default); 0: never add such a wait (the pool maps new memory
+// instead), so that calls issued on different streams stay independent.
+#ifndef TP_POOL_INTERNAL_DEPS
+#define TP_POOL_INTERNAL_DEPS 0
+#endif
+
 // Keep freed stream-ordered allocations in this process's default pool for reuse.
 cudaError_t ensure_pool() {
     int dev = 0;
@@ -46,6 +53,9 @@ cudaError_t ensure_pool() {
     if (e != cudaSuccess) return e;
     uint64_t thr = UINT64_MAX;
     e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (e != cudaSuccess) return e;
+    int deps = TP_POOL_INTERNAL_DEPS;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &deps);
     if (e != cudaSuccess) return e;
     g_pool_ready[dev] = true;
     return cudaSuccess;
@@ -613,13 +623,20 @@ tp_status sigma_op(const float* A, int64_t n1, int64_t n2, int64_t n3, int kind,
 }
 
 // Per-device streams of the host-buffer entry point (created once, never destroyed): the two
-// copy directions and one compute stream per part of the batch, part 0 at the highest stream
-// priority and each later part one level lower (as far as the device's range goes), so that
-// earlier parts finish first and their copies back overlap later parts' kernels, while the
-// later parts' blocks fill the SMs the earlier ones leave idle.
+// copy directions and TP_HOST_COMPUTE_STREAMS compute streams; part c of a batch computes on
+// stream c mod TP_HOST_COMPUTE_STREAMS.  With one compute stream the parts' kernels run in
+// order while the copies overlap them.  With one stream per part, part 0 runs at the highest
+// stream priority and each later part one level lower, so that later parts' blocks fill the
+// SMs the earlier ones leave idle -- but the persistent sketch launches that need a whole SM's
+// shared memory then wait for the other part's blocks to drain every SM, once per launch.
+#ifndef TP_HOST_COMPUTE_STREAMS
+#define TP_HOST_COMPUTE_STREAMS 1
+#endif
 constexpr int kHostParts = 2;
+constexpr int kHostComputeStreams = TP_HOST_COMPUTE_STREAMS;
+static_assert(kHostComputeStreams >= 1 && kHostComputeStreams <= kHostParts, "compute streams");
 struct SideStreams {
-    cudaStream_t h2d = nullptr, d2h = nullptr, comp[kHostParts] = {};
+    cudaStream_t h2d = nullptr, d2h = nullptr, comp[kHostComputeStreams] = {};
 };
 std::mutex g_side_mutex;
 SideStreams g_side[128];
@@ -635,7 +652,7 @@ tp_status side_streams(SideStreams* out) {
     if (!c.comp[0]) {
         int least = 0, greatest = 0;
         TP_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-        for (int p = 0; p < kHostParts; ++p)
+        for (int p = 0; p < kHostComputeStreams; ++p)
             TP_CUDA(cudaStreamCreateWithPriority(&c.comp[p], cudaStreamNonBlocking,
                                                  std::min(least, greatest + p)));
     }
@@ -1374,7 +1391,7 @@ tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
     int64_t slice_base = 0;
     for (int c = 0; c < nparts; ++c) {
         const int64_t first = cut[c], last = cut[c + 1];
-        cudaStream_t cs = ss.comp[c];
+        cudaStream_t cs = ss.comp[c % kHostComputeStreams];
         cudaEvent_t ev_in = ce.ev[1 + c], ev_done = ce.ev[1 + nparts + c];
         TP_TRY(copy_runs(descs, bytes, dev, first, last, true, ss.h2d));
         TP_CUDA(cudaEventRecord(ev_in, ss.h2d));
