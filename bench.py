@@ -565,9 +565,9 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
     """The same batch through the host-buffer entry point: every step copies the inputs from
     page-locked host memory, runs the learned batched prox and copies the results back (the
     library overlapping its copies with its kernels part by part).  Consecutive steps are
-    issued on two streams, as a serving loop would, so one step's copy-in overlaps the
-    previous step's kernels; each step reads its own input buffer and writes its own output
-    buffer (two sets, page-locked)."""
+    issued on two streams, as a serving loop would, so one step's copies also overlap the
+    neighbouring steps' kernels.  Each step reads its own input buffer and writes its own
+    output buffer (two sets, page-locked)."""
     import torch
     shapes = [tuple(Y.shape) for Y in Ys]
     sets = []
@@ -607,8 +607,8 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
     nb = sum(4 * Y.numel() for Y in Ys)
     return {"value": job_throughput(sum_over_ranks(slices, device), args.steps, ms), "unit": UNIT,
             "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
-            "api": "tp_prox_tnn_batched_host on two alternating streams (page-locked host "
-                   "tensors; copies overlap kernels within and across steps)"}
+            "api": "tp_prox_tnn_batched_host (2 parts) on two alternating streams "
+                   "(page-locked host tensors; copies overlap kernels within and across steps)"}
 
 
 BF16_PEAK_TFLOPS = 1944.2        # measured dense bf16 (MEASURED_PEAKS.json, burst)

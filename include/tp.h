@@ -94,6 +94,11 @@ typedef struct tp_options {
     int32_t* sketch_width_out; /* optional DEVICE array, same indexing: the sketch width of
                             the slice's last attempt (the proposer's choice, 4 more after a
                             wider retry; 0: the slice went straight to Jacobi) */
+    int32_t host_parts;  /* tp_prox_tnn_batched_host: parts the batch is cut into, 1 or 2
+                            (0 = 2, the default). Two parts overlap a call's copies with its
+                            own kernels; one part leaves that overlap to a caller that issues
+                            consecutive calls on alternating streams (their copies then overlap
+                            each other's kernels, with no per-part kernel tails) */
 } tp_options;
 
 #define TP_STAGE_EVENTS 6
@@ -253,7 +258,8 @@ tp_status tp_prox_tnn_batched(const tp_tensor_desc* descs, int64_t count,
 /*
  * tp_prox_tnn_batched on tensors in HOST memory: descs[t].in / .out are host pointers (in may
  * equal out). The library copies the batch into one device buffer and runs the batched prox
- * on it in place in up to 2 parts of at least 16 MiB each (cut at tensor boundaries). Each
+ * on it in place in up to opts->host_parts (default 2) parts of at least 16 MiB each (cut at
+ * tensor boundaries). Each
  * part is copied in, computed and copied back on its own: the copy in of part c+1 and the
  * copy back of part c-1 overlap part c's kernels. The parts' kernels run in order on one
  * library-owned compute stream per device and the copies on two more library-owned streams;

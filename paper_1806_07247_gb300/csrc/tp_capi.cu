@@ -124,6 +124,7 @@ struct Opts {
     int method = TP_METHOD_JACOBI;
     int32_t* slice_flags_out = nullptr;
     int32_t* sketch_width_out = nullptr;
+    int host_parts = 2;
     // Record stage boundary i (0..3) on the stream when the caller asked for it.
     tp_status mark(int i, cudaStream_t s) const {
         if (!events || !events[i]) return TP_OK;
@@ -158,6 +159,8 @@ tp_status resolve(const tp_options* o, Opts* r) {
     r->method = o->method;
     r->slice_flags_out = o->slice_flags_out;
     r->sketch_width_out = o->sketch_width_out;
+    if (o->host_parts < 0 || o->host_parts > 2) return TP_ERR_INVALID_ARG;
+    r->host_parts = o->host_parts == 0 ? 2 : o->host_parts;
     return TP_OK;
 }
 
@@ -632,7 +635,7 @@ tp_status sigma_op(const float* A, int64_t n1, int64_t n2, int64_t n3, int kind,
 #ifndef TP_HOST_COMPUTE_STREAMS
 #define TP_HOST_COMPUTE_STREAMS 1
 #endif
-constexpr int kHostParts = 2;
+constexpr int kHostParts = 2;  // most parts a host-buffer call is cut into (tp_options.host_parts)
 constexpr int kHostComputeStreams = TP_HOST_COMPUTE_STREAMS;
 static_assert(kHostComputeStreams >= 1 && kHostComputeStreams <= kHostParts, "compute streams");
 struct SideStreams {
@@ -722,6 +725,7 @@ void tp_options_default(tp_options* opts) {
     opts->method = TP_METHOD_JACOBI;
     opts->slice_flags_out = nullptr;
     opts->sketch_width_out = nullptr;
+    opts->host_parts = 2;
 }
 
 const char* tp_last_error_string(void) {
@@ -1333,11 +1337,11 @@ tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
     SideStreams ss;
     TP_TRY(side_streams(&ss));
 
-    // The batch is cut, at tensor boundaries, into up to kHostParts parts of at least 16 MiB.
+    // The batch is cut, at tensor boundaries, into up to o.host_parts parts of at least 16 MiB.
     // Part c runs on side compute stream c once its host-to-device copy has landed and is
     // copied back as soon as its kernels are done: the copy of part c+1 and the copy back of
     // part c-1 overlap part c's kernels.
-    constexpr int kParts = kHostParts;
+    const int kParts = std::min(o.host_parts, kHostParts);
     std::vector<int64_t> bytes(count), slices(count);
     int64_t total = 0;
     for (int64_t t = 0; t < count; ++t) {

@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int32), ("sync", ctypes.c_int32),
                 ("jacobi_tol", ctypes.c_double), ("sweeps_out", ctypes.c_void_p),
                 ("stage_events", ctypes.c_void_p), ("method", ctypes.c_int32),
-                ("slice_flags_out", ctypes.c_void_p), ("sketch_width_out", ctypes.c_void_p)]
+                ("slice_flags_out", ctypes.c_void_p), ("sketch_width_out", ctypes.c_void_p),
+                ("host_parts", ctypes.c_int32)]
 STAGE_EVENTS = 6
 
 
@@ -129,7 +130,7 @@ def options(precision: str = "fp32", econ: bool = False, max_sweeps: int = 30, s
             jacobi_tol: float = 0.0, sweeps_out: torch.Tensor | None = None,
             stage_events=None, method: str = "jacobi",
             slice_flags_out: torch.Tensor | None = None,
-            sketch_width_out: torch.Tensor | None = None) -> Options:
+            sketch_width_out: torch.Tensor | None = None, host_parts: int = 2) -> Options:
     """tp_options; stage_events is a list of STAGE_EVENTS recorded torch.cuda.Event (tp.h)."""
     o = Options()
     o.method = METHODS[method]
@@ -138,6 +139,7 @@ def options(precision: str = "fp32", econ: bool = False, max_sweeps: int = 30, s
             assert t.is_cuda and t.dtype == torch.int32
             setattr(o, name, t.data_ptr())
     o.precision = PRECISIONS[precision]
+    o.host_parts = int(host_parts)
     o.econ = int(bool(econ))
     o.max_sweeps = int(max_sweeps)
     o.sync = int(bool(sync))

@@ -54,6 +54,7 @@ def test_options_default(L):
     L.tp_options_default(ctypes.byref(o))
     assert (o.precision, o.econ, o.max_sweeps, o.sync, o.jacobi_tol) == (0, 0, 30, 1, 0.0)
     assert o.sweeps_out is None
+    assert o.host_parts == 2
 
 
 def test_negative_dims_rejected_before_any_cuda_call(L):
@@ -77,6 +78,10 @@ def test_limits_and_bad_options_rejected(L):
     assert L.tp_prox_tnn(None, None, 2, 2, 2, -0.5, None, None) == tp.TP_ERR_INVALID_ARG
     assert L.tp_prox_tnn(None, None, 2, 2, 2, float("nan"), None, None) == tp.TP_ERR_INVALID_ARG
     assert L.tp_prox_tnn_batched(None, -1, None, None) == tp.TP_ERR_INVALID_ARG
+    for bad in (-1, 3):
+        o = tp.options()
+        o.host_parts = bad
+        assert L.tp_prox_tnn_batched_host(None, 0, ctypes.byref(o), None) == tp.TP_ERR_INVALID_ARG
     # SVD size limit
     d = (tp.TensorDesc * 1)()
     d[0].inp, d[0].out, d[0].n1, d[0].n2, d[0].n3, d[0].tau = 16, 16, tp.MAX_SVD_DIM + 1, 4, 2, 0.1

@@ -40,13 +40,14 @@ def _np(t):
     return t.permute(2, 1, 0).contiguous().numpy().transpose(2, 1, 0)
 
 
-@pytest.mark.parametrize("method", ["jacobi", "learned"])
-def test_host_matches_device(tp, batch, method):
+@pytest.mark.parametrize("method,parts", [("jacobi", 2), ("learned", 2), ("jacobi", 1),
+                                          ("learned", 1)])
+def test_host_matches_device(tp, batch, method, parts):
     Ys, taus = batch
     if method == "learned":
         tp.proposer_train([tp.to_device(Y) for Y in Ys[:24]], taus[:24], steps=200, seed=1)
     _, hin = _host_slab(tp, Ys)
-    houts = tp.prox_tnn_batched_host(hin, taus, opts=tp.options(method=method))
+    houts = tp.prox_tnn_batched_host(hin, taus, opts=tp.options(method=method, host_parts=parts))
     douts = tp.prox_tnn_batched([tp.to_device(Y) for Y in Ys], taus, opts=tp.options(method=method))
     worst = max(rel(_np(h), tp.to_numpy(d)) for h, d in zip(houts, douts))
     assert worst < 1e-6, worst
