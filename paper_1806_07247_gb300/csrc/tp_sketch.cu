@@ -1,6 +1,6 @@
 // Learned-rank randomized singular value thresholding of the Fourier slices: the fast path
 // of prox_tnn (Algorithm 3, step 2) for slices whose number of singular values above tau is
-// small, with the full one-sided Jacobi SVD (tp_svd.cu) as fallback and judge.
+// small, with the full one-sided Jacobi SVD (tp_svd.cu) as fallback and accuracy reference.
 //
 // Per slice A (n1 x n2 complex, column-major, in place in the half spectrum):
 //   1. a tiny MLP (12 -> 64 -> 64 -> 1, ReLU) reads cheap sketch features -- log ||A||_F / tau,

@@ -1,8 +1,8 @@
 """prox_tnn with the learned rank proposer and randomized SVT (TP_METHOD_LEARNED).
 
-The plain Jacobi path is the fallback and the judge: every slice the sketch path does not
-certify is recomputed by it.  Bound for this mixed form: 1e-4 relative Frobenius error
-against the FP64 oracle.
+The plain Jacobi path is the fallback and the accuracy reference: every slice the sketch
+path does not certify is recomputed by it.  Bound for this mixed form: 1e-4 relative
+Frobenius error against the FP64 oracle.
 """
 import numpy as np
 import pytest
