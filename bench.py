@@ -19,6 +19,7 @@ The JSON line also carries:
                 on two alternating streams so copies overlap kernels;
   tprod         t-product TFLOP/s on A 2048x1024x64 times B 1024x1024x64 in FP32,
                 BF16x3 and 3xTF32 slice-GEMM arithmetic;
+  tran          the conjugate transpose of that A, GB/s against the HBM copy peak;
   trpca         the synthetic TRPCA-style loop: 50 ADMM iterations on a 240x320x100 tensor
                 (tubal rank 10, unit RMS, 10% of entries corrupted by U[-5, 5]), each one
                 prox_tnn call at tau = 1/mu (library) plus two elementwise updates; plain
@@ -510,6 +511,7 @@ def run_tp(args):
         line["e2e"] = e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device)
     if not args.no_tprod and rank == 0:
         line["tprod"] = tprod_leg(args, tp, synth, device)
+        line["tran"] = line["tprod"].pop("tran")
     if not args.no_factor and rank == 0:
         line["factor"] = factor_leg(args, tp, synth, device)
     if not args.no_trpca and rank == 0:
@@ -611,6 +613,7 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
                    "(page-locked host tensors; copies overlap kernels within and across steps)"}
 
 
+HBM_PEAK_GBS = 6685.5            # measured copy bandwidth (MEASURED_PEAKS.json)
 BF16_PEAK_TFLOPS = 1944.2        # measured dense bf16 (MEASURED_PEAKS.json, burst)
 TF32_PEAK_TFLOPS = 1051.2   # measured: torch.matmul 8192^3 FP32 with TF32 allowed, this GB300 pool
 
@@ -661,6 +664,25 @@ def tprod_leg(args, tp, synth, device):
         out[prec] = {"tflops": flops / (ms / 1e3) / 1e12, "ms_per_call": ms,
                      "stages_ms": {"rfft": st[0], "gemm": st[1], "irfft": st[2]},
                      "gemm_useful_tflops": gemm_tflops, "gemm_roofline": roof}
+    del C
+    # tran (Def. 2.2) of A: a pure permutation, one read and one write of every entry
+    AT = tp.empty(n2, n1, n3, device)
+    for _ in range(2):
+        tp.tran(A, out=AT)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        tp.tran(A, out=AT)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    nb = 8.0 * n1 * n2 * n3
+    out["tran"] = {"workload": "tran of A 2048x1024x64 (FP32, 512 MiB, larger than L2)",
+                   "ms_per_call": ms, "bytes": nb,
+                   "roofline": {"bound": "hbm", "achieved": nb / (ms / 1e3) / 1e9,
+                                "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                "frac": nb / (ms / 1e3) / 1e9 / HBM_PEAK_GBS}}
     return out
 
 
