@@ -1,0 +1,70 @@
+"""Host logic of bench.py and of the stream generator, checked on the CPU.
+
+The launch-count mirror (`svd_launch_groups`, `LEARNED_FIXED_LAUNCHES`) must agree with what
+the GPU ran: an ncu launch list of the learned batched prox on the 512-tensor batch showed
+22 kernel launches per call, 10 of them `svd_kernel` over two calls (5 Jacobi launch groups at
+the default CTA shape), and a bench run under the autotuned shape (target 7, 32 warps, shared
+launches) reported 210 launches over 10 steps, i.e. 4 Jacobi groups.
+"""
+import math
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1806_07247_gb300 import synth  # noqa: E402
+
+
+def _batch_shapes():
+    return [(s.n1, s.n2) for s in synth.batched_specs(512, 0)]
+
+
+def test_fixed_launches_of_a_learned_call():
+    # DFT, features, MLP, binning, 4 class launches, 4 x (collect + retry), inverse DFT
+    assert bench.LEARNED_FIXED_LAUNCHES == 17
+
+
+def test_jacobi_groups_match_the_measured_launch_lists():
+    shapes = _batch_shapes()
+    assert bench.svd_launch_groups(shapes) == 5
+    assert bench.LEARNED_FIXED_LAUNCHES + bench.svd_launch_groups(shapes) == 22
+    tuned = {"target_lane_pairs": 7, "max_warps": 32, "split_launches": 0}
+    assert bench.svd_launch_groups(shapes, tuned) == 4
+
+
+def test_split_launches_never_merge_fewer_groups():
+    shapes = _batch_shapes()
+    for e2 in (3, 5, 7):
+        for w in (8, 16, 32):
+            merged = bench.svd_launch_groups(shapes, {"target_lane_pairs": e2, "max_warps": w,
+                                                      "split_launches": 0})
+            split = bench.svd_launch_groups(shapes, {"target_lane_pairs": e2, "max_warps": w,
+                                                     "split_launches": 1})
+            assert split >= merged >= 1
+
+
+def test_stream_specs_are_seeded_and_in_range():
+    a = synth.stream_specs(300, 0)
+    assert a == synth.stream_specs(300, 0)
+    assert a != synth.stream_specs(300, 1)
+    ops = [c.op for c in a]
+    assert set(ops) == {"prox", "tprod"}
+    assert 0.35 < ops.count("prox") / len(ops) < 0.65
+    for c in a:
+        for sp in (c.a, c.b) if c.b else (c.a,):
+            assert 16 <= sp.n1 <= 512 and 16 <= sp.n2 <= 512
+            assert 4 <= sp.n3 <= 256 and 4 <= sp.r <= 40 and sp.noise == 0.02
+            nu = 0.02 * math.sqrt(sp.n3) * (math.sqrt(sp.n1) + math.sqrt(sp.n2))
+            assert math.isclose(sp.tau, 2.0 * nu, rel_tol=1e-12)
+        if c.op == "tprod":
+            assert c.b.n1 == c.a.n2 and c.b.n3 == c.a.n3
+        else:
+            assert c.b is None
+
+
+def test_job_throughput_is_weak_scaling_units_over_time():
+    # 9,359 slices per step, 10 steps in 72.3 ms -> 1.294M slices/s
+    assert math.isclose(bench.job_throughput(9359, 10, 72.3), 9359 * 10 / 0.0723)
