@@ -618,6 +618,61 @@ BF16_PEAK_TFLOPS = 1944.2        # measured dense bf16 (MEASURED_PEAKS.json, bur
 TF32_PEAK_TFLOPS = 1051.2   # measured: torch.matmul 8192^3 FP32 with TF32 allowed, this GB300 pool
 
 
+def tprod_oracle_sample(A32, B32, seconds):
+    """The FP64 oracle on the t-product workload, bounded (host cores, numpy/LAPACK threads):
+      literal   Eq. 9 entry by entry (a block row of bcirc(A) times a column of unfold(B),
+                `tprod_entries`) on seeded random (i, l, k) until `seconds`, extrapolated to
+                all n1*l*n3 entries; the sampled values are kept as the reference for the GPU
+                results' error;
+      dft       Eq. 10 on all n3 slices (`tprod_fourier`) for rows 0..63 of A and columns
+                0..63 of B, extrapolated to the whole product by n1*l / (64*64) (the slice
+                products dominate its cost).
+    Returns a dict with the timings, the sampled indices and reference values."""
+    import numpy as np
+
+    from oracle import tproduct as O
+    A = np.asarray(A32, dtype=np.float64)
+    B = np.asarray(B32, dtype=np.float64)
+    n1, n2, n3 = A.shape
+    l = B.shape[1]
+    h = n3 // 2 + 1
+    nreal = 2 if n3 % 2 == 0 else 1
+    flops = (2.0 * nreal + 8.0 * (h - nreal)) * n1 * n2 * l
+    rng = np.random.default_rng(20180619)
+    idx, ref, t = [], [], 0.0
+    while t < seconds or not idx:
+        blk = np.stack([rng.integers(0, n1, 64), rng.integers(0, l, 64),
+                        rng.integers(0, n3, 64)], axis=1)
+        t0 = time.perf_counter()
+        ref.append(O.tprod_entries(A, B, blk))
+        t += time.perf_counter() - t0
+        idx.append(blk)
+    idx = np.concatenate(idx)
+    ref = np.concatenate(ref)
+    lit_s = t / len(idx) * n1 * l * n3
+    m, ls = min(64, n1), min(64, l)
+    t0 = time.perf_counter()
+    O.tprod_fourier(A[:m], B[:, :ls])
+    blk_s = time.perf_counter() - t0
+    dft_s = blk_s * (n1 / m) * (l / ls)
+    return {"cores": os.cpu_count(), "kind": "oracle", "useful_flops": flops,
+            "literal": {"entries": int(len(idx)), "seconds": t, "extrapolated_s": lit_s,
+                        "tflops_equiv": flops / lit_s / 1e12},
+            "dft_domain": {"block": [m, n2, ls, n3], "seconds": blk_s, "extrapolated_s": dft_s,
+                           "tflops_equiv": flops / dft_s / 1e12},
+            "idx": idx, "ref": ref}
+
+
+def sampled_rel_err(C, oracle):
+    """||C[idx] - ref|| / ||ref|| over the oracle's sampled entries (C: an n1 x l x n3 tensor)."""
+    import numpy as np
+    import torch
+    idx = torch.as_tensor(oracle["idx"], dtype=torch.long, device=C.device)
+    got = C[idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+    ref = oracle["ref"]
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
 def tprod_leg(args, tp, synth, device):
     """t-product of A 2048x1024x64 and B 1024x1024x64 (one rank) in the three slice-GEMM
     arithmetics. Useful flops = (2 #real + 8 #complex slices) n1 n2 l; the split forms run
@@ -625,6 +680,10 @@ def tprod_leg(args, tp, synth, device):
     import torch
     g = synth.gemm(0)
     A, B = tp.to_device(g["A"], device), tp.to_device(g["B"], device)
+    try:
+        oracle = tprod_oracle_sample(g["A"], g["B"], args.cpu_seconds / 3)
+    except Exception as e:  # a host-side baseline; the GPU legs below stand without it
+        oracle = {"error": repr(e)}
     del g
     n1, n2, l, n3 = 2048, 1024, 1024, 64
     C = tp.empty(n1, l, n3, device)
@@ -664,6 +723,14 @@ def tprod_leg(args, tp, synth, device):
         out[prec] = {"tflops": flops / (ms / 1e3) / 1e12, "ms_per_call": ms,
                      "stages_ms": {"rfft": st[0], "gemm": st[1], "irfft": st[2]},
                      "gemm_useful_tflops": gemm_tflops, "gemm_roofline": roof}
+        if "ref" in oracle:
+            try:
+                out[prec]["sampled_rel_err_vs_oracle"] = sampled_rel_err(C, oracle)
+            except Exception as e:
+                out[prec]["sampled_rel_err_vs_oracle"] = repr(e)
+    oracle.pop("idx", None)
+    oracle.pop("ref", None)
+    out["oracle"] = oracle
     del C
     # tran (Def. 2.2) of A: a pure permutation, one read and one write of every entry
     AT = tp.empty(n2, n1, n3, device)

@@ -68,3 +68,26 @@ def test_stream_specs_are_seeded_and_in_range():
 def test_job_throughput_is_weak_scaling_units_over_time():
     # 9,359 slices per step, 10 steps in 72.3 ms -> 1.294M slices/s
     assert math.isclose(bench.job_throughput(9359, 10, 72.3), 9359 * 10 / 0.0723)
+
+
+def test_tprod_oracle_sample_and_sampled_error_on_a_column_major_tensor():
+    # the bench's full-size tprod error: sampled Eq. 9 entries against a result laid out as
+    # the library lays it out (column-major n1 x l x n3)
+    import numpy as np
+    import torch
+
+    from oracle import tproduct as O
+    rng = np.random.Generator(np.random.PCG64(3))
+    A = rng.standard_normal((40, 24, 6)).astype(np.float32)
+    B = rng.standard_normal((24, 30, 6)).astype(np.float32)
+    o = bench.tprod_oracle_sample(A, B, 0.05)
+    assert o["literal"]["entries"] >= 64 and o["literal"]["extrapolated_s"] > 0
+    assert o["dft_domain"]["block"] == [40, 24, 30, 6] and o["dft_domain"]["extrapolated_s"] > 0
+    C = O.tprod(A, B)
+    Ct = torch.from_numpy(np.ascontiguousarray(C.transpose(2, 1, 0))).permute(2, 1, 0)
+    assert Ct.stride() == (1, 40, 40 * 30)
+    assert bench.sampled_rel_err(Ct, o) < 1e-14
+    # a wrong entry is seen
+    i, l, k = o["idx"][0]
+    Ct[i, l, k] += 1.0
+    assert bench.sampled_rel_err(Ct, o) > 1e-6
