@@ -246,20 +246,28 @@ def jacobi_model_flops(shapes, sweeps):
 
 
 # ----------------------------------------------------------------------------- oracle legs
-def oracle_sample(specs, seed, seconds, max_items=None):
+def oracle_sample(specs, seed, seconds, max_items=None, inputs=None, check=None):
     """Time the FP64 oracle's prox_tnn on tensors 0, 1, ... of the batch until `seconds`
-    of CPU work (at least one tensor). Returns (slices/s, slices, tensors, seconds)."""
+    of CPU work (at least one tensor). Returns (slices/s, slices, tensors, seconds).
+    inputs(i), if given, returns tensor i as the FP32 array the GPU received (else the oracle
+    forms it from the generator's factors); check(i, W), if given, receives each oracle
+    result (outside the timed region)."""
     import numpy as np
 
     from oracle import tproduct as O
     from paper_1806_07247_gb300 import synth
     done_slices, done, t_total = 0, 0, 0.0
     for i, s in enumerate(specs):
-        f = synth.batched_tensor(s, i, seed)
-        X = (O.tprod_fourier(f["P"], f["Q"]) + f["E"]).astype(np.float32)
+        if inputs is not None:
+            X = inputs(i)
+        else:
+            f = synth.batched_tensor(s, i, seed)
+            X = (O.tprod_fourier(f["P"], f["Q"]) + f["E"]).astype(np.float32)
         t0 = time.perf_counter()
-        O.prox_tnn(X, s.tau)
+        W = O.prox_tnn(X, s.tau)
         t_total += time.perf_counter() - t0
+        if check is not None:
+            check(i, W)
         done_slices += s.n3 // 2 + 1
         done += 1
         if t_total >= seconds or (max_items and done >= max_items):
@@ -522,7 +530,30 @@ def run_tp(args):
         except tp.TpError as e:  # reported in the line; the measured legs above stand
             line["stream"] = {"error": str(e)}
     if rank == 0:
-        rate, sl, nt, secs = oracle_sample(specs, rank, args.cpu_seconds)
+        # the oracle on the GPU's own inputs: timed for the baseline, and its results give the
+        # plain and learned outputs' error at the bench configuration
+        import numpy as np
+        par = {"tensors": 0, "plain_max_rel": 0.0, "learned_max_rel": 0.0,
+               "bound": {"plain": 1e-5, "learned": 1e-4},
+               "note": "relative Frobenius error per tensor against the FP64 oracle on the "
+                       "same FP32 inputs, over the tensors of the cpu_baseline sample"}
+
+        def gpu_input(i):
+            return tp.to_numpy(Ys[i])
+
+        def check(i, W):
+            nW = float(np.linalg.norm(W)) or 1.0
+            for key, X in (("plain_max_rel", X_plain[i]), ("learned_max_rel", Xs[i])):
+                par[key] = max(par[key], float(np.linalg.norm(tp.to_numpy(X) - W)) / nW)
+            par["tensors"] += 1
+
+        try:
+            rate, sl, nt, secs = oracle_sample(specs, rank, args.cpu_seconds, inputs=gpu_input,
+                                               check=check)
+        except Exception as e:  # the baseline still prints without the check
+            par = {"error": repr(e)}
+            rate, sl, nt, secs = oracle_sample(specs, rank, args.cpu_seconds)
+        line["parity_vs_oracle"] = par
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(),
                                 "kind": "oracle",
                                 "sample": f"FP64 oracle prox_tnn on tensors 0-{nt - 1} of the batch "

@@ -91,3 +91,23 @@ def test_tprod_oracle_sample_and_sampled_error_on_a_column_major_tensor():
     i, l, k = o["idx"][0]
     Ct[i, l, k] += 1.0
     assert bench.sampled_rel_err(Ct, o) > 1e-6
+
+
+def test_oracle_sample_takes_given_inputs_and_reports_each_result():
+    import numpy as np
+
+    from oracle import tproduct as O
+    specs = synth.batched_specs(512, 0)[:3]
+    given = {}
+
+    def inputs(i):
+        s = specs[i]
+        given[i] = synth.normal(np.random.Generator(np.random.PCG64(i)), (s.n1, s.n2, s.n3))
+        return given[i]
+
+    seen = {}
+    rate, sl, nt, secs = bench.oracle_sample(specs, 0, 0.0, max_items=2, inputs=inputs,
+                                             check=lambda i, W: seen.setdefault(i, W))
+    assert nt == 1 and sorted(seen) == [0] and rate > 0 and secs > 0
+    assert sl == specs[0].n3 // 2 + 1
+    np.testing.assert_allclose(seen[0], O.prox_tnn(given[0], specs[0].tau), rtol=0, atol=1e-12)
