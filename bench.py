@@ -59,7 +59,30 @@ UNIT = "slices/s"
 WORKLOAD = ("batched prox_tnn, FP32: 512 tensors, n1,n2~U{16..160}, n3~U{4..64}, tubal rank "
             "r~U{2..12} t-product of N(0,1) factors + N(0,0.05^2) noise, tau = 2x noise level")
 SM_COUNT = 152
-FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * 2.070e9 / 1e12   # FFMA lanes x 2 flops x max SM clock
+
+
+def load_peaks(path=os.path.join(ROOT, "MEASURED_PEAKS.json")):
+    """Roofline denominators: the measured copy bandwidth, dense bf16 rate (burst) and maximum
+    SM clock from MEASURED_PEAKS.json when it is present, else the values recorded from it on
+    this GB300 pool."""
+    peaks = {"hbm_gbs": 6685.5, "bf16_tflops": 1944.2, "sm_max_mhz": 2070.0,
+             "source": "recorded values (MEASURED_PEAKS.json absent)"}
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz"):
+            v = d.get(k)
+            if isinstance(v, (int, float)) and v > 0:
+                peaks[k] = float(v)
+        peaks["source"] = "MEASURED_PEAKS.json"
+    except (OSError, ValueError, AttributeError):
+        pass
+    return peaks
+
+
+PEAKS = load_peaks()
+# FFMA lanes x 2 flops x maximum SM clock
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * PEAKS["sm_max_mhz"] * 1e6 / 1e12
 
 
 def parse():
@@ -513,6 +536,9 @@ def run_tp(args):
             "dft_gbs": {"rfft": dft_gbs, "irfft": idft_gbs}}
 
     line["clocks"] = learned["clocks"]
+    line["peaks"] = {"source": PEAKS["source"], "hbm_gbs": HBM_PEAK_GBS,
+                     "bf16_tflops": BF16_PEAK_TFLOPS, "tf32_tflops": TF32_PEAK_TFLOPS,
+                     "fp32_alu_tflops": FP32_PEAK_TFLOPS}
     if shape:
         tp.jacobi_shape_set(None)  # the other legs run at the default shape
     if not args.no_e2e:
@@ -644,8 +670,8 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
                    "(page-locked host tensors; copies overlap kernels within and across steps)"}
 
 
-HBM_PEAK_GBS = 6685.5            # measured copy bandwidth (MEASURED_PEAKS.json)
-BF16_PEAK_TFLOPS = 1944.2        # measured dense bf16 (MEASURED_PEAKS.json, burst)
+HBM_PEAK_GBS = PEAKS["hbm_gbs"]          # measured copy bandwidth
+BF16_PEAK_TFLOPS = PEAKS["bf16_tflops"]  # measured dense bf16, burst
 TF32_PEAK_TFLOPS = 1051.2   # measured: torch.matmul 8192^3 FP32 with TF32 allowed, this GB300 pool
 
 

@@ -111,3 +111,16 @@ def test_oracle_sample_takes_given_inputs_and_reports_each_result():
     assert nt == 1 and sorted(seen) == [0] and rate > 0 and secs > 0
     assert sl == specs[0].n3 // 2 + 1
     np.testing.assert_allclose(seen[0], O.prox_tnn(given[0], specs[0].tau), rtol=0, atol=1e-12)
+
+
+def test_peaks_come_from_the_measured_file_or_the_recorded_values(tmp_path):
+    import json
+    p = tmp_path / "peaks.json"
+    p.write_text(json.dumps({"hbm_gbs": 7000.0, "bf16_tflops": 2000.0, "sm_max_mhz": 2000.0}))
+    got = bench.load_peaks(str(p))
+    assert (got["hbm_gbs"], got["bf16_tflops"], got["sm_max_mhz"]) == (7000.0, 2000.0, 2000.0)
+    assert got["source"] == "MEASURED_PEAKS.json"
+    miss = bench.load_peaks(str(tmp_path / "absent.json"))
+    assert miss["source"].startswith("recorded") and miss["hbm_gbs"] == 6685.5
+    # FP32 ALU peak: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
+    assert abs(152 * 128 * 2 * 2.070e9 / 1e12 - 80.54784) < 1e-9
