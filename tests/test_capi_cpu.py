@@ -110,3 +110,19 @@ def test_jacobi_shape_and_autotune_argument_checks(L):
     assert L.tp_autotune_jacobi(d, 1, 2, ctypes.byref(sh), ms, None) == tp.TP_ERR_INVALID_ARG
     d[0].n3, d[0].n1 = 4, tp.MAX_SVD_DIM + 1
     assert L.tp_autotune_jacobi(d, 1, 2, ctypes.byref(sh), ms, None) == tp.TP_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_compiles_as_plain_c_and_cxx(lang, std, tmp_path):
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if not cc:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("use." + ("c" if lang == "c" else "cpp"))
+    src.write_text('#include "tp.h"\n'
+                   "int probe(void) { tp_options o; tp_options_default(&o);\n"
+                   "  tp_jacobi_shape s; (void)s; return (int)o.host_parts + (int)TP_OK; }\n")
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        f"-I{os.path.dirname(HEADER)}", str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
