@@ -58,7 +58,7 @@ METRIC = "prox_tnn slices/s & tprod TFLOP/s vs plain FP32 GPU path at ≤1e-4 re
 UNIT = "slices/s"
 WORKLOAD = ("batched prox_tnn, FP32: 512 tensors, n1,n2~U{16..160}, n3~U{4..64}, tubal rank "
             "r~U{2..12} t-product of N(0,1) factors + N(0,0.05^2) noise, tau = 2x noise level")
-SM_COUNT = 152
+SM_COUNT_DEFAULT = 152  # GB300; the device's own count replaces it when a GPU is present
 
 
 def load_peaks(path=os.path.join(ROOT, "MEASURED_PEAKS.json")):
@@ -81,8 +81,26 @@ def load_peaks(path=os.path.join(ROOT, "MEASURED_PEAKS.json")):
 
 
 PEAKS = load_peaks()
-# FFMA lanes x 2 flops x maximum SM clock
-FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * PEAKS["sm_max_mhz"] * 1e6 / 1e12
+
+
+def sm_count() -> int:
+    """Multiprocessors of the current CUDA device (the GB300 count without a GPU)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device())
+                       .multi_processor_count)
+    except Exception:  # pragma: no cover - no torch or no driver
+        pass
+    return SM_COUNT_DEFAULT
+
+
+def fp32_peak_tflops(sms: int | None = None) -> float:
+    """FFMA lanes (128 per SM) x 2 flops x maximum SM clock."""
+    return (sms or sm_count()) * 128 * 2 * PEAKS["sm_max_mhz"] * 1e6 / 1e12
+
+
+FP32_PEAK_TFLOPS = fp32_peak_tflops(SM_COUNT_DEFAULT)  # replaced in run_tp by the device's
 
 
 def parse():
@@ -409,6 +427,7 @@ def time_prox(tp, args, Ys, Xs, taus, descs, method, world, barrier, device, clo
 
 
 def run_tp(args):
+    global FP32_PEAK_TFLOPS
     import torch
     import torch.distributed as dist
 
@@ -417,6 +436,7 @@ def run_tp(args):
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
+    FP32_PEAK_TFLOPS = fp32_peak_tflops()
     if world > 1:
         dist.init_process_group("nccl", device_id=device)
 

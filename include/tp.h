@@ -99,6 +99,16 @@ typedef struct tp_options {
                             own kernels; one part leaves that overlap to a caller that issues
                             consecutive calls on alternating streams (their copies then overlap
                             each other's kernels, with no per-part kernel tails) */
+    int32_t* counts_out; /* optional DEVICE array, same indexing as sweeps_out (prox_tnn and
+                            its batched forms): #{sigma > tau} of the slice, the count of
+                            Algorithm 3's kept singular values. A singular value within 1e-6
+                            relative of tau is re-decided from its column norm accumulated in
+                            FP64 */
+    int32_t jacobi_fp64; /* 0 (default): Jacobi rotation parameters in compensated FP32;
+                            1: rotation angle, cosine and sine in FP64 from the FP32 dot
+                            products (GB300's FP64 rate is about 1/64 of FP32: slower, for
+                            accuracy studies). Either way the convergence test of a pair whose
+                            FP32 test is within a factor 2 of the tolerance is re-done in FP64 */
 } tp_options;
 
 #define TP_STAGE_EVENTS 6
@@ -347,22 +357,30 @@ tp_status tp_autotune_jacobi(const tp_tensor_desc* descs, int64_t count, int32_t
  * inside a time-critical loop, or a process whose device memory is handed out by another
  * framework's allocator so that the library may not obtain any of its own.
  *
- * It computes exactly what tp_prox_tnn computes, with the same kernels, but all scratch (the
- * half spectrum, the per-slice job records and the status word) lives in one file-scope
- * static device array of TP_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads the
- * library holds until the process exits. A tensor fits when
- *   n1*n2*(n3/2+1)*8 bytes of spectrum (+ the working matrices of slices larger than shared
- *   memory) + about 80*(n3/2+1) bytes of job records <= 16 MiB;
- * larger tensors are rejected with TP_ERR_UNSUPPORTED before anything is enqueued. The call
- * never calls cudaMalloc, cudaFree or any allocating routine.
+ * It computes exactly what tp_prox_tnn computes with TP_METHOD_JACOBI, with the same kernels,
+ * but all scratch (the half spectrum, the per-slice job records and the status word) lives in
+ * one file-scope static device array of TP_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that
+ * loads the library holds until the process exits. With h = n3/2 + 1 and R(x) = x rounded up
+ * to a multiple of 256, a tensor fits when
+ *   R(512 + h * TP_NOALLOC_JOB_BYTES) + R(8 * n1 * n2 * h) + R(8 * W * h) <= 16 MiB,
+ * where W = 0 when a slice's working matrix fits in shared memory (min(n1,n2) * ld complex
+ * values, ld = max(n1,n2) rounded up to a multiple of 16, 32 or 64, below about 226 KB) and
+ * W = min(n1,n2) * ld rounded up to a multiple of 32 otherwise. Larger tensors are rejected
+ * with TP_ERR_UNSUPPORTED before anything is enqueued. The call never calls cudaMalloc,
+ * cudaFree or any allocating routine.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
  * and fills the twiddle table, with that device current; make it before any stream capture.
  * All calls share the one array and it keeps the last call's contents (the status word is
  * cleared at the start of every call): calls that overlap on the GPU -- on different
  * streams, or from several host threads without ordering -- race and must not be issued.
- * Arguments, options, errors and aliasing (X == Y allowed) are those of tp_prox_tnn.
+ * Arguments, errors and aliasing (X == Y allowed) are those of tp_prox_tnn. Options are
+ * checked as there; in addition method must be TP_METHOD_JACOBI and stage_events,
+ * slice_flags_out and sketch_width_out must be NULL (TP_ERR_INVALID_ARG otherwise).
+ * sweeps_out and counts_out (h entries each) are written; precision, econ and host_parts
+ * have no effect.
  */
 #define TP_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define TP_NOALLOC_JOB_BYTES 128
 tp_status tp_prox_tnn_noalloc(const float* Y, float* X, int64_t n1, int64_t n2, int64_t n3,
                               double tau, const tp_options* opts, void* stream);
 

@@ -125,6 +125,8 @@ struct Opts {
     int32_t* slice_flags_out = nullptr;
     int32_t* sketch_width_out = nullptr;
     int host_parts = 2;
+    int32_t* counts_out = nullptr;
+    int jacobi_fp64 = 0;
     // Record stage boundary i (0..3) on the stream when the caller asked for it.
     tp_status mark(int i, cudaStream_t s) const {
         if (!events || !events[i]) return TP_OK;
@@ -161,8 +163,22 @@ tp_status resolve(const tp_options* o, Opts* r) {
     r->sketch_width_out = o->sketch_width_out;
     if (o->host_parts < 0 || o->host_parts > 2) return TP_ERR_INVALID_ARG;
     r->host_parts = o->host_parts == 0 ? 2 : o->host_parts;
+    if (o->jacobi_fp64 != 0 && o->jacobi_fp64 != 1) return TP_ERR_INVALID_ARG;
+    r->jacobi_fp64 = o->jacobi_fp64;
+    r->counts_out = o->counts_out;
     return TP_OK;
 }
+
+}  // namespace
+
+namespace tp {
+tp_status validate_options(const tp_options* o) {
+    Opts r;
+    return resolve(o, &r);
+}
+}  // namespace tp
+
+namespace {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -293,6 +309,7 @@ struct SvdBatch {
         p.tol = (float)o.jacobi_tol;
         p.sweeps_out = o.sweeps_out;
         p.status = d_status;
+        p.fp64_rotation = o.jacobi_fp64;
         size_t i = 0;
         while (i < items.size()) {
             size_t j = i;
@@ -462,7 +479,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             j.sweeps_index = (int32_t)sidx;
             j.tau = d[t].tau;
             j.skip = learned ? flags + sidx : nullptr;
-            j.count_out = train ? counts + sidx : nullptr;
+            j.count_out = train ? counts + sidx : (o.counts_out ? o.counts_out + sidx : nullptr);
             if (need_feat) natural.push_back(j);
             it.cfg = cfg[t];
             const int64_t m = std::max(n1, n2), n = std::min(n1, n2);
@@ -514,7 +531,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             SketchParams sp;
             sp.ell = ell;
             sp.flag = flags;
-            sp.count = counts;
+            sp.count = o.counts_out ? o.counts_out : counts;
             sp.njobs = (int)slices;
             sp.seed = 0x9e3779b9u;
             sp.power_iters = 1;
@@ -726,6 +743,8 @@ void tp_options_default(tp_options* opts) {
     opts->slice_flags_out = nullptr;
     opts->sketch_width_out = nullptr;
     opts->host_parts = 2;
+    opts->counts_out = nullptr;
+    opts->jacobi_fp64 = 0;
 }
 
 const char* tp_last_error_string(void) {
@@ -1415,6 +1434,7 @@ tp_status tp_prox_tnn_batched_host(const tp_tensor_desc* descs, int64_t count,
         oc.sweeps_out = o.sweeps_out ? o.sweeps_out + slice_base : nullptr;
         oc.slice_flags_out = o.slice_flags_out ? o.slice_flags_out + slice_base : nullptr;
         oc.sketch_width_out = o.sketch_width_out ? o.sketch_width_out + slice_base : nullptr;
+        oc.counts_out = o.counts_out ? o.counts_out + slice_base : nullptr;
         TP_TRY(prox_batched(part.data(), (int64_t)part.size(), oc, cs, nullptr, d_status));
         slice_base += part_slices;
         TP_CUDA(cudaEventRecord(ev_done, cs));

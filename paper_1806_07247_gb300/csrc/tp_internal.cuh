@@ -117,7 +117,11 @@ struct SvdParams {
     float tol;           // <= 0: default per slice
     int32_t* sweeps_out; // device, may be null
     uint32_t* status;    // device status word (bit 0: not converged)
+    int fp64_rotation = 0;  // 1: rotation parameters in FP64 (tp_options.jacobi_fp64)
 };
+
+// Checks a tp_options record as every entry point does (TP_OK or TP_ERR_INVALID_ARG).
+tp_status validate_options(const tp_options* o);
 
 // Which launch configuration a slice of size n1 x n2 needs under `shape` (NULL: default).
 bool svd_plan(int n1, int n2, int mode, SvdConfig* cfg, const JacobiShape* shape = nullptr);

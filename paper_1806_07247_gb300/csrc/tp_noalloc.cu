@@ -9,8 +9,9 @@
 // Make that first call before any stream capture.
 //
 // Scratch layout (offsets in bytes): [0, 256) status word, [256, 512) the two DFT job
-// records, then the per-slice SVD job records, then the half spectrum (and, for slices
-// that do not fit in shared memory, their working matrices).  The job records are written
+// records, then room for TP_NOALLOC_JOB_BYTES per slice of SVD job records (rounded up to
+// 256), then the half spectrum (and, for slices that do not fit in shared memory, their
+// working matrices).  The job records are written
 // by a small kernel, so a call issues no host-to-device copy either.  Every call reuses the
 // same array and it keeps the previous call's contents: the status word is cleared at the
 // start of each call, everything else is fully rewritten before it is read.  Two calls
@@ -29,6 +30,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[TP_NOALLOC_SCRA
 constexpr size_t kStatusOff = 0;
 constexpr size_t kFftOff = 256;
 constexpr size_t kSvdOff = 512;
+static_assert(sizeof(SvdJob) <= TP_NOALLOC_JOB_BYTES, "job record budget of tp.h");
+static_assert(2 * sizeof(FftJob) <= kSvdOff - kFftOff, "DFT job records");
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -55,7 +58,8 @@ cudaError_t scratch_base(void** out) {
 // Fills the two DFT job records and the h SVD job records inside the scratch array.
 __global__ void noalloc_jobs_kernel(FftJob* fft, SvdJob* svd, const float* Y, float* X,
                                     float2* spec, float2* work, int64_t work_elems, int n1,
-                                    int n2, int n3, double tau, int with_sweeps) {
+                                    int n2, int n3, double tau, int with_sweeps,
+                                    int32_t* counts_out) {
     const int64_t P = (int64_t)n1 * n2;
     const int h = free_slices(n3);
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,7 +90,7 @@ __global__ void noalloc_jobs_kernel(FftJob* fft, SvdJob* svd, const float* Y, fl
         j.sweeps_index = with_sweeps ? k : -1;
         j.tau = tau;
         j.skip = nullptr;
-        j.count_out = nullptr;
+        j.count_out = counts_out ? counts_out + k : nullptr;
         svd[k] = j;
     }
 }
@@ -103,9 +107,10 @@ extern "C" tp_status tp_prox_tnn_noalloc(const float* Y, float* X, int64_t n1, i
     tp_options o;
     tp_options_default(&o);
     if (opts) o = *opts;
-    if (o.precision < TP_PREC_FP32 || o.precision > TP_PREC_BF16X3 || (o.econ != 0 && o.econ != 1) ||
-        o.max_sweeps < 0 || o.max_sweeps > 1000 || (o.sync != 0 && o.sync != 1) ||
-        o.jacobi_tol != o.jacobi_tol || o.jacobi_tol >= 1.0)
+    // the options every entry point checks, then those this path cannot honour: it runs the
+    // Jacobi SVT only and records no stage events or sketch outputs
+    if (validate_options(&o) != TP_OK) return TP_ERR_INVALID_ARG;
+    if (o.method != TP_METHOD_JACOBI || o.stage_events || o.slice_flags_out || o.sketch_width_out)
         return TP_ERR_INVALID_ARG;
     if (n1 < 0 || n2 < 0 || n3 < 0 || tau != tau || tau < 0.0) return TP_ERR_INVALID_ARG;
     if (n3 > TP_MAX_N3 || n1 > TP_MAX_SVD_DIM || n2 > TP_MAX_SVD_DIM) return TP_ERR_UNSUPPORTED;
@@ -117,7 +122,7 @@ extern "C" tp_status tp_prox_tnn_noalloc(const float* Y, float* X, int64_t n1, i
     SvdConfig cfg;
     if (!svd_plan((int)n1, (int)n2, SVD_PROX, &cfg)) return TP_ERR_UNSUPPORTED;
     // sizes must fit the fixed array; reject anything larger before touching the GPU
-    const size_t spec_off = round256(kSvdOff + sizeof(SvdJob) * (size_t)h);
+    const size_t spec_off = round256(kSvdOff + (size_t)TP_NOALLOC_JOB_BYTES * h);
     const size_t spec_bytes = round256(sizeof(float2) * (size_t)(P * h));
     const size_t work_bytes = round256(sizeof(float2) * (size_t)(cfg.work_elems * h));
     if (spec_off + spec_bytes + work_bytes > (size_t)TP_NOALLOC_SCRATCH_BYTES)
@@ -138,7 +143,7 @@ extern "C" tp_status tp_prox_tnn_noalloc(const float* Y, float* X, int64_t n1, i
     if (cudaMemsetAsync(status, 0, sizeof(uint32_t), s) != cudaSuccess) return TP_ERR_CUDA;
     noalloc_jobs_kernel<<<(h + 127) / 128, 128, 0, s>>>(fft, svd, Y, X, spec, work, cfg.work_elems,
                                                         (int)n1, (int)n2, (int)n3, tau,
-                                                        o.sweeps_out ? 1 : 0);
+                                                        o.sweeps_out ? 1 : 0, o.counts_out);
     if (cudaGetLastError() != cudaSuccess) return TP_ERR_CUDA;
     const bool vec = (P % 4 == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15u) == 0) &&
                      ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
@@ -158,6 +163,7 @@ extern "C" tp_status tp_prox_tnn_noalloc(const float* Y, float* X, int64_t n1, i
     p.tol = (float)o.jacobi_tol;
     p.sweeps_out = o.sweeps_out;
     p.status = status;
+    p.fp64_rotation = o.jacobi_fp64;
     if (launch_svd(L, p, s) != cudaSuccess) return TP_ERR_CUDA;
     if (launch_irfft(fft + 1, 1, tiles, (int)n3, (int)n3, vec, s) != cudaSuccess) return TP_ERR_CUDA;
     if (!o.sync) return TP_OK;

@@ -130,7 +130,7 @@ __device__ __forceinline__ void group_sum4(float& v0, float& v1, float& v2, floa
 template <int LP, int MAXE2, bool WITH_V>
 __device__ __forceinline__ bool jacobi_pair(float2* gp, float2* gq, int e2, int sub, int lane,
                                             float tol2, bool active, float2* vp, float2* vq,
-                                            int nv) {
+                                            int nv, bool fp64_rot) {
     float4* p4 = reinterpret_cast<float4*>(gp);
     float4* q4 = reinterpret_cast<float4*>(gq);
     float4 xp[MAXE2], xq[MAXE2];
@@ -149,23 +149,45 @@ __device__ __forceinline__ bool jacobi_pair(float2* gp, float2* gq, int e2, int 
     }
     group_sum4<LP>(al, be, gr, gi, sub, lane);
     const float ag2 = fmaf(gr, gr, gi * gi);
-    // |gamma| > tol sqrt(alpha beta), squared
-    if (!active || !(ag2 > (tol2 * al) * be)) return false;
-    const float inv_ag = rsqrt_nr(ag2);
-    const float zeta = 0.5f * (be - al) * inv_ag;
-    const float az = fabsf(zeta);
-    float t;
-    if (az > 1e8f) {
-        t = 0.5f * rcp_nr(az);
-    } else {
-        const float q = fmaf(zeta, zeta, 1.f);
-        t = rcp_nr(az + q * rsqrt_nr(q));
+    // |gamma| > tol sqrt(alpha beta), squared; a test within a factor 2 of the threshold (or
+    // with the threshold below the FP32 normal range) is decided again in FP64
+    const float thr = (tol2 * al) * be;
+    bool rot = ag2 > thr;
+    if ((ag2 > 0.5f * thr && ag2 < 2.f * thr) || thr < 1.17549435e-38f) {
+        const double agd = fma((double)gr, (double)gr, (double)gi * (double)gi);
+        rot = agd > ((double)tol2 * (double)al) * (double)be;
     }
-    t = copysignf(t, zeta);
-    float c, s;
-    rotation_cs(t, c, s);
-    const float er = gr * inv_ag, ei = gi * inv_ag;
-    const float sr = s * er, si = s * ei;  // s e; s conj(e) = (sr, -si)
+    if (!active || !rot) return false;
+    float c, sr, si;  // s e = (sr, si); s conj(e) = (sr, -si)
+    if (fp64_rot) {
+        // zeta, t, c, s and the phase e = gamma / |gamma| in FP64 from the FP32 dot products
+        const double dgr = gr, dgi = gi;
+        const double ag = sqrt(fma(dgr, dgr, dgi * dgi));
+        const double zeta = 0.5 * ((double)be - (double)al) / ag;
+        const double az = fabs(zeta);
+        const double t = copysign(1.0 / (az + sqrt(fma(zeta, zeta, 1.0))), zeta);
+        const double cd = 1.0 / sqrt(fma(t, t, 1.0));
+        const double sd = cd * t;
+        c = (float)cd;
+        sr = (float)(sd * (dgr / ag));
+        si = (float)(sd * (dgi / ag));
+    } else {
+        const float inv_ag = rsqrt_nr(ag2);
+        const float zeta = 0.5f * (be - al) * inv_ag;
+        const float az = fabsf(zeta);
+        float t;
+        if (az > 1e8f) {
+            t = 0.5f * rcp_nr(az);
+        } else {
+            const float q = fmaf(zeta, zeta, 1.f);
+            t = rcp_nr(az + q * rsqrt_nr(q));
+        }
+        t = copysignf(t, zeta);
+        float s;
+        rotation_cs(t, c, s);
+        sr = s * (gr * inv_ag);
+        si = s * (gi * inv_ag);
+    }
     // g_p <- c g_p - s conj(e) g_q,  g_q <- s e g_p + c g_q
 #pragma unroll
     for (int i = 0; i < MAXE2; ++i) {
@@ -298,7 +320,7 @@ __global__ void __launch_bounds__(MAXE2 >= 8 ? 512 : 1024, 1)
                 bool did = jacobi_pair<LP, MAXE2, MODE == SVD_FULL>(
                     G + (size_t)p * ld, G + (size_t)q * ld, e2, sub, lane, tol2, active,
                     MODE == SVD_FULL ? VG + (size_t)p * n : nullptr,
-                    MODE == SVD_FULL ? VG + (size_t)q * n : nullptr, n);
+                    MODE == SVD_FULL ? VG + (size_t)q * n : nullptr, n, prm.fp64_rotation != 0);
                 if (did && sub == 0) s_rot = 1;
             }
             __syncthreads();
@@ -341,17 +363,44 @@ __global__ void __launch_bounds__(MAXE2 >= 8 ? 512 : 1024, 1)
     }
 
     if (MODE == SVD_PROX) {
-        // kept set {sigma_j > tau}, decided in FP64, in column order (ballot compaction)
+        // kept set {sigma_j > tau} in column order (ballot compaction); the comparison is in
+        // FP64, and a sigma within 1e-6 relative of tau is first recomputed as the column norm
+        // accumulated in FP64 (the FP32 norm's rounding could put it on the wrong side)
+        int any_near = 0;
         for (int c = tid; c < n; c += T) {
             const double sd = (double)sig[c];
             const int f = sd > J.tau;
             flag[c] = f;
+            any_near |= fabs(sd - J.tau) <= 1e-6 * J.tau;
             if (f) {
                 ratio[c] = (float)((sd - J.tau) / sd);
                 invs[c] = 1.f / sig[c];
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(any_near)) {
+            for (int cb = 0; cb < n; cb += slots) {  // uniform over the block
+                const int c = cb + slot;
+                const bool near = c < n && fabs((double)sig[c] - J.tau) <= 1e-6 * J.tau;
+                double s2 = 0.0;
+                if (near) {
+                    const float2* g = G + (size_t)c * ld;
+                    for (int e = sub; e < m; e += LP)
+                        s2 = fma((double)g[e].x, (double)g[e].x, fma((double)g[e].y, (double)g[e].y, s2));
+                }
+#pragma unroll
+                for (int o = LP / 2; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                if (near && sub == 0) {
+                    const double sd = sqrt(s2);
+                    const int f = sd > J.tau;
+                    flag[c] = f;
+                    if (f) {
+                        ratio[c] = (float)((sd - J.tau) / sd);
+                        invs[c] = (float)(1.0 / sd);
+                    }
+                }
+            }
+            __syncthreads();
+        }
         if (warp == 0) {
             int cnt = 0;
             for (int base = 0; base < n; base += 32) {

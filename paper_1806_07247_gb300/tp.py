@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
                 ("jacobi_tol", ctypes.c_double), ("sweeps_out", ctypes.c_void_p),
                 ("stage_events", ctypes.c_void_p), ("method", ctypes.c_int32),
                 ("slice_flags_out", ctypes.c_void_p), ("sketch_width_out", ctypes.c_void_p),
-                ("host_parts", ctypes.c_int32)]
+                ("host_parts", ctypes.c_int32), ("counts_out", ctypes.c_void_p),
+                ("jacobi_fp64", ctypes.c_int32)]
 STAGE_EVENTS = 6
 
 
@@ -130,11 +131,14 @@ def options(precision: str = "fp32", econ: bool = False, max_sweeps: int = 30, s
             jacobi_tol: float = 0.0, sweeps_out: torch.Tensor | None = None,
             stage_events=None, method: str = "jacobi",
             slice_flags_out: torch.Tensor | None = None,
-            sketch_width_out: torch.Tensor | None = None, host_parts: int = 2) -> Options:
+            sketch_width_out: torch.Tensor | None = None, host_parts: int = 2,
+            counts_out: torch.Tensor | None = None, jacobi_fp64: bool = False) -> Options:
     """tp_options; stage_events is a list of STAGE_EVENTS recorded torch.cuda.Event (tp.h)."""
     o = Options()
     o.method = METHODS[method]
-    for name, t in (("slice_flags_out", slice_flags_out), ("sketch_width_out", sketch_width_out)):
+    o.jacobi_fp64 = int(bool(jacobi_fp64))
+    for name, t in (("slice_flags_out", slice_flags_out), ("sketch_width_out", sketch_width_out),
+                    ("counts_out", counts_out)):
         if t is not None:
             assert t.is_cuda and t.dtype == torch.int32
             setattr(o, name, t.data_ptr())

@@ -55,6 +55,7 @@ def test_options_default(L):
     assert (o.precision, o.econ, o.max_sweeps, o.sync, o.jacobi_tol) == (0, 0, 30, 1, 0.0)
     assert o.sweeps_out is None
     assert o.host_parts == 2
+    assert o.counts_out is None and o.jacobi_fp64 == 0
 
 
 def test_negative_dims_rejected_before_any_cuda_call(L):
@@ -126,3 +127,44 @@ def test_header_compiles_as_plain_c_and_cxx(lang, std, tmp_path):
     r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                         f"-I{os.path.dirname(HEADER)}", str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_noalloc_rejects_options_it_cannot_honour(L):
+    # validated before the scratch array or any CUDA call is touched, so this runs on a CPU
+    from paper_1806_07247_gb300 import tp
+    Y = ctypes.c_void_p(16)  # never dereferenced: every call below returns during validation
+
+    def call(o):
+        return L.tp_prox_tnn_noalloc(Y, Y, 4, 4, 4, 0.5, ctypes.byref(o), None)
+
+    cases = []
+    o = tp.options(method="learned")
+    cases.append(("method", o))
+    o = tp.options()
+    o.stage_events = 16
+    cases.append(("stage_events", o))
+    o = tp.options()
+    o.slice_flags_out = 16
+    cases.append(("slice_flags_out", o))
+    o = tp.options()
+    o.sketch_width_out = 16
+    cases.append(("sketch_width_out", o))
+    o = tp.options()
+    o.host_parts = 3  # rejected by every entry point's option check
+    cases.append(("host_parts", o))
+    o = tp.options()
+    o.jacobi_fp64 = 2
+    cases.append(("jacobi_fp64", o))
+    o = tp.options()
+    o.method = 7
+    cases.append(("method range", o))
+    for name, o in cases:
+        assert call(o) == tp.TP_ERR_INVALID_ARG, name
+
+
+def test_bad_new_options_rejected_by_every_entry_point(L):
+    from paper_1806_07247_gb300 import tp
+    o = tp.options()
+    o.jacobi_fp64 = 5
+    assert L.tp_prox_tnn(None, None, 2, 2, 2, 0.5, ctypes.byref(o), None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_tnn(None, None, 2, 2, 2, ctypes.byref(o), None) == tp.TP_ERR_INVALID_ARG
