@@ -154,16 +154,23 @@ __global__ void __launch_bounds__(kT) features_kernel(const SvdJob* __restrict__
 }
 
 // Proposer inference: one thread per slice, ell = clamp(ceil(k_hat) + 4).
-__global__ void mlp_infer_kernel(const float* __restrict__ feat, const SvdJob* __restrict__ jobs,
-                                 int n, int32_t* __restrict__ ell) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+// Proposer inference: one thread per slice, ell = clamp(ceil(k_hat) + 4).  The CTA stages the
+// parameters in shared memory (every thread reads the same weight at the same time, a
+// broadcast); the first hidden layer stays in registers.
+constexpr int kInferT = 64;
+__global__ void __launch_bounds__(kInferT) mlp_infer_kernel(const float* __restrict__ feat,
+                                                            const SvdJob* __restrict__ jobs, int n,
+                                                            int32_t* __restrict__ ell) {
+    __shared__ float w[kProposerFloats];
+    for (int t = threadIdx.x; t < kProposerFloats; t += kInferT) w[t] = g_proposer[t];
+    __syncthreads();
+    const int s = blockIdx.x * kInferT + threadIdx.x;
     if (s >= n) return;
-    const float* w = g_proposer;
     float x[kD];
 #pragma unroll
     for (int d = 0; d < kD; ++d) x[d] = (feat[(size_t)s * kD + d] - w[kMean + d]) / w[kStd + d];
     float h1[kH];
-#pragma unroll 4
+#pragma unroll
     for (int a = 0; a < kH; ++a) {
         float v = w[kB1 + a];
 #pragma unroll
@@ -173,7 +180,7 @@ __global__ void mlp_infer_kernel(const float* __restrict__ feat, const SvdJob* _
     float out = w[kB3];
     for (int a = 0; a < kH; ++a) {
         float v = w[kB2 + a];
-#pragma unroll 8
+#pragma unroll
         for (int b = 0; b < kH; ++b) v = fmaf(w[kW2 + a * kH + b], h1[b], v);
         out = fmaf(w[kW3 + a], fmaxf(v, 0.f), out);
     }
@@ -284,7 +291,7 @@ cudaError_t launch_features(const SvdJob* jobs, int njobs, int max_n1, int max_n
 cudaError_t launch_proposer(const float* feat, const SvdJob* jobs, int njobs, int32_t* ell,
                             cudaStream_t s) {
     if (njobs <= 0) return cudaSuccess;
-    mlp_infer_kernel<<<(njobs + 127) / 128, 128, 0, s>>>(feat, jobs, njobs, ell);
+    mlp_infer_kernel<<<(njobs + kInferT - 1) / kInferT, kInferT, 0, s>>>(feat, jobs, njobs, ell);
     return cudaGetLastError();
 }
 

@@ -47,8 +47,11 @@ using sk::warp_sum;
 constexpr int kLMax = kSketchMaxL;
 constexpr int kPT = 256;               // threads of the product and write kernels
 constexpr int kST = 128;               // threads of the per-slice small-matrix kernels
-constexpr int kXsBytes = 32 * 1024;    // staged rows of the right-hand matrix X
-constexpr int kAccItems = 128;         // split-K accumulation tile: items of 4 complex values
+constexpr int kXsBytes = 32 * 1024;    // A X: staged rows of the right-hand matrix X
+constexpr int kXsBytesAH = 8 * 1024;   // A^H X: staged rows of X ...
+constexpr int kAtBytes = 32 * 1024;    // ... and the transposed tile of A
+constexpr int kYsBytes = 12 * 1024;    // Gram: staged rows of the tall matrix
+constexpr int kAccCplx = 2048;         // split-K accumulation tile (complex values)
 constexpr uint32_t kOmegaSeed = 0x9e3779b9u, kDeflSeed = 0x9e3779b9u ^ 0x5bd1e995u;
 
 enum : int { FLAG_DONE = 0, FLAG_FAIL = 1, FLAG_RUN = 2, FLAG_LOW = 3, FLAG_LEFT = 4 };
@@ -85,16 +88,28 @@ __device__ __forceinline__ int list_len(const StageArgs& a) {
     return a.len_d ? *a.len_d : a.len_h;
 }
 
-// Split of a K loop over S thread groups for `items` outputs of 4 columns: the fewest rounds
-// of kPT threads times K / S, plus a small cost per split level.
-__device__ __forceinline__ int choose_split(int items, int K) {
+// Split of a K loop over S thread groups for `items` outputs of W columns: the fewest rounds
+// of kPT threads times K / S, plus a small cost per split level; parts meet in a shared tile of
+// kAccCplx complex values.
+__device__ __forceinline__ int choose_split(int items, int W, int K) {
     int best = 1;
     float bc = 3.4e38f;
     for (int S = 1; S <= 8; S *= 2) {
-        if (S > 1 && items > kAccItems) break;
+        if (S > 1 && items * W > kAccCplx) break;
         const int rounds = (items * S + kPT - 1) / kPT;
         const float cost = (float)rounds * ((float)K / (float)S + 6.f) + (S > 1 ? 10.f : 0.f);
         if (cost < bc) { bc = cost; best = S; }
+    }
+    return best;
+}
+
+// Columns per thread of a product with ncols columns: the W in {4, 8, 12, 16} with the least
+// work, W per column block plus a fixed cost per block (the reloads of A).
+__device__ __forceinline__ int choose_width(int ncols) {
+    int best = 4, bc = 1 << 30;
+    for (int W = 4; W <= 16; W += 4) {
+        const int c = ((ncols + W - 1) / W) * (W + 3);
+        if (c < bc) { bc = c; best = W; }
     }
     return best;
 }
@@ -146,120 +161,170 @@ __device__ void stage_x(float2* Xs, int ld, int k0, int kc, int ncols, int src, 
 //   AH = false: Y (n1 x ncols) = A X into Q, X from Omega (SRC_OMEGA), Z (SRC_Z) or [R x]
 //               (SRC_RX, giving T = A [R x]);
 //   AH = true:  Z (n2 x l) = A^H Q.
-// A thread owns one output row and 4 columns over a part of the K range (parts meet in a
-// shared-memory tile); X is staged in shared memory in chunks of rows, read as float4 pairs.
-// For A X consecutive threads read consecutive rows of a column of A (coalesced); for A^H X
-// a thread walks down one column of A, so its loads use whole 32-byte sectors.
+// A thread owns one output row and W columns (a register tile) over a part of the K range
+// (parts meet in a shared-memory tile); X is staged in shared memory in chunks of rows, read as
+// float4 pairs.  For A X consecutive threads read consecutive rows of a column of A (coalesced
+// loads).  For A^H X the rows k0..k0+kc of A are first staged transposed (coalesced down each
+// column of A, stored with an odd stride so that threads of consecutive columns read distinct
+// banks).
+template <bool AH, int W>
+__device__ void mult_slice(const SketchJob& J, int job, int l, int src, float2* Xs, float2* At,
+                           float2* acc_tile, int xs_cap, int at_cap) {
+    const int n1 = J.n1, n2 = J.n2;
+    const bool real = J.real_slice != 0;
+    const int ncols = (src == SRC_RX) ? l + 1 : l;
+    const int rows = AH ? n2 : n1, K = AH ? n1 : n2;
+    const int nch = (ncols + W - 1) / W, ld = W * nch;
+    int kcap = max(2, xs_cap / ld);
+    if (AH) kcap = min(kcap, max(2, at_cap / n2 - 1));
+    const int items = rows * nch;
+    const int S = choose_split(items, W, K);
+    const int total = items * S;
+    float2* out = AH ? J.Z : J.Q;  // A [R x] goes to Q too: Q is dead once U = Q V is formed
+    if (S > 1) {
+        for (int t = threadIdx.x; t < items * W; t += kPT) acc_tile[t] = make_float2(0.f, 0.f);
+    }
+    const int nchunks = (K + kcap - 1) / kcap;
+    for (int base = 0; base < total; base += kPT) {
+        const int t = base + threadIdx.x;
+        const bool act = t < total;
+        const int it = act ? t % items : 0, p = act ? t / items : 0;
+        const int r = it % rows, jc = it / rows;
+        float2 acc[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) acc[q] = make_float2(0.f, 0.f);
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int k0 = ch * kcap, kc = min(kcap, K - k0);
+            if (nchunks > 1 || base == 0) {
+                __syncthreads();
+                stage_x(Xs, ld, k0, kc, ncols, AH ? SRC_Q : src, J, job, l);
+                if (AH) {  // At[c * (kc | 1) + i] = A(k0 + i, c)
+                    const int kp = kc | 1;
+                    for (int u = threadIdx.x; u < kc * n2; u += kPT) {
+                        const int i = u % kc, c = u / kc;
+                        At[c * kp + i] = ld_a(J.A, (k0 + i) + (int64_t)n1 * c, real);
+                    }
+                }
+                __syncthreads();
+            }
+            if (!act) continue;
+            const float4* x4 = reinterpret_cast<const float4*>(Xs) + (W * jc) / 2;
+            const float2* col = AH ? At + r * (kc | 1) : nullptr;
+#pragma unroll 4
+            for (int k = p; k < kc; k += S) {
+                // parts interleave over k; A X: rows of a thread group are consecutive in A
+                const float2 av = AH ? col[k] : ld_a(J.A, r + (int64_t)n1 * (k0 + k), real);
+                const float4* xr = x4 + (k * ld) / 2;
+#pragma unroll
+                for (int q = 0; q < W / 2; ++q) {
+                    const float4 xv = xr[q];
+                    if (AH) {
+                        cmac_conj(acc[2 * q], av, make_float2(xv.x, xv.y));
+                        cmac_conj(acc[2 * q + 1], av, make_float2(xv.z, xv.w));
+                    } else {
+                        cmac(acc[2 * q], av, make_float2(xv.x, xv.y));
+                        cmac(acc[2 * q + 1], av, make_float2(xv.z, xv.w));
+                    }
+                }
+            }
+        }
+        if (!act) continue;
+        if (S == 1) {
+#pragma unroll
+            for (int q = 0; q < W; ++q)
+                if (W * jc + q < ncols) out[r + (size_t)rows * (W * jc + q)] = acc[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+                atomicAdd(&acc_tile[W * it + q].x, acc[q].x);
+                atomicAdd(&acc_tile[W * it + q].y, acc[q].y);
+            }
+        }
+    }
+    if (S > 1) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < items * W; t += kPT) {
+            const int it = t / W, q = t % W;
+            const int r = it % rows, c = W * (it / rows) + q;
+            if (c < ncols) out[r + (size_t)rows * c] = acc_tile[t];
+        }
+    }
+}
+
 template <bool AH>
-__global__ void __launch_bounds__(kPT) sk_mult_kernel(StageArgs a, int src) {
+__global__ void __launch_bounds__(kPT, 2) sk_mult_kernel(StageArgs a, int src) {
     extern __shared__ float4 smem4[];
     __shared__ int s_job;
+    constexpr int xs_cap = (AH ? kXsBytesAH : kXsBytes) / (int)sizeof(float2);
+    constexpr int at_cap = kAtBytes / (int)sizeof(float2);
     float2* Xs = reinterpret_cast<float2*>(smem4);
-    float2* acc_tile = Xs + kXsBytes / sizeof(float2);
+    float2* At = Xs + xs_cap;  // A^H X only
+    float2* acc_tile = At + (AH ? at_cap : 0);
     const int n = list_len(a);
     for (int item = blockIdx.x; item < n; item += gridDim.x) {
         const int job = stage_slice(a, item, &s_job);
         if (job < 0) continue;
         const SketchJob J = a.jobs[job];
-        const int n1 = J.n1, n2 = J.n2, l = a.ell[job];
-        const bool real = J.real_slice != 0;
-        const int ncols = (src == SRC_RX) ? l + 1 : l;
-        const int rows = AH ? n2 : n1, K = AH ? n1 : n2;
-        const int nch = (ncols + 3) >> 2, ld = 4 * nch;
-        const int kcap = max(2, (kXsBytes / (int)sizeof(float2)) / ld);
-        const int items = rows * nch;
-        const int S = choose_split(items, K);
-        const int total = items * S;
-        float2* out = AH ? J.Z : J.Q;  // A [R x] goes to Q too: Q is dead once U = Q V is formed
-        if (S > 1) {
-            for (int t = threadIdx.x; t < items * 4; t += kPT) acc_tile[t] = make_float2(0.f, 0.f);
-        }
-        const int nchunks = (K + kcap - 1) / kcap;
-        for (int base = 0; base < total; base += kPT) {
-            const int t = base + threadIdx.x;
-            const bool act = t < total;
-            const int it = act ? t % items : 0, p = act ? t / items : 0;
-            const int r = it % rows, jc = it / rows;
-            float2 acc[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
-            for (int ch = 0; ch < nchunks; ++ch) {
-                const int k0 = ch * kcap, kc = min(kcap, K - k0);
-                if (nchunks > 1 || base == 0) {
-                    __syncthreads();
-                    stage_x(Xs, ld, k0, kc, ncols, AH ? SRC_Q : src, J, job, l);
-                    __syncthreads();
-                }
-                if (!act) continue;
-                const float4* x4 = reinterpret_cast<const float4*>(Xs) + (4 * jc) / 2;
-                if (!AH) {
-                    // A X: rows of a thread group are consecutive; parts interleave over k
-#pragma unroll 4
-                    for (int k = p; k < kc; k += S) {
-                        const float2 av = ld_a(J.A, r + (int64_t)n1 * (k0 + k), real);
-                        const float4 xa = x4[(k * ld) / 2], xb = x4[(k * ld) / 2 + 1];
-                        cmac(acc[0], av, make_float2(xa.x, xa.y));
-                        cmac(acc[1], av, make_float2(xa.z, xa.w));
-                        cmac(acc[2], av, make_float2(xb.x, xb.y));
-                        cmac(acc[3], av, make_float2(xb.z, xb.w));
-                    }
-                } else {
-                    // A^H X: part p walks a contiguous block of rows of column r of A
-                    const int span = (kc + S - 1) / S;
-                    const int kb = p * span, ke = min(kc, kb + span);
-                    const float2* col = J.A + (int64_t)n1 * r + k0;
-#pragma unroll 4
-                    for (int k = kb; k < ke; ++k) {
-                        const float2 av = ld_a(col, k, real);
-                        const float4 xa = x4[(k * ld) / 2], xb = x4[(k * ld) / 2 + 1];
-                        cmac_conj(acc[0], av, make_float2(xa.x, xa.y));
-                        cmac_conj(acc[1], av, make_float2(xa.z, xa.w));
-                        cmac_conj(acc[2], av, make_float2(xb.x, xb.y));
-                        cmac_conj(acc[3], av, make_float2(xb.z, xb.w));
-                    }
-                }
-            }
-            if (!act) continue;
-            if (S == 1) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (4 * jc + q < ncols) out[r + (size_t)rows * (4 * jc + q)] = acc[q];
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    atomicAdd(&acc_tile[4 * it + q].x, acc[q].x);
-                    atomicAdd(&acc_tile[4 * it + q].y, acc[q].y);
-                }
-            }
-        }
-        if (S > 1) {
-            __syncthreads();
-            for (int t = threadIdx.x; t < items * 4; t += kPT) {
-                const int it = t >> 2, q = t & 3;
-                const int r = it % rows, c = 4 * (it / rows) + q;
-                if (c < ncols) out[r + (size_t)rows * c] = acc_tile[t];
-            }
+        const int l = a.ell[job];
+        switch (choose_width((src == SRC_RX) ? l + 1 : l)) {
+            case 4: mult_slice<AH, 4>(J, job, l, src, Xs, At, acc_tile, xs_cap, at_cap); break;
+            case 8: mult_slice<AH, 8>(J, job, l, src, Xs, At, acc_tile, xs_cap, at_cap); break;
+            case 12: mult_slice<AH, 12>(J, job, l, src, Xs, At, acc_tile, xs_cap, at_cap); break;
+            default: mult_slice<AH, 16>(J, job, l, src, Xs, At, acc_tile, xs_cap, at_cap); break;
         }
     }
 }
 
 // ----------------------------------------------------------------------------- small matrices
-// G (l x l, column-major, full Hermitian, shared) = Y^H Y for Y n x l (ld n, global).
-__device__ void gram_global(const float2* __restrict__ Y, int n, int l, float2* G) {
-    for (int t = threadIdx.x; t < l * l; t += blockDim.x) {
-        const int i = t % l, j = t / l;
-        if (i > j) continue;
-        const float2* ya = Y + (size_t)n * i;
-        const float2* yb = Y + (size_t)n * j;
-        float gr = 0.f, gi = 0.f;
-#pragma unroll 4
-        for (int e = 0; e < n; ++e) {
-            const float2 u = ya[e], v = yb[e];
-            gr = fmaf(u.x, v.x, fmaf(u.y, v.y, gr));  // conj(u) v
-            gi = fmaf(u.x, v.y, fmaf(-u.y, v.x, gi));
+// G (l x l, column-major, full Hermitian, shared) = Y^H Y for Y n x l (ld n, global).  Rows
+// of Y are staged in chunks (coalesced down each column, stored row-major with an odd stride)
+// and every thread accumulates the entries i <= j it owns (at most kPairs of them) over the
+// chunk: threads of a warp read one staged row at different columns.
+constexpr int kPairs = (kLMax * (kLMax + 1) / 2 + kST - 1) / kST;
+__device__ void gram_global(const float2* __restrict__ Y, int n, int l, float2* G, float2* Ys) {
+    const int np = l * (l + 1) / 2;
+    const int lp = l | 1;
+    const int kr = max(1, (kYsBytes / (int)sizeof(float2)) / lp);
+    int pi[kPairs], pj[kPairs];
+    float2 acc[kPairs];
+#pragma unroll
+    for (int u = 0; u < kPairs; ++u) {
+        const int p = threadIdx.x + u * kST;
+        int j = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+        while (j * (j + 1) / 2 > p) --j;
+        while ((j + 1) * (j + 2) / 2 <= p) ++j;
+        pj[u] = p < np ? j : 0;
+        pi[u] = p < np ? p - j * (j + 1) / 2 : 0;
+        acc[u] = make_float2(0.f, 0.f);
+    }
+    for (int e0 = 0; e0 < n; e0 += kr) {
+        const int rows = min(kr, n - e0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < rows * l; t += blockDim.x) {
+            const int r = t % rows, c = t / rows;
+            Ys[r * lp + c] = Y[(e0 + r) + (size_t)n * c];
         }
-        G[i + l * j] = make_float2(gr, gi);
-        G[j + l * i] = make_float2(gr, -gi);
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kPairs; ++u) {
+            if (threadIdx.x + u * kST >= np) break;
+            const float2* ya = Ys + pi[u];
+            const float2* yb = Ys + pj[u];
+            float gr = acc[u].x, gi = acc[u].y;
+#pragma unroll 4
+            for (int r = 0; r < rows; ++r) {
+                const float2 x = ya[r * lp], y = yb[r * lp];
+                gr = fmaf(x.x, y.x, fmaf(x.y, y.y, gr));  // conj(x) y
+                gi = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi));
+            }
+            acc[u] = make_float2(gr, gi);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kPairs; ++u) {
+        if (threadIdx.x + u * kST >= np) break;
+        G[pi[u] + l * pj[u]] = acc[u];
+        G[pj[u] + l * pi[u]] = make_float2(acc[u].x, -acc[u].y);
     }
     __syncthreads();
 }
@@ -376,6 +441,7 @@ __global__ void __launch_bounds__(kST) sk_orth_kernel(StageArgs a, int which) {
     __shared__ SmallShared sh;
     float2* G = reinterpret_cast<float2*>(smem4);
     float2* C = G + kLMax * kLMax;
+    float2* Ys = C + kLMax * kLMax;
     const int nlist = list_len(a);
     for (int item = blockIdx.x; item < nlist; item += gridDim.x) {
         const int job = stage_slice(a, item, &sh.job);
@@ -389,7 +455,7 @@ __global__ void __launch_bounds__(kST) sk_orth_kernel(StageArgs a, int which) {
         for (int pass = 0; pass < 2 && ok; ++pass) {
             float2* src = pass == 0 ? Y : S;
             float2* dst = pass == 0 ? S : Y;
-            gram_global(src, n, l, G);
+            gram_global(src, n, l, G, Ys);
             float shift = 0.f;
             if (pass == 0) {
                 float tr = 0.f;
@@ -527,6 +593,7 @@ __global__ void __launch_bounds__(kST) sk_small_svd_kernel(StageArgs a) {
     __shared__ SmallShared sh;
     float2* G = reinterpret_cast<float2*>(smem4);
     float2* V = G + kLMax * kLMax;
+    float2* Ys = V + kLMax * kLMax;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nlist = list_len(a);
     for (int item = blockIdx.x; item < nlist; item += gridDim.x) {
@@ -534,7 +601,7 @@ __global__ void __launch_bounds__(kST) sk_small_svd_kernel(StageArgs a) {
         if (job < 0) continue;
         const SketchJob J = a.jobs[job];
         const int l = a.ell[job], n1 = J.n1, n2 = J.n2;
-        gram_global(J.Z, n2, l, G);
+        gram_global(J.Z, n2, l, G, Ys);
         const bool ok = eigh_cta(G, V, l, sh.rot, sh.pq);
         if (!ok) {
             if (tid == 0) a.flag[job] = FLAG_FAIL;
@@ -582,7 +649,7 @@ __global__ void __launch_bounds__(kST) sk_small_svd_kernel(StageArgs a) {
 // Checks (b) and (c) from T = A [R x] (in Q; column l is A x for the random start x):
 // residuals ||A r_j - sigma_j u_j|| (sigma_j - tau) / sigma_j of the kept triplets against
 // rtol sigma_max, then two power iterations on E = A - U_k S_k R_k^H; flag 0 when both pass.
-__global__ void __launch_bounds__(kST) sk_check_kernel(StageArgs a) {
+__global__ void __launch_bounds__(kST, 6) sk_check_kernel(StageArgs a) {
     extern __shared__ float4 smem4[];
     __shared__ SmallShared sh;
     __shared__ float2 coef[kLMax];
@@ -693,7 +760,7 @@ __global__ void __launch_bounds__(kST) sk_check_kernel(StageArgs a) {
                 if (lane == 0) coef[j] = make_float2(w * dr, w * di);
             }
             __syncthreads();
-            // x = A^H y - R coef: a warp per column of A (coalesced), lanes over its rows
+            // x = A^H y (a warp per column of A, coalesced, lanes over its rows) ...
             for (int c = warp; c < n2; c += kST / 32) {
                 float dr = 0.f, di = 0.f;
                 for (int i = lane; i < n1; i += 32) {
@@ -703,15 +770,18 @@ __global__ void __launch_bounds__(kST) sk_check_kernel(StageArgs a) {
                 }
                 dr = warp_sum(dr);
                 di = warp_sum(di);
-                if (lane == 0) {
-                    float2 acc = make_float2(dr, di);
-                    for (int j = 0; j < l; ++j) {
-                        const float2 rr = R[c + (size_t)n2 * j], d = coef[j];
-                        acc.x -= fmaf(rr.x, d.x, -rr.y * d.y);
-                        acc.y -= fmaf(rr.x, d.y, rr.y * d.x);
-                    }
-                    xv[c] = acc;
+                if (lane == 0) xv[c] = make_float2(dr, di);
+            }
+            __syncthreads();
+            // ... - R coef (threads over the rows of R: coalesced, independent loads)
+            for (int c = tid; c < n2; c += kST) {
+                float2 acc = xv[c];
+                for (int j = 0; j < l; ++j) {
+                    const float2 rr = R[c + (size_t)n2 * j], d = coef[j];
+                    acc.x -= fmaf(rr.x, d.x, -rr.y * d.y);
+                    acc.y -= fmaf(rr.x, d.y, rr.y * d.x);
                 }
+                xv[c] = acc;
             }
             __syncthreads();
             float s = 0.f;
@@ -833,8 +903,9 @@ __global__ void __launch_bounds__(1024) sk_collect_kernel(const SketchJob* __res
     }
 }
 
-constexpr size_t kMultSmem = kXsBytes + (size_t)kAccItems * 4 * sizeof(float2);
-constexpr size_t kSmallSmem = 2 * (size_t)kLMax * kLMax * sizeof(float2);
+constexpr size_t kMultSmem = kXsBytes + (size_t)kAccCplx * sizeof(float2);
+constexpr size_t kMultSmemAH = kXsBytesAH + kAtBytes + (size_t)kAccCplx * sizeof(float2);
+constexpr size_t kSmallSmem = 2 * (size_t)kLMax * kLMax * sizeof(float2) + kYsBytes;
 // sk_check_kernel: the vectors x (n2) and y (n1), at most 2 * TP_MAX_SVD_DIM complex values
 constexpr size_t kCheckSmem = 2 * (size_t)TP_MAX_SVD_DIM * sizeof(float2);
 
@@ -856,7 +927,7 @@ cudaError_t occupancy(Occupancy* out) {
         struct K { const void* fn; size_t smem; int threads; int* dst; };
         const K ks[] = {
             {reinterpret_cast<const void*>(sk_mult_kernel<false>), kMultSmem, kPT, &o.mult_a},
-            {reinterpret_cast<const void*>(sk_mult_kernel<true>), kMultSmem, kPT, &o.mult_ah},
+            {reinterpret_cast<const void*>(sk_mult_kernel<true>), kMultSmemAH, kPT, &o.mult_ah},
             {reinterpret_cast<const void*>(sk_orth_kernel), kSmallSmem, kST, &o.orth},
             {reinterpret_cast<const void*>(sk_small_svd_kernel), kSmallSmem, kST, &o.svd},
             {reinterpret_cast<const void*>(sk_check_kernel), kCheckSmem, kST, &o.check},
@@ -909,7 +980,7 @@ cudaError_t run_sketch_svt(const SketchJob* jobs, int n, const int32_t* order, i
     auto grid = [&](int per_sm) { return std::max(1, std::min(n, sms * per_sm)); };
     auto mult = [&](bool ah, int src, int stage) {
         a.stage = stage;
-        if (ah) sk_mult_kernel<true><<<grid(occ.mult_ah), kPT, kMultSmem, s>>>(a, src);
+        if (ah) sk_mult_kernel<true><<<grid(occ.mult_ah), kPT, kMultSmemAH, s>>>(a, src);
         else sk_mult_kernel<false><<<grid(occ.mult_a), kPT, kMultSmem, s>>>(a, src);
     };
     auto orth = [&](int which, int stage) {
