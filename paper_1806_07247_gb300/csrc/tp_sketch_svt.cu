@@ -933,10 +933,9 @@ cudaError_t occupancy(Occupancy* out) {
             {reinterpret_cast<const void*>(sk_check_kernel), kCheckSmem, kST, &o.check},
             {reinterpret_cast<const void*>(sk_write_kernel), 0, kPT, &o.write}};
         for (const K& k : ks) {
-            if (k.smem > 48 * 1024) {
-                e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
-                if (e != cudaSuccess) return e;
-            }
+            // opt in for every kernel: dynamic plus static shared memory may pass 48 KB
+            e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+            if (e != cudaSuccess) return e;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(k.dst, k.fn, k.threads, k.smem);
             if (e != cudaSuccess) return e;
             if (*k.dst < 1) return cudaErrorInvalidConfiguration;
