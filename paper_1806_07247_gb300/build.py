@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
 SOURCES = ["tp_fft.cu", "tp_gemm.cu", "tp_gemm_tc.cu", "tp_svd.cu", "tp_sketch.cu", "tp_tran.cu", "tp_capi.cu",
-           "tp_noalloc.cu", "tp_slice_la.cu", "tp_sketch_svt.cu"]
+           "tp_noalloc.cu", "tp_slice_la.cu"]
 
 
 def nvcc() -> str:

@@ -397,7 +397,6 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     const JacobiShape shape = jacobi_shape_current();
     int64_t nfft = 0;
     int max_n1 = 1, max_n2 = 1;
-    size_t sketch_floats = 0;
     for (int64_t t = 0; t < count; ++t) {
         const int64_t n1 = d[t].n1, n2 = d[t].n2, n3 = d[t].n3;
         if (n1 == 0 || n2 == 0 || n3 == 0) continue;
@@ -406,11 +405,11 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         work[t] = cfg[t].work_elems;
         bytes += cbytes(n1 * n2 * h);
         if (work[t] > 0) bytes += cbytes(work[t] * h);
-        if (learned) sketch_floats += sketch_job_floats((int)n1, (int)n2) * (size_t)h;
         slices += h;
         ++nfft;
         max_n1 = std::max<int>(max_n1, (int)n1);
         max_n2 = std::max<int>(max_n2, (int)n2);
+
     }
     if (nfft == 0) return TP_OK;
     bytes += 2 * Workspace::round(sizeof(FftJob) * (nfft + 1));
@@ -419,12 +418,10 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         bytes += Workspace::round(sizeof(SvdJob) * (slices + 1));        // natural-order jobs
         bytes += Workspace::round(sizeof(float) * kProposerInputs * slices);
         bytes += 4 * Workspace::round(sizeof(int32_t) * slices);  // ell, flags, counts, order
+        bytes += Workspace::round(sizeof(int32_t) * kSketchClasses * slices);  // sketch queues
+        bytes += Workspace::round(sizeof(int32_t) * 2 * kSketchClasses);       // queue counters
         bytes += 3 * Workspace::round(sizeof(int32_t) * slices);  // extra power its, 2 retry lists
-        bytes += Workspace::round(sizeof(int32_t) * kSketchRetryRounds);  // retry list lengths
-    }
-    if (learned) {
-        bytes += Workspace::round(sizeof(SketchJob) * (slices + 1));
-        bytes += Workspace::round(sizeof(float) * sketch_floats);
+        bytes += Workspace::round(sizeof(int32_t) * 2 * kSketchRetryRounds);  // retry counters
     }
     if (train) bytes += Workspace::round(sizeof(float) * proposer_fit_scratch_floats((int)slices));
     Workspace ws(s);
@@ -437,10 +434,9 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         TP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
     float* feat = nullptr;
     int32_t *ell = nullptr, *flags = nullptr, *counts = nullptr, *d_order = nullptr;
+    int32_t *d_queues = nullptr, *d_qcount = nullptr;
     int32_t *d_extra = nullptr, *d_retry = nullptr, *d_rcount = nullptr;
     SvdJob* d_nat = nullptr;
-    SketchJob* d_sk = nullptr;
-    float* sk_arena = nullptr;
     if (need_feat) {
         d_nat = ws.take<SvdJob>(slices);
         feat = ws.take<float>((size_t)kProposerInputs * slices);
@@ -448,18 +444,13 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         flags = ws.take<int32_t>(slices);
         counts = ws.take<int32_t>(slices);
         d_order = ws.take<int32_t>(slices);
+        d_queues = ws.take<int32_t>((size_t)kSketchClasses * slices);
+        d_qcount = ws.take<int32_t>(2 * kSketchClasses);
         d_extra = ws.take<int32_t>(slices);
         d_retry = ws.take<int32_t>(2 * (size_t)slices);
-        d_rcount = ws.take<int32_t>(kSketchRetryRounds);
+        d_rcount = ws.take<int32_t>(2 * kSketchRetryRounds);
         TP_TRY(ws.check());
     }
-    if (learned) {
-        d_sk = ws.take<SketchJob>(slices);
-        sk_arena = ws.take<float>(sketch_floats);
-        TP_TRY(ws.check());
-    }
-    std::vector<SketchJob> skjobs;
-    size_t sk_off = 0;
     FftBatch fwd, inv;
     SvdBatch svd;
     std::vector<SvdJob> natural;
@@ -490,28 +481,6 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             j.skip = learned ? flags + sidx : nullptr;
             j.count_out = train ? counts + sidx : (o.counts_out ? o.counts_out + sidx : nullptr);
             if (need_feat) natural.push_back(j);
-            if (learned) {
-                SketchJob q;
-                q.A = j.A;
-                q.W = j.W;
-                q.n1 = j.n1;
-                q.n2 = j.n2;
-                q.real_slice = j.real_slice;
-                q.tau = j.tau;
-                q.lcap = sketch_lcap(j.n1, j.n2);
-                const size_t fl = sketch_job_floats(j.n1, j.n2);
-                if (fl > 0) {
-                    const int lc = q.lcap, m = std::max(j.n1, j.n2);
-                    float2* base = reinterpret_cast<float2*>(sk_arena + sk_off);
-                    q.Q = base;
-                    q.Z = q.Q + (size_t)j.n1 * (lc + 1);
-                    q.S = q.Z + (size_t)j.n2 * lc;
-                    q.sig = reinterpret_cast<float*>(q.S + (size_t)m * (lc + 1));
-                    q.keep = reinterpret_cast<int32_t*>(q.sig + lc);
-                    sk_off += fl;
-                }
-                skjobs.push_back(q);
-            }
             it.cfg = cfg[t];
             const int64_t m = std::max(n1, n2), n = std::min(n1, n2);
             it.cost = m * n * n;
@@ -531,20 +500,71 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     if (learned) {
         TP_CUDA(launch_proposer(feat, d_nat, (int)slices, ell, s));
         TP_TRY(o.mark(2, s));
-        // The randomized SVT stages over the slices, largest first (see tp_sketch_svt.cu); the
-        // slices it does not finish keep their flag non-zero for the Jacobi launches below.
+        // Sketch queues: the slices, largest first, binned on the device by the shared memory
+        // their proposed width needs (4, 3, 2 and 1 CTAs of the sketch kernel per SM); one
+        // persistent launch per class works through its queue.  Slices too large for every
+        // class (or without a usable width) are flagged for the Jacobi path by the binning.
         std::vector<int32_t> sorted(slices);
         for (int64_t j = 0; j < slices; ++j) sorted[j] = (int32_t)j;
         std::stable_sort(sorted.begin(), sorted.end(), [&](int32_t a, int32_t b) {
             return (int64_t)natural[a].n1 * natural[a].n2 > (int64_t)natural[b].n1 * natural[b].n2;
         });
         TP_TRY(upload(d_order, sorted, s));
-        TP_TRY(upload(d_sk, skjobs, s));
+        SketchCaps caps;
+        caps.n = 4;
+        caps.bytes[0] = 55 * 1024;
+        caps.bytes[1] = 74 * 1024;
+        caps.bytes[2] = 112 * 1024;
+        caps.bytes[3] = 220 * 1024;
+        TP_CUDA(launch_sketch_bin(d_nat, d_order, (int)slices, ell, flags, caps, d_queues, d_qcount,
+                                  s));
         int sms = 0;
         TP_TRY(sm_count(&sms));
-        TP_CUDA(run_sketch_svt(d_sk, (int)slices, d_order, ell, flags,
-                               o.counts_out ? o.counts_out : counts, d_extra, d_retry, d_rcount,
-                               sms, s));
+        // retries: two rounds over lists of the slices that failed a check but are worth
+        // another attempt (more power iterations or a wider sketch), in the largest class
+        constexpr int kRetryRounds = kSketchRetryRounds;
+        constexpr int kRetryMinDim = 96;
+        const size_t retry_smem = caps.bytes[caps.n - 1];
+        TP_CUDA(cudaMemsetAsync(d_extra, 0, sizeof(int32_t) * slices, s));
+        TP_CUDA(cudaMemsetAsync(d_rcount, 0, sizeof(int32_t) * 2 * kRetryRounds, s));
+        auto base = [&]() {
+            SketchParams sp;
+            sp.ell = ell;
+            sp.flag = flags;
+            sp.count = o.counts_out ? o.counts_out : counts;
+            sp.njobs = (int)slices;
+            sp.seed = 0x9e3779b9u;
+            sp.power_iters = 1;
+            sp.extra_power = d_extra;
+            sp.resid_tol = 1e-5f;
+            return sp;
+        };
+        for (int c = 0; c < caps.n; ++c) {
+            const int per_sm = sketch_blocks_per_sm(caps.bytes[c]);
+            if (per_sm <= 0) return TP_ERR_CUDA;
+            SketchParams sp = base();
+            sp.order = d_queues + (size_t)c * slices;
+            sp.queue_len = d_qcount + 2 * c;
+            sp.queue_next = d_qcount + 2 * c + 1;
+            sp.smem_bytes = (int)caps.bytes[c];
+            const int64_t grid = std::min<int64_t>(slices, (int64_t)sms * per_sm);
+            TP_CUDA(launch_sketch_svt(d_nat, (int)grid, caps.bytes[c], sp, s));
+        }
+        const int retry_per_sm = sketch_blocks_per_sm(retry_smem);
+        if (retry_per_sm <= 0) return TP_ERR_CUDA;
+        for (int round = 0; round < kRetryRounds; ++round) {
+            int32_t* list = d_retry + (size_t)(round & 1) * slices;
+            TP_CUDA(launch_sketch_collect(d_nat, (int)slices, flags, ell, d_extra, kRetryMinDim,
+                                          (int)retry_smem, list, d_rcount + 2 * round, s));
+            SketchParams sp = base();
+            sp.retry_launch = 1;
+            sp.order = list;
+            sp.queue_len = d_rcount + 2 * round;       // round r: length, then work counter
+            sp.queue_next = d_rcount + 2 * round + 1;
+            sp.smem_bytes = (int)retry_smem;
+            const int64_t grid = std::min<int64_t>(slices, (int64_t)sms * retry_per_sm);
+            TP_CUDA(launch_sketch_svt(d_nat, (int)grid, retry_smem, sp, s));
+        }
         TP_TRY(o.mark(3, s));
         if (o.slice_flags_out)
             TP_CUDA(launch_flags01(flags, o.slice_flags_out, (int)slices, s));

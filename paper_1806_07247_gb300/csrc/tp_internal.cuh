@@ -140,49 +140,59 @@ cudaError_t launch_diag_scatter(const float* tubes, int r, int n3, float* S, int
 // ---------------------------------------------------------------------------
 // Learned-rank randomized SVT (tp_sketch.cu)
 // ---------------------------------------------------------------------------
-constexpr int kSketchMaxL = 48;        // widest sketch
+constexpr int kSketchMaxL = 32;        // widest sketch
 constexpr int kProposerInputs = 12;    // features per slice
 constexpr int kProposerFloats = TP_PROPOSER_FLOATS;
-// Retry rounds of the sketch path (each: collect the failed slices, sketch them again), and
-// the smallest min(n1, n2) worth a retry (below it the Jacobi SVD is cheap).
-constexpr int kSketchRetryRounds = 2;
-constexpr int kSketchRetryMinDim = 96;
 
-// Widest sketch a slice's buffers hold: l < min(n1, n2) is required.
-inline __host__ __device__ int sketch_lcap(int n1, int n2) {
-    const int r = (n1 < n2 ? n1 : n2) - 1;
-    return r < 0 ? 0 : (r < kSketchMaxL ? r : kSketchMaxL);
-}
-
-// One slice of the batched randomized SVT (tp_sketch_svt.cu) and its working buffers.
-struct SketchJob {
-    const float2* A = nullptr;  // Fourier slice, n1 x n2, ld n1
-    float2* W = nullptr;        // output slice (the same memory as A)
-    float2* Q = nullptr;        // n1 x (lcap + 1): range basis, later T = A [R x]
-    float2* Z = nullptr;        // n2 x lcap: A^H Q, later R
-    float2* S = nullptr;        // max(n1, n2) x (lcap + 1): orthonormalisation scratch, D, U
-    float* sig = nullptr;       // lcap computed singular values
-    int32_t* keep = nullptr;    // lcap flags: sigma_j > tau (decided in FP64)
-    int32_t n1 = 0, n2 = 0, real_slice = 0, lcap = 0;
-    double tau = 0.0;
+struct SketchParams {
+    const int32_t* order = nullptr;  // CTA (or queue position) -> job index (nullptr: identity)
+    const int32_t* queue_len = nullptr;  // persistent mode: number of entries of `order`
+    int32_t* queue_next = nullptr;       // persistent mode: work counter (zero at launch)
+    int32_t* ell;         // per job: sketch width (0: go to the full Jacobi SVD); a wider
+                          // retry raises it
+    int32_t* flag;        // per job: 0 = W written by the sketch path, 1 = needs Jacobi
+    int32_t* count;       // per job: #{sigma > tau} on success (optional)
+    uint32_t seed;
+    int power_iters;
+    int njobs = 0;                   // jobs in the launch's job array (bounds queue entries)
+    int32_t* extra_power = nullptr;  // per job: extra power iterations of a retry
+    int retry_launch = 0;            // 1: `order` is a retry list (per-slice power iterations)
+    float resid_tol;
+    int smem_bytes;       // dynamic shared memory of the launch
 };
-// 4-byte words of one slice's buffers (a multiple of 64), 0 if the slice cannot be sketched.
-size_t sketch_job_floats(int n1, int n2);
-// The whole randomized SVT of the slices `order` (largest first) with widths `ell`: rounds of
-// stage kernels, retries between rounds.  flag (per slice) ends 0 where W was written;
-// retry_lists holds 2 n ints, retry_len kSketchRetryRounds ints.
-cudaError_t run_sketch_svt(const SketchJob* jobs, int n, const int32_t* order, int32_t* ell,
-                           int32_t* flag, int32_t* count, int32_t* extra, int32_t* retry_lists,
-                           int32_t* retry_len, int sms, cudaStream_t s);
-// Kernel launches run_sketch_svt makes per call.
-int sketch_stage_launches(int power_iters);
+
+__host__ __device__ inline size_t sketch_smem_need(int n1, int n2, int l) {
+    const size_t nm = n1 > n2 ? n1 : n2;
+    return sizeof(float2) * (3 * nm * l + (size_t)3 * l * l + (size_t)n1 + n2 + 2 * kSketchMaxL) +
+           sizeof(float) * (2 * kSketchMaxL) + 64;
+}
+// Retry rounds of the sketch path (each: collect the failed slices, sketch them again).
+constexpr int kSketchRetryRounds = 4;
+// Size classes of the sketch kernel's queues: shared memory bytes per CTA, increasing.
+constexpr int kSketchClasses = 4;
+struct SketchCaps {
+    int n;
+    uint32_t bytes[kSketchClasses];
+};
+// Bins the slices (in the order of `sorted`) into one queue per class; see tp_sketch.cu.
+cudaError_t launch_sketch_bin(const SvdJob* jobs, const int32_t* sorted, int n, const int32_t* ell,
+                              int32_t* flag, const SketchCaps& caps, int32_t* queues,
+                              int32_t* counts, cudaStream_t s);
+// Queues the failed slices worth another sketch (see tp_sketch.cu) into `list`.
+cudaError_t launch_sketch_collect(const SvdJob* jobs, int n, int32_t* flag, int32_t* ell,
+                                  int32_t* extra, int min_dim, int smem, int32_t* list,
+                                  int32_t* len, cudaStream_t s);
 // out[j] = (flags[j] != 0): the per-slice fallback flags as 0 / 1.
 cudaError_t launch_flags01(const int32_t* flags, int32_t* out, int n, cudaStream_t s);
+// Resident CTAs of the sketch kernel per SM at this dynamic shared memory (0 on error).
+int sketch_blocks_per_sm(size_t smem);
 size_t features_smem_bytes(int n1, int n2);
 cudaError_t launch_features(const SvdJob* jobs, int njobs, int max_n1, int max_n2, float* feat,
                             uint32_t seed, cudaStream_t s);
 cudaError_t launch_proposer(const float* feat, const SvdJob* jobs, int njobs, int32_t* ell,
                             cudaStream_t s);
+cudaError_t launch_sketch_svt(const SvdJob* jobs, int ncta, size_t smem, const SketchParams& p,
+                              cudaStream_t s);
 bool proposer_ready();
 cudaError_t proposer_set(const float* host);
 cudaError_t proposer_get(float* host);
