@@ -88,19 +88,34 @@ __device__ __forceinline__ float2 ld_a(const float2* A, int64_t idx, bool real) 
 }
 
 // Y (n1 x l, ld n1) = A X (X: n2 x l, ld n2, shared).  A work item is one row of Y and a
-// chunk of 4 of its columns; all threads of the CTA share the items.
+// chunk of 4 of its columns; when the items fill the CTA unevenly, the column loop is also
+// split over S parts whose partial sums meet in Y through shared-memory atomics (S chosen for
+// the fewest rounds of the CTA's threads times n2 / S).
 __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, const float2* X,
                        float2* Y, int l) {
-    const int nch = (l + 3) >> 2;
-    for (int t = threadIdx.x; t < n1 * nch; t += (int)blockDim.x) {
-        const int i = t % n1, j0 = (t / n1) * 4;
+    const int nch = (l + 3) >> 2, T = (int)blockDim.x;
+    const int items = n1 * nch;
+    int S = 1;
+    float best = 3.4e38f;
+    for (int s2 = 1; s2 <= 8; s2 *= 2) {
+        const int rounds = (items * s2 + T - 1) / T;
+        const float cost = (float)rounds * ((float)n2 / (float)s2 + 4.f) + (s2 > 1 ? 6.f : 0.f);
+        if (cost < best) { best = cost; S = s2; }
+    }
+    if (S > 1) {
+        for (int t = threadIdx.x; t < n1 * l; t += T) Y[t] = make_float2(0.f, 0.f);
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < items * S; t += T) {
+        const int it = t % items, p = t / items;
+        const int i = it % n1, j0 = (it / n1) * 4;
         const int jn = min(4, l - j0);
         float2 acc[4];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) acc[jj] = make_float2(0.f, 0.f);
         const float2* x = X + (size_t)n2 * j0;
 #pragma unroll 4
-        for (int c = 0; c < n2; ++c) {
+        for (int c = p; c < n2; c += S) {
             const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
@@ -112,8 +127,16 @@ __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, 
             }
         }
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-            if (jj < jn) Y[i + (size_t)n1 * (j0 + jj)] = acc[jj];
+        for (int jj = 0; jj < 4; ++jj) {
+            if (jj >= jn) continue;
+            float2* y = Y + i + (size_t)n1 * (j0 + jj);
+            if (S == 1) {
+                *y = acc[jj];
+            } else {
+                atomicAdd(&y->x, acc[jj].x);
+                atomicAdd(&y->y, acc[jj].y);
+            }
+        }
     }
 }
 
@@ -188,71 +211,75 @@ __device__ void gram(const float2* Y, int n, int l, float2* G) {
 
 // C (l x l, upper triangular) with C^H (G + shift I) C = I, i.e. C = R^-1 for the Cholesky
 // factor R^H R = G + shift I: Gram-Schmidt of the unit vectors e_0..e_{l-1} in the
-// (G + shift I) inner product.  G is overwritten by M = (G + shift I) C, kept current column
-// by column, so every step needs only dot products of length l.  Run by ONE warp (the caller
-// synchronises the CTA around it): lane k owns columns k and k + 32 of C and M; at step j the
-// owner of column j normalises c_j and m_j, then every later column k forms h = m_j^H c_k and
-// updates c_k -= h c_j, m_k -= h m_j, with only warp-level synchronisation between steps.
-// Returns false (in every lane) if a norm is not positive (breakdown).
-__device__ bool chol_inv_warp(float2* G, float2* C, int l, float shift) {
-    const int lane = threadIdx.x & 31;
-    for (int k = lane; k < l; k += 32)
-        for (int m = 0; m < l; ++m) {
-            C[m + l * k] = make_float2(m == k ? 1.f : 0.f, 0.f);
-            if (m == k) G[m + l * k].x += shift;
-        }
-    __syncwarp();
-    for (int j = 0; j < l; ++j) {
-        const int owner = j & 31;
-        float p = 0.f;
-        if (lane == owner) {
-            for (int m = 0; m <= j; ++m) {
-                const float2 cj = C[m + l * j], mj = G[m + l * j];
-                p = fmaf(cj.x, mj.x, fmaf(cj.y, mj.y, p));  // c_j^H m_j (real)
-            }
-            const float inv = p > 0.f ? rsqrt_nr(p) : 0.f;
-            for (int m = 0; m <= j; ++m) { C[m + l * j].x *= inv; C[m + l * j].y *= inv; }
-            for (int m = 0; m < l; ++m) { G[m + l * j].x *= inv; G[m + l * j].y *= inv; }
-        }
-        p = __shfl_sync(0xffffffffu, p, owner);
-        if (!(p > 0.f)) return false;
-        __syncwarp();
-        for (int k = lane; k < l; k += 32) {
-            if (k <= j) continue;
-            float hr = 0.f, hi = 0.f;
-            for (int m = 0; m <= k; ++m) {
-                const float2 mm = G[m + l * j], c = C[m + l * k];
-                hr = fmaf(mm.x, c.x, fmaf(mm.y, c.y, hr));  // conj(m_j) c_k
-                hi = fmaf(mm.x, c.y, fmaf(-mm.y, c.x, hi));
-            }
-            for (int m = 0; m <= j; ++m) {
-                const float2 cj = C[m + l * j];
-                float2 c = C[m + l * k];
-                c.x -= fmaf(hr, cj.x, -hi * cj.y);
-                c.y -= fmaf(hr, cj.y, hi * cj.x);
-                C[m + l * k] = c;
-            }
-            for (int m = 0; m < l; ++m) {
-                const float2 mj = G[m + l * j];
-                float2 mk = G[m + l * k];
-                mk.x -= fmaf(hr, mj.x, -hi * mj.y);
-                mk.y -= fmaf(hr, mj.y, hi * mj.x);
-                G[m + l * k] = mk;
-            }
-        }
-        __syncwarp();
-    }
-    return true;
-}
-
-// chol_inv_warp run by warp 0 for the whole CTA (uniform result through *s_flag).
+// (G + shift I) inner product, each normalised vector projected out of all later ones at
+// once.  G is overwritten by M = (G + shift I) C, kept current column by column, so that
+// every step needs only dot products of length l: warp 0 normalises c_j (and m_j), then one
+// half-warp per later column k forms h = m_j^H c_k and updates c_k -= h c_j, m_k -= h m_j.
+// Returns false (uniformly) if a norm is not positive (breakdown).
 __device__ bool chol_inv(float2* G, float2* C, int l, float shift, int* s_flag) {
-    if ((threadIdx.x >> 5) == 0) {
-        const bool ok = chol_inv_warp(G, C, l, shift);
-        if ((threadIdx.x & 31) == 0) *s_flag = ok ? 0 : 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int t = tid; t < l * l; t += kTS) {
+        const bool d = (t % l) == (t / l);
+        C[t] = make_float2(d ? 1.f : 0.f, 0.f);
+        if (d) G[t].x += shift;
     }
     __syncthreads();
-    return *s_flag == 0;
+    const int hw = tid >> 4, hl = tid & 15;  // 16 half-warps; rows hl and hl + 16
+    for (int j = 0; j < l; ++j) {
+        if (warp == 0) {
+            const float2 cj = lane <= j ? C[lane + l * j] : make_float2(0.f, 0.f);
+            const float2 mj = lane < l ? G[lane + l * j] : make_float2(0.f, 0.f);
+            const float p = warp_sum(fmaf(cj.x, mj.x, cj.y * mj.y));  // c_j^H m_j (real)
+            const bool ok = p > 0.f;
+            const float inv = ok ? 1.f / sqrtf(p) : 0.f;
+            if (lane <= j) C[lane + l * j] = make_float2(cj.x * inv, cj.y * inv);
+            if (lane < l) G[lane + l * j] = make_float2(mj.x * inv, mj.y * inv);
+            if (lane == 0) *s_flag = ok ? 0 : 1;
+        }
+        __syncthreads();
+        if (*s_flag) return false;
+        for (int kb = j + 1; kb < l; kb += kTS / 16) {  // uniform over each warp
+            const int k = kb + hw;
+            const bool act = k < l;
+            float hr = 0.f, hi = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = hl + 16 * h;
+                if (act && m <= k) {
+                    const float2 mm = G[m + l * j], c = C[m + l * k];
+                    hr = fmaf(mm.x, c.x, fmaf(mm.y, c.y, hr));  // conj(m_j) c_k
+                    hi = fmaf(mm.x, c.y, fmaf(-mm.y, c.x, hi));
+                }
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                hr += __shfl_xor_sync(0xffffffffu, hr, o);
+                hi += __shfl_xor_sync(0xffffffffu, hi, o);
+            }
+            if (act) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int m = hl + 16 * h;
+                    if (m <= j) {
+                        const float2 cj = C[m + l * j];
+                        float2 c = C[m + l * k];
+                        c.x -= fmaf(hr, cj.x, -hi * cj.y);
+                        c.y -= fmaf(hr, cj.y, hi * cj.x);
+                        C[m + l * k] = c;
+                    }
+                    if (m < l) {
+                        const float2 mj = G[m + l * j];
+                        float2 mk = G[m + l * k];
+                        mk.x -= fmaf(hr, mj.x, -hi * mj.y);
+                        mk.y -= fmaf(hr, mj.y, hi * mj.x);
+                        G[m + l * k] = mk;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    return true;
 }
 
 // Yout (n x l) = Yin C for an upper triangular C (l x l); items of one row and 4 columns.
@@ -309,18 +336,17 @@ __device__ float2* orth3(float2* Y, float2* S, int n, int l, float2* G, float2* 
     return cur;
 }
 
-// Eigen-decomposition G = V diag(lambda) V^H of the l x l (l <= kLMax) Hermitian G by ONE warp
-// (the caller synchronises the CTA around it): parallel two-sided Jacobi over the round-robin
-// tournament, with only warp-level synchronisation between rounds.  Each round first forms the
+// Eigen-decomposition G = V diag(lambda) V^H of the l x l (l <= 32) Hermitian G by the whole
+// CTA: parallel two-sided Jacobi over the round-robin tournament.  Each round first forms the
 // rotations of its P pairs (one thread per pair), then applies all of them at once: every
 // 2 x 2 block of G (rows of pair i, columns of pair j) becomes J_i^H G_ij J_j and V <- V J.
 // Rows and columns of different pairs are disjoint, so the blocks are independent.  G ends
 // diagonal up to the tolerance.  `rot` (4 kLMax floats) and `pq` (kLMax ints) are scratch.
 // Returns false without convergence in 30 sweeps.
-__device__ bool eigh_warp(float2* G, float2* V, int l, float4* rot, int2* pq) {
-    const int tid = threadIdx.x & 31;
-    for (int t = tid; t < l * l; t += 32) V[t] = make_float2((t % l) == (t / l) ? 1.f : 0.f, 0.f);
-    __syncwarp();
+__device__ bool eigh_cta(float2* G, float2* V, int l, float4* rot, int2* pq) {
+    const int tid = threadIdx.x;
+    for (int t = tid; t < l * l; t += kTS) V[t] = make_float2((t % l) == (t / l) ? 1.f : 0.f, 0.f);
+    __syncthreads();
     if (l < 2) return true;
     const int Np = l + (l & 1), P = Np / 2;
     const float tol = 8.f * 1.1920928955078125e-07f, tol2 = tol * tol;
@@ -346,8 +372,8 @@ __device__ bool eigh_warp(float2* G, float2* V, int l, float4* rot, int2* pq) {
                 rot[tid] = make_float4(c, sr, si, f);
                 pq[tid] = make_int2(p, q < l ? q : -1);
             }
-            __syncwarp();
-            for (int t = tid; t < P * P + l * P; t += 32) {
+            __syncthreads();
+            for (int t = tid; t < P * P + l * P; t += kTS) {
                 if (t < P * P) {
                     const int i = t % P, j = t / P;
                     const float4 ri = rot[i], rj = rot[j];
@@ -396,21 +422,11 @@ __device__ bool eigh_warp(float2* G, float2* V, int l, float4* rot, int2* pq) {
                                                  fmaf(tr, x.y, fmaf(ti, x.x, d * y.y)));
                 }
             }
-            __syncwarp();
+            __syncthreads();
         }
-        if (!__any_sync(0xffffffffu, rotated)) return true;
+        if (!__syncthreads_or(rotated)) return true;
     }
     return false;
-}
-
-// eigh_warp run by warp 0 for the whole CTA (uniform result through *s_flag).
-__device__ bool eigh_cta(float2* G, float2* V, int l, float4* rot, int2* pq, int* s_flag) {
-    if ((threadIdx.x >> 5) == 0) {
-        const bool ok = eigh_warp(G, V, l, rot, pq);
-        if ((threadIdx.x & 31) == 0) *s_flag = ok ? 0 : 1;
-    }
-    __syncthreads();
-    return *s_flag == 0;
 }
 
 // y (n1) = A x (x: n2, shared); partial sums over column ranges meet through shared atomics.
@@ -545,7 +561,7 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     if (ok) {
         mult_ah(A, n1, n2, real, bq, bz, l);
         gram(bz, n2, l, G);
-        ok = eigh_cta(G, V, l, s_rot, s_pq, &s_flag);
+        ok = eigh_cta(G, V, l, s_rot, s_pq);
     }
     if (ok) {  // D = Z V over Z, by rows (a warp per row, lanes over columns)
         for (int e = warp; e < n2; e += kTS / 32) {
