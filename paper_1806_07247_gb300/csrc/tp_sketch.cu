@@ -88,34 +88,19 @@ __device__ __forceinline__ float2 ld_a(const float2* A, int64_t idx, bool real) 
 }
 
 // Y (n1 x l, ld n1) = A X (X: n2 x l, ld n2, shared).  A work item is one row of Y and a
-// chunk of 4 of its columns; when the items fill the CTA unevenly, the column loop is also
-// split over S parts whose partial sums meet in Y through shared-memory atomics (S chosen for
-// the fewest rounds of the CTA's threads times n2 / S).
+// chunk of 4 of its columns; all threads of the CTA share the items.
 __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, const float2* X,
                        float2* Y, int l) {
-    const int nch = (l + 3) >> 2, T = (int)blockDim.x;
-    const int items = n1 * nch;
-    int S = 1;
-    float best = 3.4e38f;
-    for (int s2 = 1; s2 <= 8; s2 *= 2) {
-        const int rounds = (items * s2 + T - 1) / T;
-        const float cost = (float)rounds * ((float)n2 / (float)s2 + 4.f) + (s2 > 1 ? 6.f : 0.f);
-        if (cost < best) { best = cost; S = s2; }
-    }
-    if (S > 1) {
-        for (int t = threadIdx.x; t < n1 * l; t += T) Y[t] = make_float2(0.f, 0.f);
-        __syncthreads();
-    }
-    for (int t = threadIdx.x; t < items * S; t += T) {
-        const int it = t % items, p = t / items;
-        const int i = it % n1, j0 = (it / n1) * 4;
+    const int nch = (l + 3) >> 2;
+    for (int t = threadIdx.x; t < n1 * nch; t += (int)blockDim.x) {
+        const int i = t % n1, j0 = (t / n1) * 4;
         const int jn = min(4, l - j0);
         float2 acc[4];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) acc[jj] = make_float2(0.f, 0.f);
         const float2* x = X + (size_t)n2 * j0;
 #pragma unroll 4
-        for (int c = p; c < n2; c += S) {
+        for (int c = 0; c < n2; ++c) {
             const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
@@ -127,16 +112,8 @@ __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, 
             }
         }
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            if (jj >= jn) continue;
-            float2* y = Y + i + (size_t)n1 * (j0 + jj);
-            if (S == 1) {
-                *y = acc[jj];
-            } else {
-                atomicAdd(&y->x, acc[jj].x);
-                atomicAdd(&y->y, acc[jj].y);
-            }
-        }
+        for (int jj = 0; jj < 4; ++jj)
+            if (jj < jn) Y[i + (size_t)n1 * (j0 + jj)] = acc[jj];
     }
 }
 

@@ -80,8 +80,11 @@ def test_tprod_empty_dims(tp):
 
 
 # ----------------------------------------------------------------------------- tran
+# multiples of 4 take the float4 64 x 64 tile path (with ragged tiles: 132, 68, 200), the rest
+# the scalar 32 x 32 path
 @pytest.mark.parametrize("shape", [(1, 1, 1), (3, 5, 4), (33, 65, 7), (64, 64, 16), (100, 3, 1),
-                                   (31, 97, 2)])
+                                   (31, 97, 2), (4, 4, 3), (132, 68, 5), (200, 132, 1),
+                                   (64, 200, 64), (8, 12, 256)])
 def test_tran_bit_exact(tp, shape):
     A = randn(shape, 5)
     T = host(tp, tp.tran(dev(tp, A)))
