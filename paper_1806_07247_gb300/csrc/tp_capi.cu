@@ -354,19 +354,40 @@ struct FftBatch {
     }
     tp_status launch(Workspace& ws, bool inverse, cudaStream_t s) {
         if (jobs.empty()) return TP_OK;
+        // the per-length kernels for n3 <= 64 run one launch per register class: jobs are
+        // grouped by class and each group's tiles count from 0
+        const bool small = fft_small_path(max_n3, uniform_n3);
+        if (small)
+            std::stable_sort(jobs.begin(), jobs.end(), [](const FftJob& a, const FftJob& b) {
+                return fft_small_class(a.n3) < fft_small_class(b.n3);
+            });
+        std::vector<int64_t> group_tiles;
+        std::vector<size_t> group_first;
         int64_t tiles = 0;
-        for (auto& j : jobs) {
-            j.tile_begin = (int32_t)tiles;
-            tiles += fft_tiles(j.P, max_n3, uniform_n3);
+        for (size_t i = 0; i < jobs.size(); ++i) {
+            if (i == 0 || (small && fft_small_class(jobs[i].n3) != fft_small_class(jobs[i - 1].n3))) {
+                group_first.push_back(i);
+                group_tiles.push_back(0);
+                tiles = 0;
+            }
+            jobs[i].tile_begin = (int32_t)tiles;
+            tiles += fft_tiles(jobs[i].P, max_n3, uniform_n3, jobs[i].n3);
+            if (tiles > 0x7fffffffLL) return TP_ERR_UNSUPPORTED;
+            group_tiles.back() = tiles;
         }
-        if (tiles > 0x7fffffffLL) return TP_ERR_UNSUPPORTED;
+        group_first.push_back(jobs.size());
         FftJob* d = ws.take<FftJob>(jobs.size());
         TP_TRY(ws.check());
         TP_TRY(upload(d, jobs, s));
-        cudaError_t e =
-            inverse ? launch_irfft(d, (int)jobs.size(), (int)tiles, max_n3, uniform_n3, vec, s)
-                    : launch_rfft(d, (int)jobs.size(), (int)tiles, max_n3, uniform_n3, vec, s);
-        return from_cuda(e);
+        for (size_t g = 0; g + 1 < group_first.size(); ++g) {
+            const size_t a = group_first[g], n = group_first[g + 1] - a;
+            const int cls = small ? fft_small_class(jobs[a].n3) : -1;
+            cudaError_t e =
+                inverse ? launch_irfft(d + a, (int)n, (int)group_tiles[g], max_n3, uniform_n3, vec, s, cls)
+                        : launch_rfft(d + a, (int)n, (int)group_tiles[g], max_n3, uniform_n3, vec, s, cls);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        return TP_OK;
     }
 };
 

@@ -15,7 +15,8 @@
 //
 // This direct form serves n3 > 64; a launch whose tubes all have the same power-of-two
 // n3 <= 64 uses the register FFT kernels further below, and any other launch with n3 <= 64
-// the register-resident direct kernels after them.
+// the register-resident mixed-radix FFT kernels after them (a direct paired DFT for the odd
+// prime lengths 37..61).
 #include <math.h>
 
 #include <mutex>
@@ -350,9 +351,9 @@ __global__ void __launch_bounds__(256) irfft_reg_kernel(const FftJob* __restrict
 bool reg_fft_size(int n3) { return n3 >= 2 && n3 <= 64 && (n3 & (n3 - 1)) == 0; }
 
 // ---------------------------------------------------------------------------------------
-// Any n3 <= 64 (launches whose tubes differ in n3): one thread per tube, the tube in
-// registers, the real DFT by its definition with every index a compile-time constant, so
-// each twiddle is an operand read straight from the constant bank.  Samples t and n3 - t are
+// Odd prime n3 in 37..61 (launches whose tubes differ in n3, see the mixed-radix kernels
+// below for the other lengths): one thread per tube, the tube in registers, the real DFT by
+// its definition.  Samples t and n3 - t are
 // paired: Re X[k] = x0 + sum_t (x_t + x_{n3-t}) cos(2 pi k t / n3) (+ (-1)^k x_{n3/2}),
 // Im X[k] = -sum_t (x_t - x_{n3-t}) sin(2 pi k t / n3), and the inverse pairs the same way.
 // A CTA's tubes belong to one job, so the switch on n3 is uniform.
@@ -427,6 +428,254 @@ __device__ __forceinline__ void irdft_small(const float2* __restrict__ X, int64_
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Mixed-radix FFTs for the other n3 <= 64, one compile-time plan per length.  A complex DFT of
+// length M is split by its smallest prime factor R (decimation in time: R sub-DFTs of length
+// M / R, twiddles, then R-point DFTs), down to prime lengths, which are computed from their
+// definition with the symmetric pairing of samples t and P - t and of frequencies k and P - k
+// (about (P - 1)^2 real multiply-adds).  Every index and twiddle index is a compile-time
+// constant, so the data stay in registers and each twiddle is an operand read from the
+// constant bank (c_twall holds exp(2 pi i m / n) for every n <= 64).
+//   Even n3:  one tube per thread, z[t] = x[2t] + i x[2t+1], a complex FFT of length n3 / 2 and
+//             the split X[k] = E[k] + W^k O[k] (the inverse runs these steps backwards).
+//   Odd n3 that is composite or <= 31:  two tubes per thread (a and b), z = x_a + i x_b, a
+//             complex FFT of length n3, X_a[k] = (Z[k] + conj Z[n3-k]) / 2,
+//             X_b[k] = (Z[k] - conj Z[n3-k]) / (2i).
+//   Odd primes 37..61: the direct paired DFT above (fully unrolled code for those lengths
+//             would not fit the instruction cache).
+// ---------------------------------------------------------------------------------------
+__host__ __device__ constexpr int smallest_factor(int n) {
+    for (int p = 2; p * p <= n; ++p)
+        if (n % p == 0) return p;
+    return n;
+}
+
+enum : int { SMALL_DIRECT = 0, SMALL_EVEN = 1, SMALL_TWO = 2 };
+// How a tube of length n3 <= 64 is transformed (see above).
+__host__ __device__ constexpr int small_kind(int n3) {
+    return (n3 >= 2 && n3 % 2 == 0) ? SMALL_EVEN
+           : (n3 >= 3 && (n3 <= 31 || smallest_factor(n3) != n3)) ? SMALL_TWO
+                                                                  : SMALL_DIRECT;
+}
+
+// exp(S 2 pi i m / N) for S = +1 or -1 (m a compile-time constant after unrolling).
+template <int N, int S>
+__device__ __forceinline__ float2 twc(int m) {
+    const float2 w = c_twall[N * (N - 1) / 2 + ((m % N) + N) % N];
+    return S > 0 ? w : make_float2(w.x, -w.y);
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// In-place DFT of prime length P: X[k] = sum_t z[t] exp(S 2 pi i k t / P).
+template <int P, int S>
+__device__ __forceinline__ void dft_prime(float2 (&z)[P]) {
+    if constexpr (P == 2) {
+        const float2 a = z[0], b = z[1];
+        z[0] = cadd(a, b);
+        z[1] = csub(a, b);
+    } else if constexpr (P > 2) {
+        constexpr int H = (P - 1) / 2;
+        float2 sp[H + 1], sm[H + 1];
+        const float2 z0 = z[0];
+        float2 sum = z0;
+#pragma unroll
+        for (int t = 1; t <= H; ++t) {
+            sp[t] = cadd(z[t], z[P - t]);
+            sm[t] = csub(z[t], z[P - t]);
+            sum = cadd(sum, sp[t]);
+        }
+        z[0] = sum;
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            float2 a = z0, b = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int t = 1; t <= H; ++t) {
+                const float2 w = twc<P, 1>(k * t);  // (cos, sin) of 2 pi k t / P
+                a.x = fmaf(sp[t].x, w.x, a.x);
+                a.y = fmaf(sp[t].y, w.x, a.y);
+                b.x = fmaf(sm[t].x, w.y, b.x);
+                b.y = fmaf(sm[t].y, w.y, b.y);
+            }
+            // X[k] = a + S i b,  X[P - k] = a - S i b
+            if (S > 0) {
+                z[k] = make_float2(a.x - b.y, a.y + b.x);
+                z[P - k] = make_float2(a.x + b.y, a.y - b.x);
+            } else {
+                z[k] = make_float2(a.x + b.y, a.y - b.x);
+                z[P - k] = make_float2(a.x - b.y, a.y + b.x);
+            }
+        }
+    }
+}
+
+// In-place DFT of length M (natural order in and out), split by the smallest prime factor.
+template <int M, int S>
+__device__ __forceinline__ void cfft(float2 (&z)[M]) {
+    constexpr int R = smallest_factor(M);
+    if constexpr (M == 1) {
+    } else if constexpr (R == M) {
+        dft_prime<M, S>(z);
+    } else {
+        constexpr int Q = M / R;
+        float2 sub[R][Q];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) sub[r][q] = z[r + R * q];
+#pragma unroll
+        for (int r = 0; r < R; ++r) cfft<Q, S>(sub[r]);
+        // X[k + Q s] = sum_r exp(S 2 pi i r s / R) (exp(S 2 pi i r k / M) Sub_r[k])
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            float2 t[R];
+            t[0] = sub[0][k];
+#pragma unroll
+            for (int r = 1; r < R; ++r) t[r] = cmul(sub[r][k], twc<M, S>(r * k));
+            dft_prime<R, S>(t);
+#pragma unroll
+            for (int q = 0; q < R; ++q) z[k + Q * q] = t[q];
+        }
+    }
+}
+
+// Even N: real DFT of one tube through a complex FFT of length N / 2.
+template <int N>
+__device__ __forceinline__ void rfft_even(const float* __restrict__ x, int64_t P, float2* X) {
+    constexpr int M = N / 2;
+    float2 z[M];
+#pragma unroll
+    for (int t = 0; t < M; ++t) z[t] = make_float2(__ldg(x + P * (2 * t)), __ldg(x + P * (2 * t + 1)));
+    cfft<M, -1>(z);
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+        const float2 zk = z[k % M], zc = z[(M - k) % M];
+        const float2 e = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+        const float2 o = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+        const float2 w = twc<N, -1>(k);
+        float2 Xk = make_float2(e.x + (w.x * o.x - w.y * o.y), e.y + (w.x * o.y + w.y * o.x));
+        if (k == 0 || k == M) Xk.y = 0.f;
+        X[P * k] = Xk;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void irfft_even(const float2* __restrict__ X, int64_t P, float* x) {
+    constexpr int M = N / 2;
+    float2 Xv[M + 1];
+#pragma unroll
+    for (int k = 0; k <= M; ++k) Xv[k] = __ldg(X + P * k);
+    Xv[0].y = 0.f;  // the real slices of Eq. 8
+    Xv[M].y = 0.f;
+    float2 z[M];  // Z[k] = E[k] + i O[k]
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const float2 xk = Xv[k], xc = Xv[M - k];
+        const float2 e = make_float2(0.5f * (xk.x + xc.x), 0.5f * (xk.y - xc.y));
+        const float2 d = make_float2(0.5f * (xk.x - xc.x), 0.5f * (xk.y + xc.y));
+        const float2 o = cmul(d, twc<N, 1>(k));
+        z[k] = make_float2(e.x - o.y, e.y + o.x);
+    }
+    cfft<M, 1>(z);
+    const float s = 1.f / (float)M;
+#pragma unroll
+    for (int t = 0; t < M; ++t) {
+        x[P * (2 * t)] = z[t].x * s;
+        x[P * (2 * t + 1)] = z[t].y * s;
+    }
+}
+
+// Odd N: real DFTs of two tubes a and b through one complex FFT of length N.
+template <int N>
+__device__ __forceinline__ void rfft_two(const float* __restrict__ xa, const float* __restrict__ xb,
+                                         int64_t P, float2* Xa, float2* Xb, bool has_b) {
+    float2 z[N];
+#pragma unroll
+    for (int t = 0; t < N; ++t)
+        z[t] = make_float2(__ldg(xa + P * t), has_b ? __ldg(xb + P * t) : 0.f);
+    cfft<N, -1>(z);
+#pragma unroll
+    for (int k = 0; k <= N / 2; ++k) {
+        const float2 zk = z[k], zc = z[(N - k) % N];
+        float2 a = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+        float2 b = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+        if (k == 0) a.y = b.y = 0.f;
+        Xa[P * k] = a;
+        if (has_b) Xb[P * k] = b;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void irfft_two(const float2* __restrict__ Xa, const float2* __restrict__ Xb,
+                                          int64_t P, float* xa, float* xb, bool has_b) {
+    float2 z[N];  // Z[k] = X_a[k] + i X_b[k] over all N frequencies
+#pragma unroll
+    for (int k = 0; k <= N / 2; ++k) {
+        float2 a = __ldg(Xa + P * k);
+        float2 b = has_b ? __ldg(Xb + P * k) : make_float2(0.f, 0.f);
+        if (k == 0) a.y = b.y = 0.f;
+        z[k] = make_float2(a.x - b.y, a.y + b.x);
+        if (k > 0) z[N - k] = make_float2(a.x + b.y, b.x - a.y);  // conj(a) + i conj(b)
+    }
+    cfft<N, 1>(z);
+    const float s = 1.f / (float)N;
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        xa[P * t] = z[t].x * s;
+        if (has_b) xb[P * t] = z[t].y * s;
+    }
+}
+
+// Register class of the transforms of length n3 <= 64 (ptxas, sm_103a): '0' needs at most 64
+// registers, '1' at most 128, '2' more.  Each class runs in its own kernel instantiation whose
+// launch bounds give it 4, 2 or 1 CTAs of 256 threads per SM.
+// Bit n3 - 1 of kClassAtLeast1 / kClass2: class >= 1 / class 2.
+constexpr unsigned long long kClassAtLeast1 = 0xffffbae555400000ull, kClass2 = 0x4145100000000000ull;
+__host__ __device__ constexpr int small_class(int n3) {
+    return (int)((kClassAtLeast1 >> (n3 - 1)) & 1ull) + (int)((kClass2 >> (n3 - 1)) & 1ull);
+}
+
+// Tubes per CTA of the kernels below for a job of length n3 (two per thread for SMALL_TWO).
+__host__ __device__ constexpr int small_tubes_per_cta(int n3) {
+    return small_kind(n3) == SMALL_TWO ? 512 : 256;
+}
+
+template <int N, int CLS>
+__device__ __forceinline__ void rfft_small_one(const FftJob& J, int64_t p0) {
+    const int64_t P = J.P;
+    if constexpr (small_class(N) != CLS) {
+    } else if constexpr (small_kind(N) == SMALL_TWO) {
+        const int64_t p = p0 + threadIdx.x;
+        if (p >= P) return;
+        const bool hb = p + 256 < P;
+        rfft_two<N>(J.x + p, J.x + p + 256, P, J.X + p, J.X + p + 256, hb);
+    } else {
+        const int64_t p = p0 + threadIdx.x;
+        if (p >= P) return;
+        if constexpr (small_kind(N) == SMALL_EVEN) rfft_even<N>(J.x + p, P, J.X + p);
+        else rdft_small<N>(J.x + p, P, J.X + p);
+    }
+}
+
+template <int N, int CLS>
+__device__ __forceinline__ void irfft_small_one(const FftJob& J, int64_t p0) {
+    const int64_t P = J.P;
+    float* x = const_cast<float*>(J.x);
+    if constexpr (small_class(N) != CLS) {
+    } else if constexpr (small_kind(N) == SMALL_TWO) {
+        const int64_t p = p0 + threadIdx.x;
+        if (p >= P) return;
+        const bool hb = p + 256 < P;
+        irfft_two<N>(J.X + p, J.X + p + 256, P, x + p, x + p + 256, hb);
+    } else {
+        const int64_t p = p0 + threadIdx.x;
+        if (p >= P) return;
+        if constexpr (small_kind(N) == SMALL_EVEN) irfft_even<N>(J.X + p, P, x + p);
+        else irdft_small<N>(J.X + p, P, x + p);
+    }
+}
+
 #define TP_SMALL_CASES(M) \
     M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16) \
     M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) \
@@ -434,32 +683,52 @@ __device__ __forceinline__ void irdft_small(const float2* __restrict__ X, int64_
     M(45) M(46) M(47) M(48) M(49) M(50) M(51) M(52) M(53) M(54) M(55) M(56) M(57) M(58) \
     M(59) M(60) M(61) M(62) M(63) M(64)
 
-__global__ void __launch_bounds__(256) rfft_small_kernel(const FftJob* __restrict__ jobs, int njobs) {
+// A CTA's tubes belong to one job, so the switch on n3 is uniform.  A launch holds the jobs of
+// one register class CLS only.
+template <int CLS>
+__global__ void __launch_bounds__(256, CLS == 0 ? 4 : (CLS == 1 ? 2 : 1))
+    rfft_small_kernel(const FftJob* __restrict__ jobs, int njobs) {
     const FftJob J = jobs[find_job(jobs, njobs, blockIdx.x)];
-    const int64_t p = (int64_t)(blockIdx.x - J.tile_begin) * 256 + threadIdx.x;
-    if (p >= J.P) return;
-    const float* x = J.x + p;
-    float2* X = J.X + p;
+    const int64_t p0 = (int64_t)(blockIdx.x - J.tile_begin) * small_tubes_per_cta(J.n3);
     switch (J.n3) {
-#define TP_FWD(n) case n: rdft_small<n>(x, J.P, X); break;
+#define TP_FWD(n) case n: rfft_small_one<n, CLS>(J, p0); break;
         TP_SMALL_CASES(TP_FWD)
 #undef TP_FWD
         default: break;
     }
 }
 
-__global__ void __launch_bounds__(256) irfft_small_kernel(const FftJob* __restrict__ jobs, int njobs) {
+template <int CLS>
+__global__ void __launch_bounds__(256, CLS == 0 ? 4 : (CLS == 1 ? 2 : 1))
+    irfft_small_kernel(const FftJob* __restrict__ jobs, int njobs) {
     const FftJob J = jobs[find_job(jobs, njobs, blockIdx.x)];
-    const int64_t p = (int64_t)(blockIdx.x - J.tile_begin) * 256 + threadIdx.x;
-    if (p >= J.P) return;
-    const float2* X = J.X + p;
-    float* x = const_cast<float*>(J.x) + p;
+    const int64_t p0 = (int64_t)(blockIdx.x - J.tile_begin) * small_tubes_per_cta(J.n3);
     switch (J.n3) {
-#define TP_INV(n) case n: irdft_small<n>(X, J.P, x); break;
+#define TP_INV(n) case n: irfft_small_one<n, CLS>(J, p0); break;
         TP_SMALL_CASES(TP_INV)
 #undef TP_INV
         default: break;
     }
+}
+
+template <bool INV>
+cudaError_t launch_small(const FftJob* d_jobs, int njobs, int tiles, int cls, cudaStream_t s) {
+    switch (cls) {
+        case 0:
+            if (INV) irfft_small_kernel<0><<<tiles, 256, 0, s>>>(d_jobs, njobs);
+            else rfft_small_kernel<0><<<tiles, 256, 0, s>>>(d_jobs, njobs);
+            break;
+        case 1:
+            if (INV) irfft_small_kernel<1><<<tiles, 256, 0, s>>>(d_jobs, njobs);
+            else rfft_small_kernel<1><<<tiles, 256, 0, s>>>(d_jobs, njobs);
+            break;
+        case 2:
+            if (INV) irfft_small_kernel<2><<<tiles, 256, 0, s>>>(d_jobs, njobs);
+            else rfft_small_kernel<2><<<tiles, 256, 0, s>>>(d_jobs, njobs);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 std::mutex g_tw_mutex;
@@ -518,8 +787,10 @@ cudaError_t ensure_twiddles() {
     return cudaSuccess;
 }
 
-int fft_tiles(int64_t P, int max_n3, int uniform_n3) {
-    const int tp = (reg_fft_size(uniform_n3) || max_n3 <= kSmallN3) ? 256 : tubes_per_cta(max_n3);
+int fft_tiles(int64_t P, int max_n3, int uniform_n3, int n3) {
+    const int tp = reg_fft_size(uniform_n3) ? 256
+                   : max_n3 <= kSmallN3    ? small_tubes_per_cta(n3)
+                                           : tubes_per_cta(max_n3);
     return (int)((P + tp - 1) / tp);
 }
 
@@ -539,13 +810,19 @@ cudaError_t launch_reg(const FftJob* d_jobs, int njobs, int tiles, int n3, cudaS
     return cudaGetLastError();
 }
 
+bool fft_small_path(int max_n3, int uniform_n3) {
+    return !reg_fft_size(uniform_n3) && max_n3 <= kSmallN3;
+}
+
+int fft_small_class(int n3) { return (n3 >= 1 && n3 <= kSmallN3) ? small_class(n3) : 0; }
+
 cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
-                        int uniform_n3, bool vec_ok, cudaStream_t s) {
+                        int uniform_n3, bool vec_ok, cudaStream_t s, int small_cls) {
     if (total_tiles <= 0) return cudaSuccess;
     if (reg_fft_size(uniform_n3)) return launch_reg<false>(d_jobs, njobs, total_tiles, uniform_n3, s);
     if (max_n3 <= kSmallN3) {
-        rfft_small_kernel<<<total_tiles, 256, 0, s>>>(d_jobs, njobs);
-        return cudaGetLastError();
+        const int cls = small_cls >= 0 ? small_cls : fft_small_class(uniform_n3);
+        return launch_small<false>(d_jobs, njobs, total_tiles, cls, s);
     }
     int tp = tubes_per_cta(max_n3);
     size_t smem = fft_smem_bytes(max_n3, false);
@@ -555,12 +832,12 @@ cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int ma
 }
 
 cudaError_t launch_irfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
-                         int uniform_n3, bool vec_ok, cudaStream_t s) {
+                         int uniform_n3, bool vec_ok, cudaStream_t s, int small_cls) {
     if (total_tiles <= 0) return cudaSuccess;
     if (reg_fft_size(uniform_n3)) return launch_reg<true>(d_jobs, njobs, total_tiles, uniform_n3, s);
     if (max_n3 <= kSmallN3) {
-        irfft_small_kernel<<<total_tiles, 256, 0, s>>>(d_jobs, njobs);
-        return cudaGetLastError();
+        const int cls = small_cls >= 0 ? small_cls : fft_small_class(uniform_n3);
+        return launch_small<true>(d_jobs, njobs, total_tiles, cls, s);
     }
     int tp = tubes_per_cta(max_n3);
     size_t smem = fft_smem_bytes(max_n3, true);

@@ -34,14 +34,20 @@ struct FftJob {
 cudaError_t ensure_twiddles();
 
 // Forward real DFT of every tube, frequencies 0..h-1 (unnormalised, Eq. 2).  uniform_n3 is
-// the common n3 of all jobs of the launch, or 0 when they differ.
+// the common n3 of all jobs of the launch, or 0 when they differ.  On the small-n3 path
+// (fft_small_path) a launch holds jobs of one register class (fft_small_class), given as
+// small_cls (-1: the class of uniform_n3).
 cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
-                        int uniform_n3, bool vec_ok, cudaStream_t s);
+                        int uniform_n3, bool vec_ok, cudaStream_t s, int small_cls = -1);
 // Inverse DFT from the half spectrum with the conjugate mirror implied, scaled by 1/n3.
 cudaError_t launch_irfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
-                         int uniform_n3, bool vec_ok, cudaStream_t s);
-// CTAs one job needs (tubes per CTA depend on the kernel the launch uses).
-int fft_tiles(int64_t P, int max_n3, int uniform_n3);
+                         int uniform_n3, bool vec_ok, cudaStream_t s, int small_cls = -1);
+// True when launches over jobs with these lengths use the per-length kernels for n3 <= 64.
+bool fft_small_path(int max_n3, int uniform_n3);
+// Register class (0, 1, 2) of the per-length kernel of n3 <= 64.
+int fft_small_class(int n3);
+// CTAs one job of length n3 needs (tubes per CTA depend on the kernel the launch uses).
+int fft_tiles(int64_t P, int max_n3, int uniform_n3, int n3);
 
 // ---------------------------------------------------------------------------
 // Slice GEMMs (tp_gemm.cu): C_k = A_k B_k for k < nslices, complex, column-major.

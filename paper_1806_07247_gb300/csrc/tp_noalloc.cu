@@ -147,7 +147,7 @@ extern "C" tp_status tp_prox_tnn_noalloc(const float* Y, float* X, int64_t n1, i
     if (cudaGetLastError() != cudaSuccess) return TP_ERR_CUDA;
     const bool vec = (P % 4 == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15u) == 0) &&
                      ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
-    const int tiles = fft_tiles(P, (int)n3, (int)n3);
+    const int tiles = fft_tiles(P, (int)n3, (int)n3, (int)n3);
     if (launch_rfft(fft, 1, tiles, (int)n3, (int)n3, vec, s) != cudaSuccess) return TP_ERR_CUDA;
     SvdLaunch L;
     L.jobs = svd;

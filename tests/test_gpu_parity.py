@@ -53,6 +53,25 @@ def test_tprod_parity(tp, dims):
     assert rel(C, ref) < TOL_FP32
 
 
+@pytest.mark.parametrize("n3", list(range(1, 65)) + [127, 251, 256])
+def test_tprod_parity_every_tube_length(tp, n3):
+    # every per-length DFT kernel (even lengths, two-tube odd lengths, direct odd primes) and
+    # the direct kernel above 64, forward and inverse
+    A, B = randn((13, 7, n3), 100 + n3), randn((7, 5, n3), 200 + n3)
+    C = host(tp, tp.tprod(dev(tp, A), dev(tp, B)))
+    assert rel(C, O.tprod_fourier(A, B)) < TOL_FP32
+
+
+def test_batched_prox_mixed_tube_lengths_all_classes(tp):
+    # one batched call over every n3 in 1..64: the DFT launches group the tensors by register
+    # class; 20 x 31 = 620 tubes covers both tubes of the two-tube kernels and a ragged tail
+    Ys = [randn((20, 31, n3), 300 + n3) for n3 in range(1, 65)]
+    taus = [median_sigma(Y) for Y in Ys]
+    outs = tp.prox_tnn_batched([dev(tp, Y) for Y in Ys], taus)
+    for Y, tau, out in zip(Ys, taus, outs):
+        assert rel(host(tp, out), O.prox_tnn(Y, tau)) < TOL_FP32, Y.shape
+
+
 @pytest.mark.parametrize("n3", [1, 2, 3, 4, 8, 9, 16, 32, 64, 65, 128])
 def test_tprod_identity_tensor(tp, n3):
     # Def. 2.3: A * I = I * A = A; covers the register FFT sizes (powers of two <= 64) and the
