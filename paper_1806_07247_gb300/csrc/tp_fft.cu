@@ -438,9 +438,10 @@ __device__ __forceinline__ void irdft_small(const float2* __restrict__ X, int64_
 // constant bank (c_twall holds exp(2 pi i m / n) for every n <= 64).
 //   Even n3:  one tube per thread, z[t] = x[2t] + i x[2t+1], a complex FFT of length n3 / 2 and
 //             the split X[k] = E[k] + W^k O[k] (the inverse runs these steps backwards).
-//   Odd n3 that is composite or <= 31:  two tubes per thread (a and b), z = x_a + i x_b, a
-//             complex FFT of length n3, X_a[k] = (Z[k] + conj Z[n3-k]) / 2,
-//             X_b[k] = (Z[k] - conj Z[n3-k]) / (2i).
+//   Odd n3 that is composite or <= 31:  one tube per thread, a complex FFT of length n3 on
+//             x + 0i (two tubes packed as x_a + i x_b would halve the work, but rounding
+//             errors of one tube would then reach the other: a zero tube beside a non-zero one
+//             would no longer come out exactly zero).
 //   Odd primes 37..61: the direct paired DFT above (fully unrolled code for those lengths
 //             would not fit the instruction cache).
 // ---------------------------------------------------------------------------------------
@@ -450,11 +451,11 @@ __host__ __device__ constexpr int smallest_factor(int n) {
     return n;
 }
 
-enum : int { SMALL_DIRECT = 0, SMALL_EVEN = 1, SMALL_TWO = 2 };
+enum : int { SMALL_DIRECT = 0, SMALL_EVEN = 1, SMALL_ODD = 2 };
 // How a tube of length n3 <= 64 is transformed (see above).
 __host__ __device__ constexpr int small_kind(int n3) {
     return (n3 >= 2 && n3 % 2 == 0) ? SMALL_EVEN
-           : (n3 >= 3 && (n3 <= 31 || smallest_factor(n3) != n3)) ? SMALL_TWO
+           : (n3 >= 3 && (n3 <= 31 || smallest_factor(n3) != n3)) ? SMALL_ODD
                                                                   : SMALL_DIRECT;
 }
 
@@ -586,74 +587,58 @@ __device__ __forceinline__ void irfft_even(const float2* __restrict__ X, int64_t
     }
 }
 
-// Odd N: real DFTs of two tubes a and b through one complex FFT of length N.
+// Odd N: real DFT of one tube through a complex FFT of length N on x + 0i.
 template <int N>
-__device__ __forceinline__ void rfft_two(const float* __restrict__ xa, const float* __restrict__ xb,
-                                         int64_t P, float2* Xa, float2* Xb, bool has_b) {
+__device__ __forceinline__ void rfft_odd(const float* __restrict__ x, int64_t P, float2* X) {
     float2 z[N];
 #pragma unroll
-    for (int t = 0; t < N; ++t)
-        z[t] = make_float2(__ldg(xa + P * t), has_b ? __ldg(xb + P * t) : 0.f);
+    for (int t = 0; t < N; ++t) z[t] = make_float2(__ldg(x + P * t), 0.f);
     cfft<N, -1>(z);
 #pragma unroll
     for (int k = 0; k <= N / 2; ++k) {
-        const float2 zk = z[k], zc = z[(N - k) % N];
-        float2 a = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
-        float2 b = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
-        if (k == 0) a.y = b.y = 0.f;
-        Xa[P * k] = a;
-        if (has_b) Xb[P * k] = b;
+        float2 v = z[k];
+        if (k == 0) v.y = 0.f;
+        X[P * k] = v;
     }
 }
 
+// Inverse: the full spectrum from the half (Z[N - k] = conj Z[k]), a complex FFT, the real part.
 template <int N>
-__device__ __forceinline__ void irfft_two(const float2* __restrict__ Xa, const float2* __restrict__ Xb,
-                                          int64_t P, float* xa, float* xb, bool has_b) {
-    float2 z[N];  // Z[k] = X_a[k] + i X_b[k] over all N frequencies
+__device__ __forceinline__ void irfft_odd(const float2* __restrict__ X, int64_t P, float* x) {
+    float2 z[N];
 #pragma unroll
     for (int k = 0; k <= N / 2; ++k) {
-        float2 a = __ldg(Xa + P * k);
-        float2 b = has_b ? __ldg(Xb + P * k) : make_float2(0.f, 0.f);
-        if (k == 0) a.y = b.y = 0.f;
-        z[k] = make_float2(a.x - b.y, a.y + b.x);
-        if (k > 0) z[N - k] = make_float2(a.x + b.y, b.x - a.y);  // conj(a) + i conj(b)
+        float2 v = __ldg(X + P * k);
+        if (k == 0) v.y = 0.f;
+        z[k] = v;
+        if (k > 0) z[N - k] = make_float2(v.x, -v.y);
     }
     cfft<N, 1>(z);
     const float s = 1.f / (float)N;
 #pragma unroll
-    for (int t = 0; t < N; ++t) {
-        xa[P * t] = z[t].x * s;
-        if (has_b) xb[P * t] = z[t].y * s;
-    }
+    for (int t = 0; t < N; ++t) x[P * t] = z[t].x * s;
 }
 
 // Register class of the transforms of length n3 <= 64 (ptxas, sm_103a): '0' needs at most 64
 // registers, '1' at most 128, '2' more.  Each class runs in its own kernel instantiation whose
 // launch bounds give it 4, 2 or 1 CTAs of 256 threads per SM.
 // Bit n3 - 1 of kClassAtLeast1 / kClass2: class >= 1 / class 2.
-constexpr unsigned long long kClassAtLeast1 = 0xffffbae555400000ull, kClass2 = 0x4145100000000000ull;
+constexpr unsigned long long kClassAtLeast1 = 0xffffbae500000000ull, kClass2 = 0x0ull;
 __host__ __device__ constexpr int small_class(int n3) {
     return (int)((kClassAtLeast1 >> (n3 - 1)) & 1ull) + (int)((kClass2 >> (n3 - 1)) & 1ull);
 }
 
-// Tubes per CTA of the kernels below for a job of length n3 (two per thread for SMALL_TWO).
-__host__ __device__ constexpr int small_tubes_per_cta(int n3) {
-    return small_kind(n3) == SMALL_TWO ? 512 : 256;
-}
+// Tubes per CTA of the kernels below (one per thread).
+__host__ __device__ constexpr int small_tubes_per_cta(int) { return 256; }
 
 template <int N, int CLS>
 __device__ __forceinline__ void rfft_small_one(const FftJob& J, int64_t p0) {
     const int64_t P = J.P;
-    if constexpr (small_class(N) != CLS) {
-    } else if constexpr (small_kind(N) == SMALL_TWO) {
-        const int64_t p = p0 + threadIdx.x;
-        if (p >= P) return;
-        const bool hb = p + 256 < P;
-        rfft_two<N>(J.x + p, J.x + p + 256, P, J.X + p, J.X + p + 256, hb);
-    } else {
+    if constexpr (small_class(N) == CLS) {
         const int64_t p = p0 + threadIdx.x;
         if (p >= P) return;
         if constexpr (small_kind(N) == SMALL_EVEN) rfft_even<N>(J.x + p, P, J.X + p);
+        else if constexpr (small_kind(N) == SMALL_ODD) rfft_odd<N>(J.x + p, P, J.X + p);
         else rdft_small<N>(J.x + p, P, J.X + p);
     }
 }
@@ -662,16 +647,11 @@ template <int N, int CLS>
 __device__ __forceinline__ void irfft_small_one(const FftJob& J, int64_t p0) {
     const int64_t P = J.P;
     float* x = const_cast<float*>(J.x);
-    if constexpr (small_class(N) != CLS) {
-    } else if constexpr (small_kind(N) == SMALL_TWO) {
-        const int64_t p = p0 + threadIdx.x;
-        if (p >= P) return;
-        const bool hb = p + 256 < P;
-        irfft_two<N>(J.X + p, J.X + p + 256, P, x + p, x + p + 256, hb);
-    } else {
+    if constexpr (small_class(N) == CLS) {
         const int64_t p = p0 + threadIdx.x;
         if (p >= P) return;
         if constexpr (small_kind(N) == SMALL_EVEN) irfft_even<N>(J.X + p, P, x + p);
+        else if constexpr (small_kind(N) == SMALL_ODD) irfft_odd<N>(J.X + p, P, x + p);
         else irdft_small<N>(J.X + p, P, x + p);
     }
 }

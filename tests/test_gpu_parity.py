@@ -64,7 +64,7 @@ def test_tprod_parity_every_tube_length(tp, n3):
 
 def test_batched_prox_mixed_tube_lengths_all_classes(tp):
     # one batched call over every n3 in 1..64: the DFT launches group the tensors by register
-    # class; 20 x 31 = 620 tubes covers both tubes of the two-tube kernels and a ragged tail
+    # class; 20 x 31 = 620 tubes spans three CTAs of 256 tubes with a ragged tail
     Ys = [randn((20, 31, n3), 300 + n3) for n3 in range(1, 65)]
     taus = [median_sigma(Y) for Y in Ys]
     outs = tp.prox_tnn_batched([dev(tp, Y) for Y in Ys], taus)
