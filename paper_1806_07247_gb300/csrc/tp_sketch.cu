@@ -117,48 +117,125 @@ __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, 
     }
 }
 
-// Z (n2 x l, ld n2) = A^H Y (Y: n1 x l, ld n1, shared).  A work item is one column of A, a
-// chunk of 4 columns of Y and (when items are fewer than threads) a range of rows; partial
-// sums over row ranges meet in Z through shared-memory atomics.
-__device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real, const float2* Y,
-                        float2* Z, int l) {
-    const int nch = (l + 3) >> 2;
-    const int items = n2 * nch;
-    const int parts = max(1, min((int)blockDim.x / max(items, 1), 8));
-    const int span = (n1 + parts - 1) / parts;
+// ---------------------------------------------------------------------------------------
+// The sketch products on the tensor cores: warp-level mma.m16n8k8 in 3xTF32 (x = hi + lo with
+// hi = tf32(x), lo = tf32(x - hi); a b ~ hi hi + hi lo + lo hi, FP32 accumulation).
+//
+// A complex product Y = H X (H: M x K, X: K x l) becomes one real product Y' = H' B' with
+//   H'(m, 2c + p) = (Re, Im)[p] of H(m, c),
+//   B'(2c, 2j) = Re X(c, j), B'(2c + 1, 2j) = -Im X(c, j),
+//   B'(2c, 2j + 1) = Im X(c, j), B'(2c + 1, 2j + 1) = Re X(c, j),
+// so that columns 2j and 2j + 1 of Y' are the real and imaginary parts of Y(:, j).  An MMA
+// tile is 16 rows of H by 4 complex columns of Y over 4 complex columns of H (8 real K).  With
+// g = lane / 4 and t = lane % 4 the fragments are: A rows g and g + 8, K columns t and t + 4
+// (complex column t / 2 and t / 2 + 2, part t % 2); B K rows t and t + 4, column g (complex
+// column g / 2, part g % 2); D rows g and g + 8, columns 2t and 2t + 1 -- the (re, im) pair of
+// complex output column t.
+// H is the Fourier slice A (H = A for Y = A X) or its conjugate transpose (H = A^H for
+// Z = A^H Y); X is a shared-memory matrix (ld K).  Warps take (row tile, group of column tiles,
+// K part) items; when the items do not fill the CTA the K range is split and
+// the parts meet in Y through shared-memory atomics.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+        "{%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Entry (m, c) of H as the part p of a complex value: H = A (AH = false) or H = A^H.
+template <bool AH>
+__device__ __forceinline__ float h_entry(const float2* __restrict__ A, int n1, int n2, bool real,
+                                         int m, int c, int p) {
+    const int rows = AH ? n2 : n1, cols = AH ? n1 : n2;
+    if (m >= rows || c >= cols) return 0.f;
+    const float2 v = AH ? A[c + (int64_t)n1 * m] : A[m + (int64_t)n1 * c];
+    if (p == 0) return v.x;
+    return real ? 0.f : (AH ? -v.y : v.y);
+}
+
+// Y (rows x l, ld rows, shared) = H X (X: K x l, ld K, shared).  kNG column tiles (4 complex
+// columns each) share the A fragments of a K step.
+constexpr int kNG = 2;
+template <bool AH>
+__device__ void mult_tc(const float2* __restrict__ A, int n1, int n2, bool real, const float2* X,
+                        float2* Y, int l) {
+    const int rows = AH ? n2 : n1, K = AH ? n1 : n2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int nw = blockDim.x >> 5;
+    const int mtiles = (rows + 15) >> 4, ntiles = (l + 3) >> 2, ngroups = (ntiles + kNG - 1) / kNG;
+    const int ksteps = (K + 3) >> 2;
+    int parts = 1;
+    while (parts < 8 && mtiles * ngroups * parts * 2 <= nw && ksteps >= 4 * parts) parts *= 2;
     if (parts > 1) {
-        for (int t = threadIdx.x; t < n2 * l; t += (int)blockDim.x) Z[t] = make_float2(0.f, 0.f);
+        for (int e = threadIdx.x; e < rows * l; e += blockDim.x) Y[e] = make_float2(0.f, 0.f);
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < items * parts; t += (int)blockDim.x) {
-        const int c = t % n2, rest = t / n2, ch = rest % nch, pr = rest / nch;
-        const int j0 = ch * 4, jn = min(4, l - j0);
-        const int i0 = pr * span, i1 = min(n1, i0 + span);
-        float2 acc[4];
+    const int items = mtiles * ngroups * parts;
+    for (int it = warp; it < items; it += nw) {
+        const int mt = it % mtiles, rest = it / mtiles, ng = rest % ngroups, part = rest / ngroups;
+        const int kb = (int)((int64_t)ksteps * part / parts), ke = (int)((int64_t)ksteps * (part + 1) / parts);
+        const int nt0 = kNG * ng, ntn = min(kNG, ntiles - nt0);
+        float d[kNG][4];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) acc[jj] = make_float2(0.f, 0.f);
-        const float2* y = Y + (size_t)n1 * j0;
-#pragma unroll 4
-        for (int i = i0; i < i1; ++i) {
-            const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
+        for (int q = 0; q < kNG; ++q) d[q][0] = d[q][1] = d[q][2] = d[q][3] = 0.f;
+        const int r0 = 16 * mt + g, p = t & 1;
+        for (int ks = kb; ks < ke; ++ks) {
+            const int c0 = 4 * ks + (t >> 1);
+            uint32_t ah[4], al[4];
+            split_tf32(h_entry<AH>(A, n1, n2, real, r0, c0, p), ah[0], al[0]);
+            split_tf32(h_entry<AH>(A, n1, n2, real, r0 + 8, c0, p), ah[1], al[1]);
+            split_tf32(h_entry<AH>(A, n1, n2, real, r0, c0 + 2, p), ah[2], al[2]);
+            split_tf32(h_entry<AH>(A, n1, n2, real, r0 + 8, c0 + 2, p), ah[3], al[3]);
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                if (jj < jn) {
-                    const float2 yv = y[i + (size_t)n1 * jj];
-                    acc[jj].x = fmaf(a.x, yv.x, fmaf(a.y, yv.y, acc[jj].x));  // conj(a) y
-                    acc[jj].y = fmaf(a.x, yv.y, fmaf(-a.y, yv.x, acc[jj].y));
+            for (int q = 0; q < kNG; ++q) {
+                if (q >= ntn) break;
+                const int j = 4 * (nt0 + q) + (g >> 1), qq = g & 1;
+                float bv[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = c0 + 2 * h;
+                    float2 x = make_float2(0.f, 0.f);
+                    if (c < K && j < l) x = X[c + (size_t)K * j];
+                    // B'(2c + p, 2j + qq)
+                    bv[h] = qq == 0 ? (p == 0 ? x.x : -x.y) : (p == 0 ? x.y : x.x);
                 }
+                uint32_t bh0, bl0, bh1, bl1;
+                split_tf32(bv[0], bh0, bl0);
+                split_tf32(bv[1], bh1, bl1);
+                mma_tf32(d[q], ah, bh0, bh1);
+                mma_tf32(d[q], ah, bl0, bl1);
+                mma_tf32(d[q], al, bh0, bh1);
             }
         }
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            if (jj < jn) {
-                float2* z = Z + c + (size_t)n2 * (j0 + jj);
+        for (int q = 0; q < kNG; ++q) {
+            if (q >= ntn) break;
+            const int j = 4 * (nt0 + q) + t;
+            if (j >= l) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + 8 * h;
+                if (r >= rows) continue;
+                float2* y = Y + r + (size_t)rows * j;
                 if (parts == 1) {
-                    *z = acc[jj];
+                    *y = make_float2(d[q][2 * h], d[q][2 * h + 1]);
                 } else {
-                    atomicAdd(&z->x, acc[jj].x);
-                    atomicAdd(&z->y, acc[jj].y);
+                    atomicAdd(&y->x, d[q][2 * h]);
+                    atomicAdd(&y->y, d[q][2 * h + 1]);
                 }
             }
         }
@@ -516,18 +593,18 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         }
     }
     __syncthreads();
-    mult_a(A, n1, n2, real, bs, bq, l);
+    mult_tc<false>(A, n1, n2, real, bs, bq, l);
     __syncthreads();
     float2* r = orth3(bq, bs, n1, l, G, C, &s_flag, TP_SKETCH_Q > 0 ? 2 : 3);
     bool ok = r != nullptr;
     if (ok && r != bq) { bs = bq; bq = r; }
     for (int it = 0; ok && it < TP_SKETCH_Q; ++it) {
-        mult_ah(A, n1, n2, real, bq, bz, l);
+        mult_tc<true>(A, n1, n2, real, bq, bz, l);
         r = orth3(bz, bs, n2, l, G, C, &s_flag, 2);
         ok = r != nullptr;
         if (!ok) break;
         if (r != bz) { bs = bz; bz = r; }
-        mult_a(A, n1, n2, real, bz, bq, l);
+        mult_tc<false>(A, n1, n2, real, bz, bq, l);
         __syncthreads();
         r = orth3(bq, bs, n1, l, G, C, &s_flag, 2);
         ok = r != nullptr;
@@ -536,7 +613,7 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     // 3. Z = A^H Q = B^H; one-sided Jacobi Z V = D with orthogonal columns, sigma_j = ||d_j||,
     // so A ~ Q Z^H = (Q V) diag(sigma) (D / sigma)^H
     if (ok) {
-        mult_ah(A, n1, n2, real, bq, bz, l);
+        mult_tc<true>(A, n1, n2, real, bq, bz, l);
         gram(bz, n2, l, G);
         ok = eigh_cta(G, V, l, s_rot, s_pq);
     }
@@ -621,7 +698,7 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         }
         __syncthreads();
         // 4(b): residuals of the kept triplets, T = A R in one pass
-        mult_a(A, n1, n2, real, R, T, l);
+        mult_tc<false>(A, n1, n2, real, R, T, l);
         __syncthreads();
         float worst = 0.f;
         for (int j = warp; j < l; j += kTS / 32) {
