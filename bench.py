@@ -249,11 +249,30 @@ def svd_launch_groups(shapes, shape=None):
     return len(groups)
 
 
-# Kernel launches of one learned batched prox call besides the Jacobi groups: the tube DFT,
-# features, proposer MLP, binning, one persistent sketch launch per size class, a collect and
-# a sketch launch per retry round, the inverse DFT.
-SKETCH_CLASSES, SKETCH_RETRY_ROUNDS = 4, 4
-LEARNED_FIXED_LAUNCHES = 4 + SKETCH_CLASSES + 2 * SKETCH_RETRY_ROUNDS + 1
+# Kernel launches of one learned batched prox call besides the Jacobi groups and the tube DFTs:
+# features, proposer MLP, binning, one persistent sketch launch per size class (four shared-
+# memory classes and the global-scratch class), a collect and a sketch launch per retry round.
+SKETCH_CLASSES, SKETCH_RETRY_ROUNDS = 5, 4
+LEARNED_FIXED_LAUNCHES = 3 + SKETCH_CLASSES + 2 * SKETCH_RETRY_ROUNDS
+
+# Register classes of the per-length DFT kernels for n3 <= 64 (bit n3 - 1: class >= 1, class 2),
+# the masks of the library's DFT source; a batch of mixed lengths launches each direction once
+# per class present.
+DFT_CLASS_AT_LEAST_1, DFT_CLASS_2 = 0xffffbae500000000, 0x0
+
+
+def dft_launches(n3s):
+    """Launches of one direction of the tube DFT over tensors of these lengths."""
+    n3s = [int(n) for n in n3s if n > 0]
+    if not n3s:
+        return 0
+    uniform = len(set(n3s)) == 1
+    if uniform and n3s[0] & (n3s[0] - 1) == 0 and n3s[0] <= 64 and n3s[0] >= 2:
+        return 1  # register radix-2 kernel
+    if max(n3s) > 64:
+        return 1  # direct kernel
+    cls = {((DFT_CLASS_AT_LEAST_1 >> (n - 1)) & 1) + ((DFT_CLASS_2 >> (n - 1)) & 1) for n in n3s}
+    return len(cls)
 
 
 def make_batch(tp, synth, count, seed, device):
@@ -554,7 +573,8 @@ def run_tp(args):
                        "Jacobi fallback", "tensors": len(specs), "free_slices": slices,
                        "seed": rank, "input_bytes": nbytes,
                        "l2": "inputs larger than L2 (%.2f GB in + out per step)" % (2 * nbytes / 1e9)},
-            "gpu_launches": (LEARNED_FIXED_LAUNCHES + groups) * args.steps,
+            "gpu_launches": (LEARNED_FIXED_LAUNCHES + 2 * dft_launches([n3 for _, _, n3 in shapes])
+                             + groups) * args.steps,
             "roofline": roof,
             "stages_ms": st,
             "learned": {"fallback_fraction": float((fb == 1).mean()),

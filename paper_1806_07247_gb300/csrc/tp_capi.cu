@@ -444,6 +444,24 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         bytes += 3 * Workspace::round(sizeof(int32_t) * slices);  // extra power its, 2 retry lists
         bytes += Workspace::round(sizeof(int32_t) * 2 * kSketchRetryRounds);  // retry counters
     }
+    // sketch class 4 (tall buffers in global memory): one scratch slot per CTA of its launch,
+    // sized for the largest slice whose widest possible sketch misses the shared-memory classes
+    int sms_ws = 0;
+    TP_TRY(sm_count(&sms_ws));
+    int64_t g_stride = 0;
+    size_t g_small = 0;
+    if (learned) {
+        for (int64_t t = 0; t < count; ++t) {
+            const int n1 = (int)d[t].n1, n2 = (int)d[t].n2;
+            if (n1 == 0 || n2 == 0 || d[t].n3 == 0) continue;
+            const int lcap = std::min(kSketchMaxL, std::min(n1, n2) - 1);
+            if (lcap <= 0 || sketch_smem_need(n1, n2, lcap) <= kSketchSmemCap) continue;
+            g_stride = std::max<int64_t>(g_stride, (int64_t)3 * std::max(n1, n2) * lcap);
+            g_small = std::max(g_small, sketch_small_need(n1, n2, lcap));
+        }
+        g_stride = (g_stride + 31) & ~(int64_t)31;
+        if (g_stride > 0) bytes += Workspace::round(sizeof(float2) * (size_t)g_stride * sms_ws);
+    }
     if (train) bytes += Workspace::round(sizeof(float) * proposer_fit_scratch_floats((int)slices));
     Workspace ws(s);
     TP_TRY(ws.reserve(bytes));
@@ -532,11 +550,14 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         });
         TP_TRY(upload(d_order, sorted, s));
         SketchCaps caps;
-        caps.n = 4;
+        caps.n = kSketchClasses;
         caps.bytes[0] = 55 * 1024;
         caps.bytes[1] = 74 * 1024;
         caps.bytes[2] = 112 * 1024;
-        caps.bytes[3] = 220 * 1024;
+        caps.bytes[3] = kSketchSmemCap;
+        caps.bytes[4] = 0xffffffffu;  // the rest: tall buffers in global scratch
+        float2* gscratch = g_stride > 0 ? ws.take<float2>((size_t)g_stride * sms_ws) : nullptr;
+        TP_TRY(ws.check());
         TP_CUDA(launch_sketch_bin(d_nat, d_order, (int)slices, ell, flags, caps, d_queues, d_qcount,
                                   s));
         int sms = 0;
@@ -545,7 +566,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         // another attempt (more power iterations or a wider sketch), in the largest class
         constexpr int kRetryRounds = kSketchRetryRounds;
         constexpr int kRetryMinDim = 96;
-        const size_t retry_smem = caps.bytes[caps.n - 1];
+        const size_t retry_smem = caps.bytes[3];
         TP_CUDA(cudaMemsetAsync(d_extra, 0, sizeof(int32_t) * slices, s));
         TP_CUDA(cudaMemsetAsync(d_rcount, 0, sizeof(int32_t) * 2 * kRetryRounds, s));
         auto base = [&]() {
@@ -561,15 +582,24 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             return sp;
         };
         for (int c = 0; c < caps.n; ++c) {
-            const int per_sm = sketch_blocks_per_sm(caps.bytes[c]);
+            const bool global_class = c == caps.n - 1;
+            // the global-scratch class: its shared part, one CTA per SM (one scratch slot each);
+            // empty unless some slice can need it (then a one-CTA launch finds its queue empty)
+            const size_t smem = global_class ? (g_stride > 0 ? g_small : (size_t)1024) : caps.bytes[c];
+            const int per_sm = sketch_blocks_per_sm(smem);
             if (per_sm <= 0) return TP_ERR_CUDA;
             SketchParams sp = base();
             sp.order = d_queues + (size_t)c * slices;
             sp.queue_len = d_qcount + 2 * c;
             sp.queue_next = d_qcount + 2 * c + 1;
-            sp.smem_bytes = (int)caps.bytes[c];
-            const int64_t grid = std::min<int64_t>(slices, (int64_t)sms * per_sm);
-            TP_CUDA(launch_sketch_svt(d_nat, (int)grid, caps.bytes[c], sp, s));
+            sp.smem_bytes = (int)smem;
+            int64_t grid = std::min<int64_t>(slices, (int64_t)sms * per_sm);
+            if (global_class) {
+                sp.gscratch = gscratch;
+                sp.gstride = g_stride;
+                grid = g_stride > 0 ? std::min<int64_t>(slices, sms_ws) : 1;
+            }
+            TP_CUDA(launch_sketch_svt(d_nat, (int)grid, smem, sp, s));
         }
         const int retry_per_sm = sketch_blocks_per_sm(retry_smem);
         if (retry_per_sm <= 0) return TP_ERR_CUDA;

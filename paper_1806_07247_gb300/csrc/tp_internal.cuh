@@ -146,7 +146,7 @@ cudaError_t launch_diag_scatter(const float* tubes, int r, int n3, float* S, int
 // ---------------------------------------------------------------------------
 // Learned-rank randomized SVT (tp_sketch.cu)
 // ---------------------------------------------------------------------------
-constexpr int kSketchMaxL = 32;        // widest sketch
+constexpr int kSketchMaxL = 48;        // widest sketch
 constexpr int kProposerInputs = 12;    // features per slice
 constexpr int kProposerFloats = TP_PROPOSER_FLOATS;
 
@@ -165,17 +165,27 @@ struct SketchParams {
     int retry_launch = 0;            // 1: `order` is a retry list (per-slice power iterations)
     float resid_tol;
     int smem_bytes;       // dynamic shared memory of the launch
+    float2* gscratch = nullptr;  // if set: the three tall buffers of CTA b at gscratch + b * gstride
+    int64_t gstride = 0;         // (complex values), the rest in shared memory
 };
 
+// Shared memory of the sketch of one slice without its three max(n1, n2) x l buffers.
+__host__ __device__ inline size_t sketch_small_need(int n1, int n2, int l) {
+    return sizeof(float2) * ((size_t)3 * l * l + (size_t)n1 + n2 + 2 * kSketchMaxL) +
+           sizeof(float) * (2 * kSketchMaxL) + 64;
+}
+// ... and with them.
 __host__ __device__ inline size_t sketch_smem_need(int n1, int n2, int l) {
     const size_t nm = n1 > n2 ? n1 : n2;
-    return sizeof(float2) * (3 * nm * l + (size_t)3 * l * l + (size_t)n1 + n2 + 2 * kSketchMaxL) +
-           sizeof(float) * (2 * kSketchMaxL) + 64;
+    return sizeof(float2) * 3 * nm * l + sketch_small_need(n1, n2, l);
 }
 // Retry rounds of the sketch path (each: collect the failed slices, sketch them again).
 constexpr int kSketchRetryRounds = 4;
 // Size classes of the sketch kernel's queues: shared memory bytes per CTA, increasing.
-constexpr int kSketchClasses = 4;
+// Classes 0..3 hold everything in shared memory; the last class keeps the three tall buffers
+// in global memory (slices larger than the largest shared-memory class).
+constexpr int kSketchClasses = 5;
+constexpr uint32_t kSketchSmemCap = 220 * 1024;  // the largest shared-memory class
 struct SketchCaps {
     int n;
     uint32_t bytes[kSketchClasses];

@@ -117,125 +117,48 @@ __device__ void mult_a(const float2* __restrict__ A, int n1, int n2, bool real, 
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// The sketch products on the tensor cores: warp-level mma.m16n8k8 in 3xTF32 (x = hi + lo with
-// hi = tf32(x), lo = tf32(x - hi); a b ~ hi hi + hi lo + lo hi, FP32 accumulation).
-//
-// A complex product Y = H X (H: M x K, X: K x l) becomes one real product Y' = H' B' with
-//   H'(m, 2c + p) = (Re, Im)[p] of H(m, c),
-//   B'(2c, 2j) = Re X(c, j), B'(2c + 1, 2j) = -Im X(c, j),
-//   B'(2c, 2j + 1) = Im X(c, j), B'(2c + 1, 2j + 1) = Re X(c, j),
-// so that columns 2j and 2j + 1 of Y' are the real and imaginary parts of Y(:, j).  An MMA
-// tile is 16 rows of H by 4 complex columns of Y over 4 complex columns of H (8 real K).  With
-// g = lane / 4 and t = lane % 4 the fragments are: A rows g and g + 8, K columns t and t + 4
-// (complex column t / 2 and t / 2 + 2, part t % 2); B K rows t and t + 4, column g (complex
-// column g / 2, part g % 2); D rows g and g + 8, columns 2t and 2t + 1 -- the (re, im) pair of
-// complex output column t.
-// H is the Fourier slice A (H = A for Y = A X) or its conjugate transpose (H = A^H for
-// Z = A^H Y); X is a shared-memory matrix (ld K).  Warps take (row tile, group of column tiles,
-// K part) items; when the items do not fill the CTA the K range is split and
-// the parts meet in Y through shared-memory atomics.
-// ---------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-    hi = to_tf32(x);
-    lo = to_tf32(x - __uint_as_float(hi));
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-        "{%8, %9}, {%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Entry (m, c) of H as the part p of a complex value: H = A (AH = false) or H = A^H.
-template <bool AH>
-__device__ __forceinline__ float h_entry(const float2* __restrict__ A, int n1, int n2, bool real,
-                                         int m, int c, int p) {
-    const int rows = AH ? n2 : n1, cols = AH ? n1 : n2;
-    if (m >= rows || c >= cols) return 0.f;
-    const float2 v = AH ? A[c + (int64_t)n1 * m] : A[m + (int64_t)n1 * c];
-    if (p == 0) return v.x;
-    return real ? 0.f : (AH ? -v.y : v.y);
-}
-
-// Y (rows x l, ld rows, shared) = H X (X: K x l, ld K, shared).  kNG column tiles (4 complex
-// columns each) share the A fragments of a K step.
-constexpr int kNG = 2;
-template <bool AH>
-__device__ void mult_tc(const float2* __restrict__ A, int n1, int n2, bool real, const float2* X,
-                        float2* Y, int l) {
-    const int rows = AH ? n2 : n1, K = AH ? n1 : n2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int nw = blockDim.x >> 5;
-    const int mtiles = (rows + 15) >> 4, ntiles = (l + 3) >> 2, ngroups = (ntiles + kNG - 1) / kNG;
-    const int ksteps = (K + 3) >> 2;
-    int parts = 1;
-    while (parts < 8 && mtiles * ngroups * parts * 2 <= nw && ksteps >= 4 * parts) parts *= 2;
+// Z (n2 x l, ld n2) = A^H Y (Y: n1 x l, ld n1, shared).  A work item is one column of A, a
+// chunk of 4 columns of Y and (when items are fewer than threads) a range of rows; partial
+// sums over row ranges meet in Z through shared-memory atomics.
+__device__ void mult_ah(const float2* __restrict__ A, int n1, int n2, bool real, const float2* Y,
+                        float2* Z, int l) {
+    const int nch = (l + 3) >> 2;
+    const int items = n2 * nch;
+    const int parts = max(1, min((int)blockDim.x / max(items, 1), 8));
+    const int span = (n1 + parts - 1) / parts;
     if (parts > 1) {
-        for (int e = threadIdx.x; e < rows * l; e += blockDim.x) Y[e] = make_float2(0.f, 0.f);
+        for (int t = threadIdx.x; t < n2 * l; t += (int)blockDim.x) Z[t] = make_float2(0.f, 0.f);
         __syncthreads();
     }
-    const int items = mtiles * ngroups * parts;
-    for (int it = warp; it < items; it += nw) {
-        const int mt = it % mtiles, rest = it / mtiles, ng = rest % ngroups, part = rest / ngroups;
-        const int kb = (int)((int64_t)ksteps * part / parts), ke = (int)((int64_t)ksteps * (part + 1) / parts);
-        const int nt0 = kNG * ng, ntn = min(kNG, ntiles - nt0);
-        float d[kNG][4];
+    for (int t = threadIdx.x; t < items * parts; t += (int)blockDim.x) {
+        const int c = t % n2, rest = t / n2, ch = rest % nch, pr = rest / nch;
+        const int j0 = ch * 4, jn = min(4, l - j0);
+        const int i0 = pr * span, i1 = min(n1, i0 + span);
+        float2 acc[4];
 #pragma unroll
-        for (int q = 0; q < kNG; ++q) d[q][0] = d[q][1] = d[q][2] = d[q][3] = 0.f;
-        const int r0 = 16 * mt + g, p = t & 1;
-        for (int ks = kb; ks < ke; ++ks) {
-            const int c0 = 4 * ks + (t >> 1);
-            uint32_t ah[4], al[4];
-            split_tf32(h_entry<AH>(A, n1, n2, real, r0, c0, p), ah[0], al[0]);
-            split_tf32(h_entry<AH>(A, n1, n2, real, r0 + 8, c0, p), ah[1], al[1]);
-            split_tf32(h_entry<AH>(A, n1, n2, real, r0, c0 + 2, p), ah[2], al[2]);
-            split_tf32(h_entry<AH>(A, n1, n2, real, r0 + 8, c0 + 2, p), ah[3], al[3]);
+        for (int jj = 0; jj < 4; ++jj) acc[jj] = make_float2(0.f, 0.f);
+        const float2* y = Y + (size_t)n1 * j0;
+#pragma unroll 4
+        for (int i = i0; i < i1; ++i) {
+            const float2 a = ld_a(A, i + (int64_t)n1 * c, real);
 #pragma unroll
-            for (int q = 0; q < kNG; ++q) {
-                if (q >= ntn) break;
-                const int j = 4 * (nt0 + q) + (g >> 1), qq = g & 1;
-                float bv[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = c0 + 2 * h;
-                    float2 x = make_float2(0.f, 0.f);
-                    if (c < K && j < l) x = X[c + (size_t)K * j];
-                    // B'(2c + p, 2j + qq)
-                    bv[h] = qq == 0 ? (p == 0 ? x.x : -x.y) : (p == 0 ? x.y : x.x);
+            for (int jj = 0; jj < 4; ++jj) {
+                if (jj < jn) {
+                    const float2 yv = y[i + (size_t)n1 * jj];
+                    acc[jj].x = fmaf(a.x, yv.x, fmaf(a.y, yv.y, acc[jj].x));  // conj(a) y
+                    acc[jj].y = fmaf(a.x, yv.y, fmaf(-a.y, yv.x, acc[jj].y));
                 }
-                uint32_t bh0, bl0, bh1, bl1;
-                split_tf32(bv[0], bh0, bl0);
-                split_tf32(bv[1], bh1, bl1);
-                mma_tf32(d[q], ah, bh0, bh1);
-                mma_tf32(d[q], ah, bl0, bl1);
-                mma_tf32(d[q], al, bh0, bh1);
             }
         }
 #pragma unroll
-        for (int q = 0; q < kNG; ++q) {
-            if (q >= ntn) break;
-            const int j = 4 * (nt0 + q) + t;
-            if (j >= l) continue;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = r0 + 8 * h;
-                if (r >= rows) continue;
-                float2* y = Y + r + (size_t)rows * j;
+        for (int jj = 0; jj < 4; ++jj) {
+            if (jj < jn) {
+                float2* z = Z + c + (size_t)n2 * (j0 + jj);
                 if (parts == 1) {
-                    *y = make_float2(d[q][2 * h], d[q][2 * h + 1]);
+                    *z = acc[jj];
                 } else {
-                    atomicAdd(&y->x, d[q][2 * h]);
-                    atomicAdd(&y->y, d[q][2 * h + 1]);
+                    atomicAdd(&z->x, acc[jj].x);
+                    atomicAdd(&z->y, acc[jj].y);
                 }
             }
         }
@@ -278,16 +201,23 @@ __device__ bool chol_inv(float2* G, float2* C, int l, float shift, int* s_flag) 
         if (d) G[t].x += shift;
     }
     __syncthreads();
-    const int hw = tid >> 4, hl = tid & 15;  // 16 half-warps; rows hl and hl + 16
+    constexpr int kRowSets = (kLMax + 15) / 16;  // rows hl + 16 h of a half-warp, h < kRowSets
+    const int hw = tid >> 4, hl = tid & 15;       // 16 half-warps
     for (int j = 0; j < l; ++j) {
         if (warp == 0) {
-            const float2 cj = lane <= j ? C[lane + l * j] : make_float2(0.f, 0.f);
-            const float2 mj = lane < l ? G[lane + l * j] : make_float2(0.f, 0.f);
-            const float p = warp_sum(fmaf(cj.x, mj.x, cj.y * mj.y));  // c_j^H m_j (real)
+            float p = 0.f;
+            for (int m = lane; m <= j; m += 32) {
+                const float2 cj = C[m + l * j], mj = G[m + l * j];
+                p = fmaf(cj.x, mj.x, fmaf(cj.y, mj.y, p));  // c_j^H m_j (real)
+            }
+            p = warp_sum(p);
             const bool ok = p > 0.f;
             const float inv = ok ? 1.f / sqrtf(p) : 0.f;
-            if (lane <= j) C[lane + l * j] = make_float2(cj.x * inv, cj.y * inv);
-            if (lane < l) G[lane + l * j] = make_float2(mj.x * inv, mj.y * inv);
+            for (int m = lane; m < l; m += 32) {
+                if (m <= j) { C[m + l * j].x *= inv; C[m + l * j].y *= inv; }
+                G[m + l * j].x *= inv;
+                G[m + l * j].y *= inv;
+            }
             if (lane == 0) *s_flag = ok ? 0 : 1;
         }
         __syncthreads();
@@ -297,7 +227,7 @@ __device__ bool chol_inv(float2* G, float2* C, int l, float shift, int* s_flag) 
             const bool act = k < l;
             float hr = 0.f, hi = 0.f;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kRowSets; ++h) {
                 const int m = hl + 16 * h;
                 if (act && m <= k) {
                     const float2 mm = G[m + l * j], c = C[m + l * k];
@@ -312,7 +242,7 @@ __device__ bool chol_inv(float2* G, float2* C, int l, float shift, int* s_flag) 
             }
             if (act) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
+                for (int h = 0; h < kRowSets; ++h) {
                     const int m = hl + 16 * h;
                     if (m <= j) {
                         const float2 cj = C[m + l * j];
@@ -555,15 +485,20 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     const int q_retry = RETRY ? P.power_iters + P.extra_power[job] : 0;
 #define TP_SKETCH_Q (RETRY ? q_retry : P.power_iters)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool global_bufs = P.gscratch != nullptr;
     if (l <= 0 || l >= min(n1, n2) || l > kLMax ||
-        sketch_smem_need(n1, n2, l) > (size_t)P.smem_bytes) {
+        (global_bufs ? (sketch_small_need(n1, n2, l) > (size_t)P.smem_bytes ||
+                        (int64_t)3 * nm * l > P.gstride)
+                     : sketch_smem_need(n1, n2, l) > (size_t)P.smem_bytes)) {
         if (tid == 0) P.flag[job] = 1;
         return;
     }
-    float2* B0 = reinterpret_cast<float2*>(smem4);  // three max(n1, n2) x l buffers
+    // three max(n1, n2) x l buffers: in shared memory, or in this CTA's global scratch
+    float2* B0 = global_bufs ? P.gscratch + (int64_t)blockIdx.x * P.gstride
+                             : reinterpret_cast<float2*>(smem4);
     float2* B1 = B0 + (size_t)nm * l;
     float2* B2 = B1 + (size_t)nm * l;
-    float2* V = B2 + (size_t)nm * l;                // l x l
+    float2* V = global_bufs ? reinterpret_cast<float2*>(smem4) : B2 + (size_t)nm * l;  // l x l
     float2* G = V + (size_t)l * l;                  // l x l
     float2* C = G + (size_t)l * l;                  // l x l
     float2* xv = C + (size_t)l * l;                 // n2
@@ -593,18 +528,18 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         }
     }
     __syncthreads();
-    mult_tc<false>(A, n1, n2, real, bs, bq, l);
+    mult_a(A, n1, n2, real, bs, bq, l);
     __syncthreads();
     float2* r = orth3(bq, bs, n1, l, G, C, &s_flag, TP_SKETCH_Q > 0 ? 2 : 3);
     bool ok = r != nullptr;
     if (ok && r != bq) { bs = bq; bq = r; }
     for (int it = 0; ok && it < TP_SKETCH_Q; ++it) {
-        mult_tc<true>(A, n1, n2, real, bq, bz, l);
+        mult_ah(A, n1, n2, real, bq, bz, l);
         r = orth3(bz, bs, n2, l, G, C, &s_flag, 2);
         ok = r != nullptr;
         if (!ok) break;
         if (r != bz) { bs = bz; bz = r; }
-        mult_tc<false>(A, n1, n2, real, bz, bq, l);
+        mult_a(A, n1, n2, real, bz, bq, l);
         __syncthreads();
         r = orth3(bq, bs, n1, l, G, C, &s_flag, 2);
         ok = r != nullptr;
@@ -613,22 +548,28 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     // 3. Z = A^H Q = B^H; one-sided Jacobi Z V = D with orthogonal columns, sigma_j = ||d_j||,
     // so A ~ Q Z^H = (Q V) diag(sigma) (D / sigma)^H
     if (ok) {
-        mult_tc<true>(A, n1, n2, real, bq, bz, l);
+        mult_ah(A, n1, n2, real, bq, bz, l);
         gram(bz, n2, l, G);
         ok = eigh_cta(G, V, l, s_rot, s_pq);
     }
-    if (ok) {  // D = Z V over Z, by rows (a warp per row, lanes over columns)
+    if (ok) {  // D = Z V over Z, by rows (a warp per row, lanes over columns lane, lane + 32)
         for (int e = warp; e < n2; e += kTS / 32) {
-            float2 acc = make_float2(0.f, 0.f);
-            if (lane < l) {
-                for (int m = 0; m < l; ++m) {
-                    const float2 z = bz[e + (size_t)n2 * m], v = V[m + (size_t)l * lane];
-                    acc.x = fmaf(z.x, v.x, fmaf(-z.y, v.y, acc.x));
-                    acc.y = fmaf(z.x, v.y, fmaf(z.y, v.x, acc.y));
+            float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col = lane + 32 * h;
+                if (col < l) {
+                    for (int m = 0; m < l; ++m) {
+                        const float2 z = bz[e + (size_t)n2 * m], v = V[m + (size_t)l * col];
+                        acc[h].x = fmaf(z.x, v.x, fmaf(-z.y, v.y, acc[h].x));
+                        acc[h].y = fmaf(z.x, v.y, fmaf(z.y, v.x, acc[h].y));
+                    }
                 }
             }
             __syncwarp();
-            if (lane < l) bz[e + (size_t)n2 * lane] = acc;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (lane + 32 * h < l) bz[e + (size_t)n2 * (lane + 32 * h)] = acc[h];
         }
         __syncthreads();
     }
@@ -698,7 +639,7 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         }
         __syncthreads();
         // 4(b): residuals of the kept triplets, T = A R in one pass
-        mult_tc<false>(A, n1, n2, real, R, T, l);
+        mult_a(A, n1, n2, real, R, T, l);
         __syncthreads();
         float worst = 0.f;
         for (int j = warp; j < l; j += kTS / 32) {
@@ -1155,7 +1096,8 @@ __global__ void __launch_bounds__(1024) sketch_collect_kernel(const SvdJob* __re
         const int n1 = jobs[j].n1, n2 = jobs[j].n2, l = ell[j];
         bool again = min(n1, n2) >= min_dim;
         if (again && f == 1) {
-            extra[j] += 2;
+            again = sketch_smem_need(n1, n2, l) <= (size_t)smem;  // the retry launch's class
+            if (again) extra[j] += 2;
         } else if (again) {
             again = l + 4 < min(n1, n2) && l + 4 <= kLMax &&
                     sketch_smem_need(n1, n2, l + 4) <= (size_t)smem;

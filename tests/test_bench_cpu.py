@@ -2,9 +2,11 @@
 
 The launch-count mirror (`svd_launch_groups`, `LEARNED_FIXED_LAUNCHES`) must agree with what
 the GPU ran: an ncu launch list of the learned batched prox on the 512-tensor batch showed
-22 kernel launches per call, 10 of them `svd_kernel` over two calls (5 Jacobi launch groups at
-the default CTA shape), and a bench run under the autotuned shape (target 7, 32 warps, shared
-launches) reported 210 launches over 10 steps, i.e. 4 Jacobi groups.
+22 kernel launches per call with one DFT launch per direction, 10 of them `svd_kernel` over two
+calls (5 Jacobi launch groups at the default CTA shape), and a bench run under the autotuned
+shape (target 7, 32 warps, shared launches) reported 210 launches over 10 steps, i.e. 4 Jacobi
+groups.  The DFTs of mixed lengths now launch once per register class (two classes in this
+batch) and the sketch has a fifth (global-scratch) class launch, 25 launches per call.
 """
 import math
 import os
@@ -23,14 +25,31 @@ def _batch_shapes():
 
 
 def test_fixed_launches_of_a_learned_call():
-    # DFT, features, MLP, binning, 4 class launches, 4 x (collect + retry), inverse DFT
-    assert bench.LEARNED_FIXED_LAUNCHES == 17
+    # features, MLP, binning, 5 class launches, 4 x (collect + retry)
+    assert bench.LEARNED_FIXED_LAUNCHES == 16
+
+
+def test_dft_launch_mirror_matches_the_library_source():
+    # the register-class masks mirrored in bench.py are the ones the DFT source defines
+    import re
+    src = open(os.path.join(ROOT, "paper_1806_07247_gb300", "csrc", "tp_fft.cu")).read()
+    m = re.search(r"kClassAtLeast1 = (0x[0-9a-f]+)ull, kClass2 = (0x[0-9a-f]+)ull", src)
+    assert m, "class masks not found"
+    assert (int(m.group(1), 16), int(m.group(2), 16)) == (bench.DFT_CLASS_AT_LEAST_1,
+                                                          bench.DFT_CLASS_2)
+    # the batched workload (n3 in 4..64) has lengths of both classes 0 and 1
+    n3s = [s.n3 for s in synth.batched_specs(512, 0)]
+    assert bench.dft_launches(n3s) == 2
+    assert bench.dft_launches([64]) == 1 and bench.dft_launches([64, 64]) == 1
+    assert bench.dft_launches([100, 3]) == 1 and bench.dft_launches([5]) == 1
 
 
 def test_jacobi_groups_match_the_measured_launch_lists():
     shapes = _batch_shapes()
     assert bench.svd_launch_groups(shapes) == 5
-    assert bench.LEARNED_FIXED_LAUNCHES + bench.svd_launch_groups(shapes) == 22
+    n3s = [s.n3 for s in synth.batched_specs(512, 0)]
+    assert bench.LEARNED_FIXED_LAUNCHES + 2 * bench.dft_launches(n3s) + \
+        bench.svd_launch_groups(shapes) == 25
     tuned = {"target_lane_pairs": 7, "max_warps": 32, "split_launches": 0}
     assert bench.svd_launch_groups(shapes, tuned) == 4
 
