@@ -455,7 +455,8 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             const int n1 = (int)d[t].n1, n2 = (int)d[t].n2;
             if (n1 == 0 || n2 == 0 || d[t].n3 == 0) continue;
             const int lcap = std::min(kSketchMaxL, std::min(n1, n2) - 1);
-            if (lcap <= 0 || sketch_smem_need(n1, n2, lcap) <= kSketchSmemCap) continue;
+            if (lcap <= 0 || (lcap <= kNarrowL && sketch_smem_need(n1, n2, lcap) <= kSketchSmemCap))
+                continue;
             g_stride = std::max<int64_t>(g_stride, (int64_t)3 * std::max(n1, n2) * lcap);
             g_small = std::max(g_small, sketch_small_need(n1, n2, lcap));
         }
@@ -595,6 +596,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             sp.smem_bytes = (int)smem;
             int64_t grid = std::min<int64_t>(slices, (int64_t)sms * per_sm);
             if (global_class) {
+                sp.wide = 1;
                 sp.gscratch = gscratch;
                 sp.gstride = g_stride;
                 grid = g_stride > 0 ? std::min<int64_t>(slices, sms_ws) : 1;

@@ -147,6 +147,7 @@ cudaError_t launch_diag_scatter(const float* tubes, int r, int n3, float* S, int
 // Learned-rank randomized SVT (tp_sketch.cu)
 // ---------------------------------------------------------------------------
 constexpr int kSketchMaxL = 48;        // widest sketch
+constexpr int kNarrowL = 32;           // widest sketch of the shared-memory classes
 constexpr int kProposerInputs = 12;    // features per slice
 constexpr int kProposerFloats = TP_PROPOSER_FLOATS;
 
@@ -165,6 +166,7 @@ struct SketchParams {
     int retry_launch = 0;            // 1: `order` is a retry list (per-slice power iterations)
     float resid_tol;
     int smem_bytes;       // dynamic shared memory of the launch
+    int wide = 0;                // 1: widths up to kSketchMaxL (the last class; retries are wide)
     float2* gscratch = nullptr;  // if set: the three tall buffers of CTA b at gscratch + b * gstride
     int64_t gstride = 0;         // (complex values), the rest in shared memory
 };

@@ -193,7 +193,73 @@ __device__ void gram(const float2* Y, int n, int l, float2* G) {
 // every step needs only dot products of length l: warp 0 normalises c_j (and m_j), then one
 // half-warp per later column k forms h = m_j^H c_k and updates c_k -= h c_j, m_k -= h m_j.
 // Returns false (uniformly) if a norm is not positive (breakdown).
-__device__ bool chol_inv(float2* G, float2* C, int l, float shift, int* s_flag) {
+__device__ bool chol_inv_narrow(float2* G, float2* C, int l, float shift, int* s_flag) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int t = tid; t < l * l; t += kTS) {
+        const bool d = (t % l) == (t / l);
+        C[t] = make_float2(d ? 1.f : 0.f, 0.f);
+        if (d) G[t].x += shift;
+    }
+    __syncthreads();
+    const int hw = tid >> 4, hl = tid & 15;  // 16 half-warps; rows hl and hl + 16
+    for (int j = 0; j < l; ++j) {
+        if (warp == 0) {
+            const float2 cj = lane <= j ? C[lane + l * j] : make_float2(0.f, 0.f);
+            const float2 mj = lane < l ? G[lane + l * j] : make_float2(0.f, 0.f);
+            const float p = warp_sum(fmaf(cj.x, mj.x, cj.y * mj.y));  // c_j^H m_j (real)
+            const bool ok = p > 0.f;
+            const float inv = ok ? 1.f / sqrtf(p) : 0.f;
+            if (lane <= j) C[lane + l * j] = make_float2(cj.x * inv, cj.y * inv);
+            if (lane < l) G[lane + l * j] = make_float2(mj.x * inv, mj.y * inv);
+            if (lane == 0) *s_flag = ok ? 0 : 1;
+        }
+        __syncthreads();
+        if (*s_flag) return false;
+        for (int kb = j + 1; kb < l; kb += kTS / 16) {  // uniform over each warp
+            const int k = kb + hw;
+            const bool act = k < l;
+            float hr = 0.f, hi = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = hl + 16 * h;
+                if (act && m <= k) {
+                    const float2 mm = G[m + l * j], c = C[m + l * k];
+                    hr = fmaf(mm.x, c.x, fmaf(mm.y, c.y, hr));  // conj(m_j) c_k
+                    hi = fmaf(mm.x, c.y, fmaf(-mm.y, c.x, hi));
+                }
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                hr += __shfl_xor_sync(0xffffffffu, hr, o);
+                hi += __shfl_xor_sync(0xffffffffu, hi, o);
+            }
+            if (act) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int m = hl + 16 * h;
+                    if (m <= j) {
+                        const float2 cj = C[m + l * j];
+                        float2 c = C[m + l * k];
+                        c.x -= fmaf(hr, cj.x, -hi * cj.y);
+                        c.y -= fmaf(hr, cj.y, hi * cj.x);
+                        C[m + l * k] = c;
+                    }
+                    if (m < l) {
+                        const float2 mj = G[m + l * j];
+                        float2 mk = G[m + l * k];
+                        mk.x -= fmaf(hr, mj.x, -hi * mj.y);
+                        mk.y -= fmaf(hr, mj.y, hi * mj.x);
+                        G[m + l * k] = mk;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+__device__ bool chol_inv_wide(float2* G, float2* C, int l, float shift, int* s_flag) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int t = tid; t < l * l; t += kTS) {
         const bool d = (t % l) == (t / l);
@@ -266,6 +332,14 @@ __device__ bool chol_inv(float2* G, float2* C, int l, float shift, int* s_flag) 
     return true;
 }
 
+// The Cholesky inverse above: rows of a column in one lane of warp 0 and of each half-warp
+// (WIDE = false, l <= 32), or in several (WIDE = true, l <= kLMax).
+template <bool WIDE>
+__device__ __forceinline__ bool chol_inv(float2* G, float2* C, int l, float shift, int* s_flag) {
+    if constexpr (WIDE) return chol_inv_wide(G, C, l, shift, s_flag);
+    else return chol_inv_narrow(G, C, l, shift, s_flag);
+}
+
 // Yout (n x l) = Yin C for an upper triangular C (l x l); items of one row and 4 columns.
 __device__ void mult_upper(const float2* Yin, const float2* C, float2* Yout, int n, int l) {
     const int nq = (l + 3) >> 2;
@@ -299,6 +373,7 @@ __device__ void mult_upper(const float2* Yin, const float2* C, float2* Yout, int
 // (u = 2^-24) so that it cannot break down.  The passes alternate between Y and the scratch
 // S (both n x l); returns the buffer that holds the result, or nullptr if a pass still broke
 // down (the slice then goes to the Jacobi path).
+template <bool WIDE>
 __device__ float2* orth3(float2* Y, float2* S, int n, int l, float2* G, float2* C, int* s_flag,
                          int passes = 3) {
     float2* cur = Y;
@@ -311,7 +386,7 @@ __device__ float2* orth3(float2* Y, float2* S, int n, int l, float2* G, float2* 
             for (int j = 0; j < l; ++j) tr += G[j + l * j].x;
             shift = 11.f * (float)(n * l + l * (l + 1)) * 5.9604645e-08f * tr;
         }
-        if (!chol_inv(G, C, l, shift, s_flag)) return nullptr;
+        if (!chol_inv<WIDE>(G, C, l, shift, s_flag)) return nullptr;
         mult_upper(cur, C, oth, n, l);
         float2* t = cur;
         cur = oth;
@@ -458,6 +533,29 @@ __device__ void matvec_ah(const float2* __restrict__ A, int n1, int n2, bool rea
     __syncthreads();
 }
 
+// D = Z V over Z (n2 x l, l > 32) by rows: a warp per row, lanes over columns lane and lane + 32.
+__device__ __forceinline__ void zv_wide(float2* bz, const float2* V, int n2, int l) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = warp; e < n2; e += kTS / 32) {
+        float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int col = lane + 32 * h;
+            if (col < l) {
+                for (int m = 0; m < l; ++m) {
+                    const float2 z = bz[e + (size_t)n2 * m], v = V[m + (size_t)l * col];
+                    acc[h].x = fmaf(z.x, v.x, fmaf(-z.y, v.y, acc[h].x));
+                    acc[h].y = fmaf(z.x, v.y, fmaf(z.y, v.x, acc[h].y));
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (lane + 32 * h < l) bz[e + (size_t)n2 * (lane + 32 * h)] = acc[h];
+    }
+}
+
 // Shared state of one CTA of the sketch kernel besides the dynamic buffers.
 struct SketchShared {
     int flag, item;
@@ -470,7 +568,7 @@ struct SketchShared {
 // The whole sketch SVT of one slice (steps 2-5 of the file comment) by the calling CTA.
 // RETRY: the slice comes from a retry list and takes its extra power iterations from
 // P.extra_power (a first attempt uses P.power_iters alone, a block-uniform loop bound).
-template <bool RETRY>
+template <bool RETRY, bool WIDE>
 __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const SketchParams& P,
                            float4* smem4, SketchShared& sh) {
     int& s_flag = sh.flag;
@@ -485,8 +583,8 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     const int q_retry = RETRY ? P.power_iters + P.extra_power[job] : 0;
 #define TP_SKETCH_Q (RETRY ? q_retry : P.power_iters)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool global_bufs = P.gscratch != nullptr;
-    if (l <= 0 || l >= min(n1, n2) || l > kLMax ||
+    const bool global_bufs = WIDE && P.gscratch != nullptr;  // only the last class (wide)
+    if (l <= 0 || l >= min(n1, n2) || l > (WIDE ? kLMax : kNarrowL) ||
         (global_bufs ? (sketch_small_need(n1, n2, l) > (size_t)P.smem_bytes ||
                         (int64_t)3 * nm * l > P.gstride)
                      : sketch_smem_need(n1, n2, l) > (size_t)P.smem_bytes)) {
@@ -530,18 +628,18 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     __syncthreads();
     mult_a(A, n1, n2, real, bs, bq, l);
     __syncthreads();
-    float2* r = orth3(bq, bs, n1, l, G, C, &s_flag, TP_SKETCH_Q > 0 ? 2 : 3);
+    float2* r = orth3<WIDE>(bq, bs, n1, l, G, C, &s_flag, TP_SKETCH_Q > 0 ? 2 : 3);
     bool ok = r != nullptr;
     if (ok && r != bq) { bs = bq; bq = r; }
     for (int it = 0; ok && it < TP_SKETCH_Q; ++it) {
         mult_ah(A, n1, n2, real, bq, bz, l);
-        r = orth3(bz, bs, n2, l, G, C, &s_flag, 2);
+        r = orth3<WIDE>(bz, bs, n2, l, G, C, &s_flag, 2);
         ok = r != nullptr;
         if (!ok) break;
         if (r != bz) { bs = bz; bz = r; }
         mult_a(A, n1, n2, real, bz, bq, l);
         __syncthreads();
-        r = orth3(bq, bs, n1, l, G, C, &s_flag, 2);
+        r = orth3<WIDE>(bq, bs, n1, l, G, C, &s_flag, 2);
         ok = r != nullptr;
         if (ok && r != bq) { bs = bq; bq = r; }
     }
@@ -552,25 +650,22 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         gram(bz, n2, l, G);
         ok = eigh_cta(G, V, l, s_rot, s_pq);
     }
-    if (ok) {  // D = Z V over Z, by rows (a warp per row, lanes over columns lane, lane + 32)
+    if (ok && !WIDE) {  // D = Z V over Z, by rows (a warp per row, lanes over columns)
         for (int e = warp; e < n2; e += kTS / 32) {
-            float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int col = lane + 32 * h;
-                if (col < l) {
-                    for (int m = 0; m < l; ++m) {
-                        const float2 z = bz[e + (size_t)n2 * m], v = V[m + (size_t)l * col];
-                        acc[h].x = fmaf(z.x, v.x, fmaf(-z.y, v.y, acc[h].x));
-                        acc[h].y = fmaf(z.x, v.y, fmaf(z.y, v.x, acc[h].y));
-                    }
+            float2 acc = make_float2(0.f, 0.f);
+            if (lane < l) {
+                for (int m = 0; m < l; ++m) {
+                    const float2 z = bz[e + (size_t)n2 * m], v = V[m + (size_t)l * lane];
+                    acc.x = fmaf(z.x, v.x, fmaf(-z.y, v.y, acc.x));
+                    acc.y = fmaf(z.x, v.y, fmaf(z.y, v.x, acc.y));
                 }
             }
             __syncwarp();
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (lane + 32 * h < l) bz[e + (size_t)n2 * (lane + 32 * h)] = acc[h];
+            if (lane < l) bz[e + (size_t)n2 * lane] = acc;
         }
+        __syncthreads();
+    } else if (ok) {  // the same with up to kLMax columns
+        zv_wide(bz, V, n2, l);
         __syncthreads();
     }
     float smax = 0.f;
@@ -783,13 +878,15 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
 // One slice per CTA (P.queue_next == nullptr, CTA b takes P.order[b]), or a persistent grid
 // that takes slices P.order[i] from a work counter until the queue of *P.queue_len is empty;
 // the queue is ordered largest slice first, so the tail is made of small slices.
-template <bool RETRY>
+// WIDE: widths up to kLMax (the global-scratch class and the retry rounds); otherwise up to
+// kNarrowL, with the leaner code of one lane per column.
+template <bool RETRY, bool WIDE>
 __global__ void __launch_bounds__(kTS, 4) sketch_svt_kernel(const SvdJob* __restrict__ jobs,
                                                            SketchParams P) {
     extern __shared__ float4 smem4[];
     __shared__ SketchShared sh;
     if (!P.queue_next) {
-        sketch_one<RETRY>(jobs, P.order ? P.order[blockIdx.x] : (int)blockIdx.x, P, smem4, sh);
+        sketch_one<RETRY, WIDE>(jobs, P.order ? P.order[blockIdx.x] : (int)blockIdx.x, P, smem4, sh);
         return;
     }
     for (;;) {
@@ -798,7 +895,7 @@ __global__ void __launch_bounds__(kTS, 4) sketch_svt_kernel(const SvdJob* __rest
         const int item = sh.item;
         if (item >= *P.queue_len) break;
         const int job = P.order[item];
-        if (job >= 0 && job < P.njobs) sketch_one<RETRY>(jobs, job, P, smem4, sh);
+        if (job >= 0 && job < P.njobs) sketch_one<RETRY, WIDE>(jobs, job, P, smem4, sh);
         __syncthreads();  // the CTA is done with this slice's shared state
     }
 }
@@ -830,8 +927,12 @@ __global__ void __launch_bounds__(1024) sketch_bin_kernel(const SvdJob* __restri
             const int l = ell[job];
             if (l > 0 && l < min(J.n1, J.n2) && l <= kLMax) {
                 const size_t need = sketch_smem_need(J.n1, J.n2, l);
-                for (int q = 0; q < ncls; ++q)
-                    if (need <= caps.bytes[q]) { c = q; break; }
+                if (l > kNarrowL) {
+                    c = ncls - 1;  // the wide kernel runs only in the last class
+                } else {
+                    for (int q = 0; q < ncls; ++q)
+                        if (need <= caps.bytes[q]) { c = q; break; }
+                }
             }
             if (c < 0) flag[job] = 1;
         }
@@ -1137,14 +1238,15 @@ cudaError_t launch_sketch_bin(const SvdJob* jobs, const int32_t* sorted, int n, 
 
 // Both instantiations have the same resources; the first stands for them.
 int sketch_blocks_per_sm(size_t smem) {
-    for (const void* fn : {reinterpret_cast<const void*>(sketch_svt_kernel<false>),
-                           reinterpret_cast<const void*>(sketch_svt_kernel<true>)})
+    for (const void* fn : {reinterpret_cast<const void*>(sketch_svt_kernel<false, false>),
+                           reinterpret_cast<const void*>(sketch_svt_kernel<false, true>),
+                           reinterpret_cast<const void*>(sketch_svt_kernel<true, true>)})
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess)
             return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sketch_svt_kernel<false>, kTS, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sketch_svt_kernel<false, true>, kTS, smem) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -1153,14 +1255,16 @@ int sketch_blocks_per_sm(size_t smem) {
 cudaError_t launch_sketch_svt(const SvdJob* jobs, int ncta, size_t smem, const SketchParams& p,
                               cudaStream_t s) {
     if (ncta <= 0) return cudaSuccess;
-    const void* fn = p.retry_launch ? reinterpret_cast<const void*>(sketch_svt_kernel<true>)
-                                    : reinterpret_cast<const void*>(sketch_svt_kernel<false>);
+    const void* fn = p.retry_launch ? reinterpret_cast<const void*>(sketch_svt_kernel<true, true>)
+                     : p.wide       ? reinterpret_cast<const void*>(sketch_svt_kernel<false, true>)
+                                    : reinterpret_cast<const void*>(sketch_svt_kernel<false, false>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    if (p.retry_launch) sketch_svt_kernel<true><<<ncta, kTS, smem, s>>>(jobs, p);
-    else sketch_svt_kernel<false><<<ncta, kTS, smem, s>>>(jobs, p);
+    if (p.retry_launch) sketch_svt_kernel<true, true><<<ncta, kTS, smem, s>>>(jobs, p);
+    else if (p.wide) sketch_svt_kernel<false, true><<<ncta, kTS, smem, s>>>(jobs, p);
+    else sketch_svt_kernel<false, false><<<ncta, kTS, smem, s>>>(jobs, p);
     return cudaGetLastError();
 }
 
