@@ -1011,7 +1011,7 @@ def stream_leg(args, tp, synth, device):
 
     # proposer for these sizes and ranks
     t0 = time.time()
-    tcalls = [c for c in synth.stream_specs(8 * args.stream_calls, seed=1) if c.op == "prox"][:24]
+    tcalls = [c for c in synth.stream_specs(8 * args.stream_calls, seed=1) if c.op == "prox"][:96]
     tY = [low_rank(c.a) for c in tcalls]
     mse = tp.proposer_train(tY, [c.a.tau for c in tcalls], steps=300, seed=3)
     train = {"tensors": len(tY), "slices": sum(Y.shape[2] // 2 + 1 for Y in tY), "mse": mse,

@@ -92,8 +92,9 @@ typedef struct tp_options {
                             (same indexing as sweeps_out): with TP_METHOD_LEARNED, 0 if the
                             sketch path finished the slice, 1 if it fell back to Jacobi */
     int32_t* sketch_width_out; /* optional DEVICE array, same indexing: the sketch width of
-                            the slice's last attempt (the proposer's choice, 4 more after a
-                            wider retry; 0: the slice went straight to Jacobi) */
+                            the slice's last attempt (the proposer's choice, wider after a
+                            retry for an underestimated rank; 0: the slice went straight to
+                            Jacobi) */
     int32_t host_parts;  /* tp_prox_tnn_batched_host: parts the batch is cut into, 1 or 2
                             (0 = 2, the default). Two parts overlap a call's copies with its
                             own kernels; one part leaves that overlap to a caller that issues
@@ -123,9 +124,11 @@ typedef struct tp_options {
  *   tau, the kept triplets' residuals ||A r - sigma u|| (times their weight (sigma - tau)/sigma
  *   in the result) are below 1e-5 sigma_max and the
  *   deflated matrix's norm is estimated below 0.8 tau. A slice with min(n1, n2) >= 96 that
- *   fails is sketched again (up to twice) with two more power iterations, or 4 columns wider
- *   if the rank was underestimated; every other failed slice is recomputed by the Jacobi
- *   path. Error target 1e-4 relative (Frobenius) against the exact prox.
+ *   fails is sketched again (up to four times) with two more power iterations, or half again
+ *   as wide (at least 4 columns more, at most 48) if the rank was underestimated; every other
+ *   failed slice is recomputed by the Jacobi path. Widths up to 48; slices whose sketch
+ *   buffers exceed shared memory keep them in a global scratch area of the call. Error target
+ *   1e-4 relative (Frobenius) against the exact prox.
  */
 #define TP_METHOD_JACOBI 0
 #define TP_METHOD_LEARNED 1

@@ -608,14 +608,20 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
         for (int round = 0; round < kRetryRounds; ++round) {
             int32_t* list = d_retry + (size_t)(round & 1) * slices;
             TP_CUDA(launch_sketch_collect(d_nat, (int)slices, flags, ell, d_extra, kRetryMinDim,
-                                          (int)retry_smem, list, d_rcount + 2 * round, s));
+                                          (int)retry_smem, g_stride, list, d_rcount + 2 * round,
+                                          s));
             SketchParams sp = base();
             sp.retry_launch = 1;
             sp.order = list;
             sp.queue_len = d_rcount + 2 * round;       // round r: length, then work counter
             sp.queue_next = d_rcount + 2 * round + 1;
             sp.smem_bytes = (int)retry_smem;
-            const int64_t grid = std::min<int64_t>(slices, (int64_t)sms * retry_per_sm);
+            int64_t grid = std::min<int64_t>(slices, (int64_t)sms * retry_per_sm);
+            if (g_stride > 0) {
+                sp.gscratch = gscratch;
+                sp.gstride = g_stride;
+                grid = std::min<int64_t>(slices, sms_ws);
+            }
             TP_CUDA(launch_sketch_svt(d_nat, (int)grid, retry_smem, sp, s));
         }
         TP_TRY(o.mark(3, s));

@@ -198,8 +198,8 @@ cudaError_t launch_sketch_bin(const SvdJob* jobs, const int32_t* sorted, int n, 
                               int32_t* counts, cudaStream_t s);
 // Queues the failed slices worth another sketch (see tp_sketch.cu) into `list`.
 cudaError_t launch_sketch_collect(const SvdJob* jobs, int n, int32_t* flag, int32_t* ell,
-                                  int32_t* extra, int min_dim, int smem, int32_t* list,
-                                  int32_t* len, cudaStream_t s);
+                                  int32_t* extra, int min_dim, int smem, int64_t gstride,
+                                  int32_t* list, int32_t* len, cudaStream_t s);
 // out[j] = (flags[j] != 0): the per-slice fallback flags as 0 / 1.
 cudaError_t launch_flags01(const int32_t* flags, int32_t* out, int n, cudaStream_t s);
 // Resident CTAs of the sketch kernel per SM at this dynamic shared memory (0 on error).

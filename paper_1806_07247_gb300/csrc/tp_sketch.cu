@@ -583,7 +583,7 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     const int q_retry = RETRY ? P.power_iters + P.extra_power[job] : 0;
 #define TP_SKETCH_Q (RETRY ? q_retry : P.power_iters)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool global_bufs = WIDE && P.gscratch != nullptr;  // only the last class (wide)
+    const bool global_bufs = WIDE && P.gscratch != nullptr;  // the last class and retries
     if (l <= 0 || l >= min(n1, n2) || l > (WIDE ? kLMax : kNarrowL) ||
         (global_bufs ? (sketch_small_need(n1, n2, l) > (size_t)P.smem_bytes ||
                         (int64_t)3 * nm * l > P.gstride)
@@ -1182,27 +1182,35 @@ cudaError_t launch_proposer(const float* feat, const SvdJob* jobs, int njobs, in
 
 // Between sketch rounds: every slice that failed (flag 1 or 3) and has min(n1, n2) >=
 // min_dim (its Jacobi SVD would cost much more than another sketch) is queued for another
-// attempt -- with two more power iterations if its sketch reached below tau (flag 1), or 4
-// columns wider if the rank was underestimated (flag 3) and the wider sketch fits `smem`;
-// it is marked 2 (pending).  Any other failed slice is marked 4 (left to the Jacobi path).
+// attempt -- with two more power iterations if its sketch reached below tau (flag 1), or half
+// again as wide (at least 4 columns more, at most kLMax) if the rank was underestimated
+// (flag 3) -- when the attempt fits the retry launch (shared memory `smem`, and with gstride > 0
+// the tall buffers in a global scratch slot of gstride complex values); it is marked 2
+// (pending).  Any other failed slice is marked 4 (left to the Jacobi path).
 __global__ void __launch_bounds__(1024) sketch_collect_kernel(const SvdJob* __restrict__ jobs,
                                                               int n, int32_t* __restrict__ flag,
                                                               int32_t* __restrict__ ell,
                                                               int32_t* __restrict__ extra,
-                                                              int min_dim, int smem,
+                                                              int min_dim, int smem, int64_t gstride,
                                                               int32_t* list, int32_t* len) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const int f = flag[j];
         if (f != 1 && f != 3) continue;
         const int n1 = jobs[j].n1, n2 = jobs[j].n2, l = ell[j];
+        const int64_t nm = max(n1, n2);
+        auto fits = [&](int lw) {
+            return gstride > 0 ? (sketch_small_need(n1, n2, lw) <= (size_t)smem &&
+                                  3 * nm * lw <= gstride)
+                               : sketch_smem_need(n1, n2, lw) <= (size_t)smem;
+        };
         bool again = min(n1, n2) >= min_dim;
         if (again && f == 1) {
-            again = sketch_smem_need(n1, n2, l) <= (size_t)smem;  // the retry launch's class
+            again = fits(l);
             if (again) extra[j] += 2;
         } else if (again) {
-            again = l + 4 < min(n1, n2) && l + 4 <= kLMax &&
-                    sketch_smem_need(n1, n2, l + 4) <= (size_t)smem;
-            if (again) ell[j] = l + 4;
+            const int lw = min(min(kLMax, min(n1, n2) - 1), max(l + 4, l + l / 2));
+            again = lw > l && fits(lw);
+            if (again) ell[j] = lw;
         }
         flag[j] = again ? 2 : 4;
         if (again) list[atomicAdd(len, 1)] = j;
@@ -1210,10 +1218,11 @@ __global__ void __launch_bounds__(1024) sketch_collect_kernel(const SvdJob* __re
 }
 
 cudaError_t launch_sketch_collect(const SvdJob* jobs, int n, int32_t* flag, int32_t* ell,
-                                  int32_t* extra, int min_dim, int smem, int32_t* list,
-                                  int32_t* len, cudaStream_t s) {
+                                  int32_t* extra, int min_dim, int smem, int64_t gstride,
+                                  int32_t* list, int32_t* len, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    sketch_collect_kernel<<<1, 1024, 0, s>>>(jobs, n, flag, ell, extra, min_dim, smem, list, len);
+    sketch_collect_kernel<<<1, 1024, 0, s>>>(jobs, n, flag, ell, extra, min_dim, smem, gstride, list,
+                                             len);
     return cudaGetLastError();
 }
 
