@@ -858,7 +858,41 @@ def tprod_leg(args, tp, synth, device):
                    "roofline": {"bound": "hbm", "achieved": nb / (ms / 1e3) / 1e9,
                                 "peak": HBM_PEAK_GBS, "unit": "GB/s",
                                 "frac": nb / (ms / 1e3) / 1e9 / HBM_PEAK_GBS}}
+    del AT
+    out["dft_long"] = dft_long_leg(tp, device)
     return out
+
+
+def dft_long_leg(tp, device, n3s=(61, 64, 127, 128, 251, 256), tubes=1 << 20):
+    """The tube DFTs alone at long tube lengths (the mixed call stream's n3 reaches 256): a
+    t-product A * B with A tubes x 1 x n3 and B 1 x 1 x n3, timed by the library's stage events
+    around its forward DFT (A and the one tube of B) and its inverse DFT (C); bytes are one
+    read of the real tubes and one write of the half spectrum (or the reverse)."""
+    import torch
+    res = {}
+    for n3 in n3s:
+        A = tp.empty(tubes, 1, n3, device)
+        A.normal_()
+        B = tp.empty(1, 1, n3, device)
+        B.normal_()
+        C = tp.empty(tubes, 1, n3, device)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        for e in ev:
+            e.record()
+        o = tp.options(stage_events=ev)
+        fw, iv = [], []
+        for rep in range(4):
+            tp.tprod(A, B, out=C, opts=o)
+            torch.cuda.synchronize()
+            if rep:
+                fw.append(ev[0].elapsed_time(ev[1]))
+                iv.append(ev[4].elapsed_time(ev[5]))
+        nb = tubes * (4.0 * n3 + 8.0 * (n3 // 2 + 1))
+        res[str(n3)] = {"fwd_gbs": nb / (min(fw) / 1e3) / 1e9, "inv_gbs": nb / (min(iv) / 1e3) / 1e9,
+                        "fwd_ms": min(fw), "inv_ms": min(iv)}
+        del A, B, C
+    return {"workload": f"{tubes} tubes per length, N(0,1); stage events include the job-table "
+                        "upload (a few microseconds)", "lengths": res}
 
 
 def factor_leg(args, tp, synth, device):

@@ -122,7 +122,8 @@ typedef struct tp_options {
  *   width k + 4 with one power iteration and a small Jacobi SVD gives the top singular
  *   triplets; the slice is accepted only if the smallest computed singular value is below
  *   tau, the kept triplets' residuals ||A r - sigma u|| (times their weight (sigma - tau)/sigma
- *   in the result) are below 1e-5 sigma_max and the
+ *   in the result) are below 1e-5 sigma_max (times sqrt(max(n1, n2) / 100) above 100 rows, the
+ *   growth of the product's FP32 rounding) and the
  *   deflated matrix's norm is estimated below 0.8 tau. A slice with min(n1, n2) >= 96 that
  *   fails is sketched again (up to four times) with two more power iterations, or half again
  *   as wide (at least 4 columns more, at most 48) if the rank was underestimated; every other

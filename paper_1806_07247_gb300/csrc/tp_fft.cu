@@ -106,17 +106,37 @@ __global__ void __launch_bounds__(kFftThreads) rfft_kernel(const FftJob* __restr
 #pragma unroll
             for (int i = 0; i < 4; ++i) ar[q][i] = ai[q][i] = 0.f;
         }
-        for (int t = 0; t < n3; ++t) {
-            float4 xv = xs4[t * G + g];
+        // samples t and n3 - t paired: x_t e^{-i th k t} + x_{n3-t} e^{+i th k t}
+        //   = (x_t + x_{n3-t}) cos(th k t) - i (x_t - x_{n3-t}) sin(th k t)
+        {
+            const float4 x0 = xs4[g];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                float2 w = tw[e[q]];
+                ar[q][0] = x0.x; ar[q][1] = x0.y; ar[q][2] = x0.z; ar[q][3] = x0.w;
+            }
+            if ((n3 & 1) == 0) {  // x_{n3/2} e^{-i pi k} = (-1)^k x_{n3/2}
+                const float4 xm = xs4[(n3 / 2) * G + g];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float sg = (k[q] & 1) ? -1.f : 1.f;
+                    ar[q][0] = fmaf(sg, xm.x, ar[q][0]); ar[q][1] = fmaf(sg, xm.y, ar[q][1]);
+                    ar[q][2] = fmaf(sg, xm.z, ar[q][2]); ar[q][3] = fmaf(sg, xm.w, ar[q][3]);
+                }
+            }
+        }
+        for (int t = 1; 2 * t < n3; ++t) {
+            const float4 a = xs4[t * G + g], b = xs4[(n3 - t) * G + g];
+            const float4 sv = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+            const float4 dv = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
                 e[q] += k[q];
                 if (e[q] >= n3) e[q] -= n3;
-                ar[q][0] = fmaf(xv.x, w.x, ar[q][0]); ai[q][0] = fmaf(-xv.x, w.y, ai[q][0]);
-                ar[q][1] = fmaf(xv.y, w.x, ar[q][1]); ai[q][1] = fmaf(-xv.y, w.y, ai[q][1]);
-                ar[q][2] = fmaf(xv.z, w.x, ar[q][2]); ai[q][2] = fmaf(-xv.z, w.y, ai[q][2]);
-                ar[q][3] = fmaf(xv.w, w.x, ar[q][3]); ai[q][3] = fmaf(-xv.w, w.y, ai[q][3]);
+                const float2 w = tw[e[q]];
+                ar[q][0] = fmaf(sv.x, w.x, ar[q][0]); ai[q][0] = fmaf(-dv.x, w.y, ai[q][0]);
+                ar[q][1] = fmaf(sv.y, w.x, ar[q][1]); ai[q][1] = fmaf(-dv.y, w.y, ai[q][1]);
+                ar[q][2] = fmaf(sv.z, w.x, ar[q][2]); ai[q][2] = fmaf(-dv.z, w.y, ai[q][2]);
+                ar[q][3] = fmaf(sv.w, w.x, ar[q][3]); ai[q][3] = fmaf(-dv.w, w.y, ai[q][3]);
             }
         }
 #pragma unroll
@@ -190,19 +210,22 @@ __global__ void __launch_bounds__(kFftThreads) irfft_kernel(const FftJob* __rest
     }
     __syncthreads();
 
+    // outputs t and n3 - t paired: with the weighted X_k = Xr + i Xi,
+    //   x_t = sum_k (Xr cos - Xi sin),  x_{n3-t} = sum_k (Xr cos + Xi sin)   (angle th k t)
     const int g = tid % G, f = tid / G, F = kFftThreads / G;
     const int64_t pg = p0 + 4 * g;
     float* xout = const_cast<float*>(J.x);
-    for (int base = f; base < n3; base += 4 * F) {
+    const int half = n3 / 2;  // t = 0..half produce every output
+    for (int base = f; base <= half; base += 4 * F) {
         int tt[4], e[4];
-        float acc[4][4];
+        float ca[4][4], sb[4][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             int tq = base + q * F;
-            tt[q] = (tq < n3) ? tq : 0;
+            tt[q] = (tq <= half) ? tq : 0;
             e[q] = 0;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[q][i] = 0.f;
+            for (int i = 0; i < 4; ++i) ca[q][i] = sb[q][i] = 0.f;
         }
         for (int k = 0; k < h; ++k) {
             const float4* row = reinterpret_cast<const float4*>(Xs + (size_t)k * TP + 4 * g);
@@ -212,24 +235,32 @@ __global__ void __launch_bounds__(kFftThreads) irfft_kernel(const FftJob* __rest
                 float2 w = tw[e[q]];
                 e[q] += tt[q];
                 if (e[q] >= n3) e[q] -= n3;
-                acc[q][0] = fmaf(a.x, w.x, fmaf(-a.y, w.y, acc[q][0]));
-                acc[q][1] = fmaf(a.z, w.x, fmaf(-a.w, w.y, acc[q][1]));
-                acc[q][2] = fmaf(b.x, w.x, fmaf(-b.y, w.y, acc[q][2]));
-                acc[q][3] = fmaf(b.z, w.x, fmaf(-b.w, w.y, acc[q][3]));
+                ca[q][0] = fmaf(a.x, w.x, ca[q][0]); sb[q][0] = fmaf(a.y, w.y, sb[q][0]);
+                ca[q][1] = fmaf(a.z, w.x, ca[q][1]); sb[q][1] = fmaf(a.w, w.y, sb[q][1]);
+                ca[q][2] = fmaf(b.x, w.x, ca[q][2]); sb[q][2] = fmaf(b.y, w.y, sb[q][2]);
+                ca[q][3] = fmaf(b.z, w.x, ca[q][3]); sb[q][3] = fmaf(b.w, w.y, sb[q][3]);
             }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            int tq = base + q * F;
-            if (tq >= n3) continue;
-            float* dst = xout + pg + P * tq;
-            if (VEC) {
-                if (pg < P)
-                    *reinterpret_cast<float4*>(dst) = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
-            } else {
+            const int tq = base + q * F;
+            if (tq > half) continue;
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (pg + i < P) dst[i] = acc[q][i];
+            for (int m = 0; m < 2; ++m) {  // m = 0: t, m = 1: n3 - t
+                const int tout = m == 0 ? tq : n3 - tq;
+                if (m == 1 && (tq == 0 || 2 * tq == n3)) continue;
+                const float sg = m == 0 ? -1.f : 1.f;
+                float o[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) o[i] = fmaf(sg, sb[q][i], ca[q][i]);
+                float* dst = xout + pg + P * tout;
+                if (VEC) {
+                    if (pg < P) *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (pg + i < P) dst[i] = o[i];
+                }
             }
         }
     }
