@@ -556,69 +556,6 @@ __device__ __forceinline__ void zv_wide(float2* bz, const float2* V, int n2, int
     }
 }
 
-// Up to two sweeps of one-sided Jacobi on the columns of D = Z V (n2 x l, shared or global),
-// with V (l x l, shared) accumulating the same rotations (D = Z V stays true).  D's columns are
-// orthogonal up to what the Gram eigensolver resolved: forming Z^H Z squares the condition
-// number, so when sigma_max / sigma_l is large the small columns keep components of the large
-// ones, which inflate their norms.  Rotating the columns themselves removes that leakage.  A
-// warp per column pair of a round (lanes over the rows); the sweep count is small because the
-// columns start nearly orthogonal.
-__device__ void refine_onesided(float2* D, float2* V, int n2, int l) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (l < 2) return;
-    const int Np = l + (l & 1), P = Np / 2;
-    const float tol = 8.f * 1.1920928955078125e-07f, tol2 = tol * tol;
-    for (int sweep = 0; sweep < 2; ++sweep) {
-        int rotated = 0;
-        for (int r = 0; r < Np - 1; ++r) {
-            for (int pi = warp; pi < P; pi += kTS / 32) {  // uniform over each warp
-                int pa, pb;
-                if (pi == 0) { pa = Np - 1; pb = r; }
-                else { pa = (r + pi) % (Np - 1); pb = (r - pi + Np - 1) % (Np - 1); }
-                const int p = min(pa, pb), q = max(pa, pb);
-                if (q >= l) continue;  // the odd-l dummy
-                float2* dp = D + (size_t)n2 * p;
-                float2* dq = D + (size_t)n2 * q;
-                float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
-                for (int e = lane; e < n2; e += 32) {
-                    const float2 a = dp[e], b = dq[e];
-                    al = fmaf(a.x, a.x, fmaf(a.y, a.y, al));
-                    be = fmaf(b.x, b.x, fmaf(b.y, b.y, be));
-                    gr = fmaf(a.x, b.x, fmaf(a.y, b.y, gr));  // conj(a) b
-                    gi = fmaf(a.x, b.y, fmaf(-a.y, b.x, gi));
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                gr = warp_sum(gr);
-                gi = warp_sum(gi);
-                const float ag2 = fmaf(gr, gr, gi * gi);
-                if (!(ag2 > (tol2 * al) * be) || !(ag2 > 0.f)) continue;
-                float c, sr, si;  // p <- c p - conj(w) q,  q <- w p + c q,  w = sr + i si
-                jacobi_rotation(al, be, gr, gi, ag2, c, sr, si);
-                rotated = 1;
-                for (int e = lane; e < n2; e += 32) {
-                    const float2 a = dp[e], b = dq[e];
-                    dp[e] = make_float2(fmaf(c, a.x, -fmaf(sr, b.x, si * b.y)),
-                                        fmaf(c, a.y, -fmaf(sr, b.y, -si * b.x)));
-                    dq[e] = make_float2(fmaf(sr, a.x, fmaf(-si, a.y, c * b.x)),
-                                        fmaf(sr, a.y, fmaf(si, a.x, c * b.y)));
-                }
-                float2* vp = V + (size_t)l * p;
-                float2* vq = V + (size_t)l * q;
-                for (int e = lane; e < l; e += 32) {
-                    const float2 a = vp[e], b = vq[e];
-                    vp[e] = make_float2(fmaf(c, a.x, -fmaf(sr, b.x, si * b.y)),
-                                        fmaf(c, a.y, -fmaf(sr, b.y, -si * b.x)));
-                    vq[e] = make_float2(fmaf(sr, a.x, fmaf(-si, a.y, c * b.x)),
-                                        fmaf(sr, a.y, fmaf(si, a.x, c * b.y)));
-                }
-            }
-            __syncthreads();
-        }
-        if (!__syncthreads_or(rotated)) break;
-    }
-}
-
 // Shared state of one CTA of the sketch kernel besides the dynamic buffers.
 struct SketchShared {
     int flag, item;
@@ -731,7 +668,6 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
         zv_wide(bz, V, n2, l);
         __syncthreads();
     }
-    if (ok) refine_onesided(bz, V, n2, l);
     float smax = 0.f;
     int k = 0;
 
