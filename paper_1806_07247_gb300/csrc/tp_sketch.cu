@@ -8,7 +8,8 @@
 //      log min(n1, n2) -- and predicts k = #{sigma > tau}; the sketch width is l = k + 4;
 //   2. randomized range finder: Y = A Omega (Omega n2 x l, random +-1 / (+-1 +- i)/sqrt 2
 //      from a counter-based hash), q power iterations (Z = A^H Q, Y = A Z), each followed by
-//      shifted CholeskyQR3 orthonormalisation, Q = orth(Y);
+//      shifted CholeskyQR3 orthonormalisation, Q = orth(Y) (rank revealing: columns that
+//      are dependent to working precision become zero columns);
 //   3. small SVD: Z = A^H Q (n2 x l) = B^H; one-sided Jacobi over the whole CTA turns Z into
 //      D = Z V with orthogonal columns, sigma_j = ||d_j||, so
 //      A ~ Q Z^H = (Q V) diag(sigma) (D / sigma)^H;
@@ -192,8 +193,13 @@ __device__ void gram(const float2* Y, int n, int l, float2* G) {
 // once.  G is overwritten by M = (G + shift I) C, kept current column by column, so that
 // every step needs only dot products of length l: warp 0 normalises c_j (and m_j), then one
 // half-warp per later column k forms h = m_j^H c_k and updates c_k -= h c_j, m_k -= h m_j.
-// Returns false (uniformly) if a norm is not positive (breakdown).
-__device__ bool chol_inv_narrow(float2* G, float2* C, int l, float shift, int* s_flag) {
+// Rank revealing: a column whose squared norm after the projections, c_j^H m_j, is at most
+// drop_tol times its squared norm before them (G_jj + shift) lies in the span of the earlier
+// columns to working precision; it is dropped (c_j = m_j = 0), so Y C gets a zero column
+// there instead of a normalised rounding error.  Returns false (uniformly) only if a norm is
+// not a number.
+__device__ bool chol_inv_narrow(float2* G, float2* C, int l, float shift, float drop_tol,
+                                int* s_flag) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int t = tid; t < l * l; t += kTS) {
         const bool d = (t % l) == (t / l);
@@ -201,17 +207,20 @@ __device__ bool chol_inv_narrow(float2* G, float2* C, int l, float shift, int* s
         if (d) G[t].x += shift;
     }
     __syncthreads();
+    // squared column norms before the projections (warp 0, lane j: column j)
+    const float dreg = (warp == 0 && lane < l) ? G[lane + l * lane].x : 0.f;
     const int hw = tid >> 4, hl = tid & 15;  // 16 half-warps; rows hl and hl + 16
     for (int j = 0; j < l; ++j) {
         if (warp == 0) {
             const float2 cj = lane <= j ? C[lane + l * j] : make_float2(0.f, 0.f);
             const float2 mj = lane < l ? G[lane + l * j] : make_float2(0.f, 0.f);
             const float p = warp_sum(fmaf(cj.x, mj.x, cj.y * mj.y));  // c_j^H m_j (real)
-            const bool ok = p > 0.f;
-            const float inv = ok ? 1.f / sqrtf(p) : 0.f;
+            const float dj = __shfl_sync(0xffffffffu, dreg, j);
+            const bool keep = p > drop_tol * dj;
+            const float inv = keep ? 1.f / sqrtf(p) : 0.f;
             if (lane <= j) C[lane + l * j] = make_float2(cj.x * inv, cj.y * inv);
             if (lane < l) G[lane + l * j] = make_float2(mj.x * inv, mj.y * inv);
-            if (lane == 0) *s_flag = ok ? 0 : 1;
+            if (lane == 0) *s_flag = (p == p) ? 0 : 1;
         }
         __syncthreads();
         if (*s_flag) return false;
@@ -259,7 +268,8 @@ __device__ bool chol_inv_narrow(float2* G, float2* C, int l, float shift, int* s
     return true;
 }
 
-__device__ bool chol_inv_wide(float2* G, float2* C, int l, float shift, int* s_flag) {
+__device__ bool chol_inv_wide(float2* G, float2* C, int l, float shift, float drop_tol,
+                              int* s_flag) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int t = tid; t < l * l; t += kTS) {
         const bool d = (t % l) == (t / l);
@@ -267,6 +277,9 @@ __device__ bool chol_inv_wide(float2* G, float2* C, int l, float shift, int* s_f
         if (d) G[t].x += shift;
     }
     __syncthreads();
+    static_assert(kLMax <= 64, "two squared norms per lane");
+    const float dreg0 = (warp == 0 && lane < l) ? G[lane + l * lane].x : 0.f;
+    const float dreg1 = (warp == 0 && lane + 32 < l) ? G[lane + 32 + l * (lane + 32)].x : 0.f;
     constexpr int kRowSets = (kLMax + 15) / 16;  // rows hl + 16 h of a half-warp, h < kRowSets
     const int hw = tid >> 4, hl = tid & 15;       // 16 half-warps
     for (int j = 0; j < l; ++j) {
@@ -277,14 +290,16 @@ __device__ bool chol_inv_wide(float2* G, float2* C, int l, float shift, int* s_f
                 p = fmaf(cj.x, mj.x, fmaf(cj.y, mj.y, p));  // c_j^H m_j (real)
             }
             p = warp_sum(p);
-            const bool ok = p > 0.f;
-            const float inv = ok ? 1.f / sqrtf(p) : 0.f;
+            const float d0 = __shfl_sync(0xffffffffu, dreg0, j & 31);
+            const float d1 = __shfl_sync(0xffffffffu, dreg1, j & 31);
+            const bool keep = p > drop_tol * (j < 32 ? d0 : d1);
+            const float inv = keep ? 1.f / sqrtf(p) : 0.f;
             for (int m = lane; m < l; m += 32) {
                 if (m <= j) { C[m + l * j].x *= inv; C[m + l * j].y *= inv; }
                 G[m + l * j].x *= inv;
                 G[m + l * j].y *= inv;
             }
-            if (lane == 0) *s_flag = ok ? 0 : 1;
+            if (lane == 0) *s_flag = (p == p) ? 0 : 1;
         }
         __syncthreads();
         if (*s_flag) return false;
@@ -335,9 +350,10 @@ __device__ bool chol_inv_wide(float2* G, float2* C, int l, float shift, int* s_f
 // The Cholesky inverse above: rows of a column in one lane of warp 0 and of each half-warp
 // (WIDE = false, l <= 32), or in several (WIDE = true, l <= kLMax).
 template <bool WIDE>
-__device__ __forceinline__ bool chol_inv(float2* G, float2* C, int l, float shift, int* s_flag) {
-    if constexpr (WIDE) return chol_inv_wide(G, C, l, shift, s_flag);
-    else return chol_inv_narrow(G, C, l, shift, s_flag);
+__device__ __forceinline__ bool chol_inv(float2* G, float2* C, int l, float shift, float drop_tol,
+                                         int* s_flag) {
+    if constexpr (WIDE) return chol_inv_wide(G, C, l, shift, drop_tol, s_flag);
+    else return chol_inv_narrow(G, C, l, shift, drop_tol, s_flag);
 }
 
 // Yout (n x l) = Yin C for an upper triangular C (l x l); items of one row and 4 columns.
@@ -371,8 +387,15 @@ __device__ void mult_upper(const float2* Yin, const float2* C, float2* Yout, int
 // Y (n x l, ld n) are orthonormalised by three passes of Y <- Y R^-1 with R^H R the Cholesky
 // factorisation of the Gram matrix, the first pass shifted by 11 (n l + l (l + 1)) u ||Y||_F^2
 // (u = 2^-24) so that it cannot break down.  The passes alternate between Y and the scratch
-// S (both n x l); returns the buffer that holds the result, or nullptr if a pass still broke
-// down (the slice then goes to the Jacobi path).
+// S (both n x l); returns the buffer that holds the result, or nullptr if a norm was not a
+// number (the slice then goes to the Jacobi path).
+// When Y has fewer than l numerically independent columns (a sketch wider than the slice's
+// rank, whose remaining singular values sit below FP32 resolution relative to the largest),
+// a plain pass finds columns that lie in the span of the earlier ones to within
+// 8 n u of their norm (the rounding of an n-term Gram entry) and drops them: the result
+// has orthonormal columns and zero columns, and the zero columns stay zero through the
+// power iterations and come out as singular values 0 (not kept).  Check (c) still rejects
+// the sketch if a dropped direction carried a singular value above tau.
 template <bool WIDE>
 __device__ float2* orth3(float2* Y, float2* S, int n, int l, float2* G, float2* C, int* s_flag,
                          int passes = 3) {
@@ -386,7 +409,8 @@ __device__ float2* orth3(float2* Y, float2* S, int n, int l, float2* G, float2* 
             for (int j = 0; j < l; ++j) tr += G[j + l * j].x;
             shift = 11.f * (float)(n * l + l * (l + 1)) * 5.9604645e-08f * tr;
         }
-        if (!chol_inv<WIDE>(G, C, l, shift, s_flag)) return nullptr;
+        if (!chol_inv<WIDE>(G, C, l, shift, 8.f * (float)n * 5.9604645e-08f, s_flag))
+            return nullptr;
         mult_upper(cur, C, oth, n, l);
         float2* t = cur;
         cur = oth;
