@@ -339,6 +339,7 @@ struct FftBatch {
     int max_n3 = 1;
     int uniform_n3 = -1;  // common n3 of all jobs, 0 once two differ
     bool vec = true;
+    bool planes = false;  // the jobs write BF16x3 operand planes (all of them, add_planes)
     void add(const float* x, float2* X, int64_t P, int n3) {
         if (P <= 0 || n3 <= 0) return;
         FftJob j{};
@@ -351,6 +352,26 @@ struct FftBatch {
         max_n3 = std::max(max_n3, n3);
         uniform_n3 = (uniform_n3 == -1 || uniform_n3 == n3) ? n3 : 0;
         vec = vec && (P % 4 == 0) && aligned16(x) && aligned16(X);
+    }
+    // Forward DFT whose output is the BF16x3 operand planes (kind PLANE_LEFT / PLANE_RIGHT,
+    // rows M or K) instead of a complex spectrum; n3 must satisfy fft_writes_planes.
+    void add_planes(const float* x, int64_t P, int n3, int kind, int rows, int64_t pitch,
+                    uint16_t* hi, uint16_t* lo) {
+        if (P <= 0 || n3 <= 0) return;
+        FftJob j{};
+        j.x = x;
+        j.P = P;
+        j.n3 = n3;
+        j.plane_kind = kind;
+        j.plane_rows = rows;
+        j.plane_pitch = pitch;
+        j.plane_hi = hi;
+        j.plane_lo = lo;
+        jobs.push_back(j);
+        planes = true;
+        max_n3 = std::max(max_n3, n3);
+        uniform_n3 = (uniform_n3 == -1 || uniform_n3 == n3) ? n3 : 0;
+        vec = vec && (P % 4 == 0) && aligned16(x);
     }
     tp_status launch(Workspace& ws, bool inverse, cudaStream_t s) {
         if (jobs.empty()) return TP_OK;
@@ -384,7 +405,8 @@ struct FftBatch {
             const int cls = small ? fft_small_class(jobs[a].n3) : -1;
             cudaError_t e =
                 inverse ? launch_irfft(d + a, (int)n, (int)group_tiles[g], max_n3, uniform_n3, vec, s, cls)
-                        : launch_rfft(d + a, (int)n, (int)group_tiles[g], max_n3, uniform_n3, vec, s, cls);
+                        : launch_rfft(d + a, (int)n, (int)group_tiles[g], max_n3, uniform_n3, vec, s, cls,
+                                      planes);
             if (e != cudaSuccess) return from_cuda(e);
         }
         return TP_OK;
@@ -843,30 +865,50 @@ tp_status tp_tprod(const float* A, const float* B, float* C, int64_t n1, int64_t
     const int h = free_slices((int)n3);
     const int64_t PA = n1 * n2, PB = n2 * l, PC = n1 * l;
     const bool tc = o.precision != TP_PREC_FP32;
+    // BF16x3: the operands go to the tensor cores as BF16 hi/lo planes; for power-of-two
+    // n3 <= 64 the forward DFT writes them itself and no complex spectrum of A or B exists
+    const bool bf = o.precision == TP_PREC_BF16X3;
+    const bool direct_planes = bf && fft_writes_planes((int)n3);
+    const int64_t la = bf ? bf16_left_plane_elems((int)n1, (int)n2, h) : 0;
+    const int64_t lb = bf ? bf16_right_plane_elems((int)l, (int)n2, h) : 0;
     const int64_t plane_bytes =
-        tc ? cgemm_tc_plane_bytes((int)n1, (int)l, (int)n2, h, o.precision) : 0;
+        bf ? 2 * (int64_t)sizeof(uint16_t) * (la + lb)
+           : tc ? cgemm_tc_plane_bytes((int)n1, (int)l, (int)n2, h, o.precision) : 0;
+    const int64_t spec_a = direct_planes ? 0 : PA * h, spec_b = direct_planes ? 0 : PB * h;
     Workspace ws(s);
-    TP_TRY(ws.reserve(cbytes(PA * h) + cbytes(PB * h) + cbytes(PC * h) +
+    TP_TRY(ws.reserve(cbytes(spec_a) + cbytes(spec_b) + cbytes(PC * h) +
                       2 * Workspace::round(sizeof(FftJob) * 3) + Workspace::round(4) +
                       Workspace::round((size_t)plane_bytes)));
-    float2* Ab = ws.take<float2>(PA * h);
-    float2* Bb = ws.take<float2>(PB * h);
+    float2* Ab = spec_a ? ws.take<float2>(spec_a) : nullptr;
+    float2* Bb = spec_b ? ws.take<float2>(spec_b) : nullptr;
     float2* Cb = ws.take<float2>(PC * h);
     uint32_t* d_err = ws.take<uint32_t>(1);
     void* planes = tc ? static_cast<void*>(ws.take<char>((size_t)plane_bytes)) : nullptr;
     TP_TRY(ws.check());
     if (tc) TP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
     FftBatch fwd, inv;
-    fwd.add(A, Ab, PA, (int)n3);
-    fwd.add(B, Bb, PB, (int)n3);
+    if (direct_planes) {
+        uint16_t* pl = static_cast<uint16_t*>(planes);
+        fwd.add_planes(A, PA, (int)n3, PLANE_LEFT, (int)n1, bf16_plane_pitch((int)n1), pl, pl + la);
+        fwd.add_planes(B, PB, (int)n3, PLANE_RIGHT, (int)n2, bf16_plane_pitch((int)n2),
+                       pl + 2 * la, pl + 2 * la + lb);
+    } else {
+        fwd.add(A, Ab, PA, (int)n3);
+        fwd.add(B, Bb, PB, (int)n3);
+    }
     TP_TRY(o.mark(0, s));
     TP_TRY(fwd.launch(ws, false, s));
     TP_TRY(o.marks(1, 3, s));
     TP_TRY(ws.check());
-    if (tc)
+    if (bf) {
+        if (!direct_planes)
+            TP_CUDA(bf16_planes_from_spectrum(Ab, Bb, (int)n1, (int)l, (int)n2, h, planes, s));
+        TP_CUDA(launch_cgemm_bf16x3(planes, Cb, (int)n1, (int)l, (int)n2, h, (int)n3, d_err, s));
+    } else if (tc) {
         TP_CUDA(launch_cgemm_tc(Ab, Bb, Cb, (int)n1, (int)l, (int)n2, h, o.precision, planes, d_err, s));
-    else
+    } else {
         TP_CUDA(launch_cgemm_fp32(Ab, Bb, Cb, (int)n1, (int)l, (int)n2, PA, PB, PC, h, s));
+    }
     TP_TRY(o.mark(4, s));
     inv.add(C, Cb, PC, (int)n3);
     TP_TRY(inv.launch(ws, true, s));

@@ -16,13 +16,16 @@
 // This direct form serves n3 > 64; a launch whose tubes all have the same power-of-two
 // n3 <= 64 uses the register FFT kernels further below, and any other launch with n3 <= 64
 // the register-resident mixed-radix FFT kernels after them (a direct paired DFT for the odd
-// prime lengths 37..61).
+// prime lengths 37..61).  The power-of-two kernels can also write the forward spectrum
+// straight into the BF16 hi/lo operand planes of the tensor-core slice GEMM
+// (FftJob::plane_kind), so that the t-product's BF16x3 path needs no separate split pass.
 #include <math.h>
 
 #include <mutex>
 #include <vector>
 
 #include "tp_internal.cuh"
+#include "tp_planes.cuh"
 
 namespace tp {
 
@@ -49,11 +52,20 @@ size_t fft_smem_bytes(int max_n3, bool inverse) {
     return (size_t)rows * tp * elem + (size_t)max_n3 * sizeof(float2);
 }
 
+// The job of CTA b: the last job whose tile_begin <= b (tile_begin increases with the job
+// index, job 0 starts at 0).  Each warp searches with 32 probes per round (two rounds up to
+// 1,024 jobs) instead of a binary search's chain of dependent loads; every lane of the warp
+// must call it.
 __device__ inline int find_job(const FftJob* jobs, int njobs, int b) {
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].tile_begin <= b) lo = mid; else hi = mid - 1;
+    const int lane = threadIdx.x & 31;
+    int lo = 0, end = njobs;
+    while (end - lo > 1) {
+        const int step = (end - lo + 31) / 32;
+        const int j = lo + lane * step;
+        const bool le = j < end && __ldg(&jobs[j].tile_begin) <= b;  // true in lane 0
+        const unsigned m = __ballot_sync(0xffffffffu, le);
+        lo += (31 - __clz(m)) * step;
+        end = min(end, lo + step);
     }
     return lo;
 }
@@ -318,8 +330,11 @@ __device__ __forceinline__ void cfft_bitrev_regs(float2 (&z)[N]) {
     }
 }
 
-template <int N3>
-__global__ void __launch_bounds__(256) rfft_reg_kernel(const FftJob* __restrict__ jobs, int njobs) {
+// PLANES: the jobs write the BF16x3 operand planes instead of X (FftJob::plane_kind); that
+// instantiation is held to 128 registers so that two CTAs still fit on an SM.
+template <int N3, bool PLANES>
+__global__ void __launch_bounds__(256, PLANES ? 2 : 1)
+    rfft_reg_kernel(const FftJob* __restrict__ jobs, int njobs) {
     constexpr int N = N3 / 2;
     const FftJob J = jobs[find_job(jobs, njobs, blockIdx.x)];
     const int64_t p = (int64_t)(blockIdx.x - J.tile_begin) * 256 + threadIdx.x;
@@ -332,6 +347,7 @@ __global__ void __launch_bounds__(256) rfft_reg_kernel(const FftJob* __restrict_
         z[bit_reverse(t, B)] =
             make_float2(__ldg(J.x + p + P * (2 * t)), __ldg(J.x + p + P * (2 * t + 1)));
     cfft_bitrev_regs<N, false>(z);
+    const PlaneCursor pc = PLANES ? plane_cursor(J, p) : PlaneCursor{};
 #pragma unroll
     for (int k = 0; k <= N; ++k) {
         const float2 zk = z[k % N], zc = z[(N - k) % N];
@@ -342,7 +358,8 @@ __global__ void __launch_bounds__(256) rfft_reg_kernel(const FftJob* __restrict_
         if (k == N) w = make_float2(-1.f, 0.f);
         float2 X = make_float2(e.x + (w.x * o.x - w.y * o.y), e.y + (w.x * o.y + w.y * o.x));
         if (k == 0 || k == N) X.y = 0.f;
-        J.X[p + P * k] = X;
+        if constexpr (PLANES) store_plane_value(J, pc, k, X);
+        else J.X[p + P * k] = X;
     }
 }
 
@@ -385,77 +402,107 @@ bool reg_fft_size(int n3) { return n3 >= 2 && n3 <= 64 && (n3 & (n3 - 1)) == 0; 
 // Odd prime n3 in 37..61 (launches whose tubes differ in n3, see the mixed-radix kernels
 // below for the other lengths): one thread per tube, the tube in registers, the real DFT by
 // its definition.  Samples t and n3 - t are
-// paired: Re X[k] = x0 + sum_t (x_t + x_{n3-t}) cos(2 pi k t / n3) (+ (-1)^k x_{n3/2}),
+// paired: Re X[k] = x0 + sum_t (x_t + x_{n3-t}) cos(2 pi k t / n3),
 // Im X[k] = -sum_t (x_t - x_{n3-t}) sin(2 pi k t / n3), and the inverse pairs the same way.
+// The twiddles come from a row table: row k of length n3 holds exp(2 pi i k t / n3) for
+// t = 1..H (H = (n3 - 1) / 2, padded to an even count), so the unrolled inner loop reads them
+// two at a time (16-byte loads, the same address across the warp) at fixed offsets from one
+// row pointer and needs no index arithmetic.  The table is symmetric in k and t, so the
+// inverse reads row t for its sum over k.
 // A CTA's tubes belong to one job, so the switch on n3 is uniform.
 // ---------------------------------------------------------------------------------------
 constexpr int kSmallN3 = 64;
 __constant__ float2 c_twall[kSmallN3 * (kSmallN3 + 1) / 2];  // length n at n (n - 1) / 2
 
+__host__ __device__ constexpr int prime_row_len(int n) { return ((n - 1) / 2 + 1) & ~1; }
+// Offset of the rows of prime length n (37 <= n <= 61) in g_prime_rows; -1 for other n.
+__host__ __device__ constexpr int prime_rows_offset(int n) {
+    constexpr int primes[7] = {37, 41, 43, 47, 53, 59, 61};
+    int off = 0;
+    for (int i = 0; i < 7; ++i) {
+        if (primes[i] == n) return off;
+        off += (primes[i] / 2 + 1) * prime_row_len(primes[i]);
+    }
+    return -1;
+}
+constexpr int kPrimeRowsTotal = prime_rows_offset(61) + 31 * prime_row_len(61);
+__device__ __align__(16) float2 g_prime_rows[kPrimeRowsTotal];
+
 template <int N>
 __device__ __forceinline__ void rdft_small(const float* __restrict__ x, int64_t P, float2* X) {
     constexpr int H = (N - 1) / 2;  // pairs (t, N - t), 1 <= t <= H
-    constexpr int O = N * (N - 1) / 2;
-    float s[H + 1], d[H + 1];
-    int e[H + 1];  // (k t) mod N for the current k
+    constexpr int L = prime_row_len(N);
+    static_assert(N == 1 || prime_rows_offset(N) >= 0, "row table");
+    float s[L + 1], d[L + 1];  // entries H + 1 .. L are zero padding
     const float x0 = __ldg(x);
-    float xm = 0.f;
 #pragma unroll
-    for (int t = 1; t <= H; ++t) {
-        const float a = __ldg(x + P * t), b = __ldg(x + P * (N - t));
-        s[t] = a + b;
-        d[t] = a - b;
-        e[t] = 0;
-    }
-    if (N % 2 == 0 && N > 1) xm = __ldg(x + P * (N / 2));
-#pragma unroll 1
-    for (int k = 0; k <= N / 2; ++k) {  // rolled: the body stays small in the instruction cache
-        float re = x0, im = 0.f;
-        if (N % 2 == 0 && N > 1) re += (k & 1) ? -xm : xm;
-#pragma unroll
-        for (int t = 1; t <= H; ++t) {
-            const float2 w = c_twall[O + e[t]];  // the same index across the warp
-            re = fmaf(s[t], w.x, re);
-            im = fmaf(-d[t], w.y, im);
-            e[t] += t;
-            if (e[t] >= N) e[t] -= N;
+    for (int t = 1; t <= L; ++t) {
+        if (t <= H) {
+            const float a = __ldg(x + P * t), b = __ldg(x + P * (N - t));
+            s[t] = a + b;
+            d[t] = a - b;
+        } else {
+            s[t] = d[t] = 0.f;
         }
-        if (k == 0 || 2 * k == N) im = 0.f;
-        X[P * k] = make_float2(re, im);
+    }
+    if constexpr (N > 1) {
+        const float4* rows = reinterpret_cast<const float4*>(g_prime_rows + prime_rows_offset(N));
+#pragma unroll 1
+        for (int k = 0; k <= N / 2; ++k) {  // rolled: the body stays small in the instruction cache
+            const float4* row = rows + k * (L / 2);
+            float re = x0, im = 0.f;
+#pragma unroll
+            for (int u = 0; u < L / 2; ++u) {
+                const float4 w = __ldg(row + u);  // t = 2u + 1 and 2u + 2
+                re = fmaf(s[2 * u + 1], w.x, re);
+                im = fmaf(-d[2 * u + 1], w.y, im);
+                re = fmaf(s[2 * u + 2], w.z, re);
+                im = fmaf(-d[2 * u + 2], w.w, im);
+            }
+            if (k == 0) im = 0.f;
+            X[P * k] = make_float2(re, im);
+        }
+    } else {
+        X[0] = make_float2(x0, 0.f);
     }
 }
 
 template <int N>
 __device__ __forceinline__ void irdft_small(const float2* __restrict__ X, int64_t P, float* x) {
     constexpr int H = (N - 1) / 2;  // frequencies 1..H appear twice (k and N - k)
-    constexpr int O = N * (N - 1) / 2;
-    float re[H + 1], im[H + 1];
-    int e[H + 1];  // (k t) mod N for the current t
+    constexpr int L = prime_row_len(N);
+    float re[L + 1], im[L + 1];
     const float r0 = __ldg(X).x;
-    float rm = 0.f;
 #pragma unroll
-    for (int k = 1; k <= H; ++k) {
-        const float2 v = __ldg(X + P * k);
-        re[k] = 2.f * v.x;
-        im[k] = 2.f * v.y;
-        e[k] = 0;
-    }
-    if (N % 2 == 0 && N > 1) rm = __ldg(X + P * (N / 2)).x;
-    const float sc = 1.f / (float)N;
-#pragma unroll 1
-    for (int t = 0; t <= N / 2; ++t) {
-        float a = r0, b = 0.f;
-        if (N % 2 == 0 && N > 1) a += (t & 1) ? -rm : rm;
-#pragma unroll
-        for (int k = 1; k <= H; ++k) {
-            const float2 w = c_twall[O + e[k]];
-            a = fmaf(re[k], w.x, a);
-            b = fmaf(im[k], w.y, b);
-            e[k] += k;
-            if (e[k] >= N) e[k] -= N;
+    for (int k = 1; k <= L; ++k) {
+        if (k <= H) {
+            const float2 v = __ldg(X + P * k);
+            re[k] = 2.f * v.x;
+            im[k] = 2.f * v.y;
+        } else {
+            re[k] = im[k] = 0.f;
         }
-        x[P * t] = (a - b) * sc;
-        if (t > 0 && 2 * t != N) x[P * (N - t)] = (a + b) * sc;
+    }
+    const float sc = 1.f / (float)N;
+    if constexpr (N > 1) {
+        const float4* rows = reinterpret_cast<const float4*>(g_prime_rows + prime_rows_offset(N));
+#pragma unroll 1
+        for (int t = 0; t <= N / 2; ++t) {
+            const float4* row = rows + t * (L / 2);
+            float a = r0, b = 0.f;
+#pragma unroll
+            for (int u = 0; u < L / 2; ++u) {
+                const float4 w = __ldg(row + u);  // k = 2u + 1 and 2u + 2
+                a = fmaf(re[2 * u + 1], w.x, a);
+                b = fmaf(im[2 * u + 1], w.y, b);
+                a = fmaf(re[2 * u + 2], w.z, a);
+                b = fmaf(im[2 * u + 2], w.w, b);
+            }
+            x[P * t] = (a - b) * sc;
+            if (t > 0) x[P * (N - t)] = (a + b) * sc;
+        }
+    } else {
+        x[0] = r0 * sc;
     }
 }
 
@@ -654,7 +701,7 @@ __device__ __forceinline__ void irfft_odd(const float2* __restrict__ X, int64_t 
 // registers, '1' at most 128, '2' more.  Each class runs in its own kernel instantiation whose
 // launch bounds give it 4, 2 or 1 CTAs of 256 threads per SM.
 // Bit n3 - 1 of kClassAtLeast1 / kClass2: class >= 1 / class 2.
-constexpr unsigned long long kClassAtLeast1 = 0xffffbae500000000ull, kClass2 = 0x0ull;
+constexpr unsigned long long kClassAtLeast1 = 0xfffffff500000000ull, kClass2 = 0x0ull;
 __host__ __device__ constexpr int small_class(int n3) {
     return (int)((kClassAtLeast1 >> (n3 - 1)) & 1ull) + (int)((kClass2 >> (n3 - 1)) & 1ull);
 }
@@ -781,6 +828,19 @@ cudaError_t ensure_twiddles() {
     err = cudaMemcpyToSymbol(c_twall, host.data(),
                              sizeof(float2) * (size_t)kSmallN3 * (kSmallN3 + 1) / 2);
     if (err != cudaSuccess) return err;
+    {
+        // rows of the direct prime-length DFTs: entry (k, t) = w(n, k t mod n), zero padding
+        std::vector<float2> rows((size_t)kPrimeRowsTotal, make_float2(0.f, 0.f));
+        for (int n : {37, 41, 43, 47, 53, 59, 61}) {
+            const int L = prime_row_len(n), H = (n - 1) / 2;
+            float2* base = rows.data() + prime_rows_offset(n);
+            for (int k = 0; k <= n / 2; ++k)
+                for (int t = 1; t <= H; ++t)
+                    base[(size_t)k * L + (t - 1)] = host[(size_t)tw_offset(n) + (size_t)((k * t) % n)];
+        }
+        err = cudaMemcpyToSymbol(g_prime_rows, rows.data(), sizeof(float2) * rows.size());
+        if (err != cudaSuccess) return err;
+    }
     // the largest dynamic shared memory any launch of these kernels asks for
     const int fwd = (int)fft_smem_bytes(TP_MAX_N3, false), inv = (int)fft_smem_bytes(TP_MAX_N3, true);
     int mf = fwd, mi = inv;
@@ -806,12 +866,14 @@ int fft_tiles(int64_t P, int max_n3, int uniform_n3, int n3) {
 }
 
 template <bool INV>
-cudaError_t launch_reg(const FftJob* d_jobs, int njobs, int tiles, int n3, cudaStream_t s) {
+cudaError_t launch_reg(const FftJob* d_jobs, int njobs, int tiles, int n3, bool planes,
+                       cudaStream_t s) {
     switch (n3) {
 #define TP_REG_CASE(n)                                                                 \
     case n:                                                                            \
         if (INV) irfft_reg_kernel<n><<<tiles, 256, 0, s>>>(d_jobs, njobs);             \
-        else rfft_reg_kernel<n><<<tiles, 256, 0, s>>>(d_jobs, njobs);                  \
+        else if (planes) rfft_reg_kernel<n, true><<<tiles, 256, 0, s>>>(d_jobs, njobs); \
+        else rfft_reg_kernel<n, false><<<tiles, 256, 0, s>>>(d_jobs, njobs);           \
         break;
         TP_REG_CASE(2) TP_REG_CASE(4) TP_REG_CASE(8) TP_REG_CASE(16) TP_REG_CASE(32)
         TP_REG_CASE(64)
@@ -821,6 +883,8 @@ cudaError_t launch_reg(const FftJob* d_jobs, int njobs, int tiles, int n3, cudaS
     return cudaGetLastError();
 }
 
+bool fft_writes_planes(int n3) { return reg_fft_size(n3); }
+
 bool fft_small_path(int max_n3, int uniform_n3) {
     return !reg_fft_size(uniform_n3) && max_n3 <= kSmallN3;
 }
@@ -828,9 +892,11 @@ bool fft_small_path(int max_n3, int uniform_n3) {
 int fft_small_class(int n3) { return (n3 >= 1 && n3 <= kSmallN3) ? small_class(n3) : 0; }
 
 cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
-                        int uniform_n3, bool vec_ok, cudaStream_t s, int small_cls) {
+                        int uniform_n3, bool vec_ok, cudaStream_t s, int small_cls, bool planes) {
     if (total_tiles <= 0) return cudaSuccess;
-    if (reg_fft_size(uniform_n3)) return launch_reg<false>(d_jobs, njobs, total_tiles, uniform_n3, s);
+    if (planes && !reg_fft_size(uniform_n3)) return cudaErrorInvalidValue;
+    if (reg_fft_size(uniform_n3))
+        return launch_reg<false>(d_jobs, njobs, total_tiles, uniform_n3, planes, s);
     if (max_n3 <= kSmallN3) {
         const int cls = small_cls >= 0 ? small_cls : fft_small_class(uniform_n3);
         return launch_small<false>(d_jobs, njobs, total_tiles, cls, s);
@@ -845,7 +911,8 @@ cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int ma
 cudaError_t launch_irfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
                          int uniform_n3, bool vec_ok, cudaStream_t s, int small_cls) {
     if (total_tiles <= 0) return cudaSuccess;
-    if (reg_fft_size(uniform_n3)) return launch_reg<true>(d_jobs, njobs, total_tiles, uniform_n3, s);
+    if (reg_fft_size(uniform_n3))
+        return launch_reg<true>(d_jobs, njobs, total_tiles, uniform_n3, false, s);
     if (max_n3 <= kSmallN3) {
         const int cls = small_cls >= 0 ? small_cls : fft_small_class(uniform_n3);
         return launch_small<true>(d_jobs, njobs, total_tiles, cls, s);

@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "tp_internal.cuh"
+#include "tp_planes.cuh"
 
 namespace tp {
 
@@ -344,6 +345,171 @@ __global__ void __launch_bounds__(kThreads, 1) cgemm_tc_kernel(
 }
 
 // ---------------------------------------------------------------------------------------
+// BF16x3 on the operand planes of tp_internal.cuh (PLANE_LEFT / PLANE_RIGHT), which the
+// forward DFT writes directly for power-of-two n3 <= 64.  A is read MN-major (m contiguous,
+// as the DFT lays out the spectrum), B K-major; 4-D tensor maps [slice][part][row][col]
+// zero-fill the M, N and K tails, so the planes carry no padding.  One K block is 64
+// elements (128 bytes); the K loop runs over part 0 (Re A against the rows [Br; Bi]) and then
+// part 1 (Im A against [-Bi; Br]).  On the real slices (0 and n3 / 2) Im A is zero and the
+// loop stops after part 0.  The CTA's roles, the ring and the bounded waits are those of
+// cgemm_tc_kernel above.
+// ---------------------------------------------------------------------------------------
+constexpr int kHalfA = 64 * kRowBytes;  // 64 k rows of one 64-element half of M: 8 KB
+
+// Shared-memory descriptor of an MN-major tile with the 128-byte swizzle: a 128-byte row holds
+// 64 consecutive m of one k, groups of 8 rows (8 k) are 1024 bytes apart (stride byte
+// offset) and the second 64 m start kHalfA bytes after the first (leading byte offset).
+__device__ __forceinline__ uint64_t sw128_mn_desc(const void* tile) {
+    const uint64_t a = smem_u32(tile);
+    uint64_t d = (a >> 4) & 0x3FFFull;
+    d |= (uint64_t)(kHalfA >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= 1ull << 46;
+    d |= 2ull << 61;
+    return d;
+}
+
+// bf16 x bf16 -> FP32, A MN-major (transpose-A bit), B K-major, M = kBM, N = kBN.
+__device__ __forceinline__ void umma_bf16_mn(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc(1) | (1u << 15)), "r"(acc));
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
+        "r"(c3)
+        : "memory");
+}
+
+// Grid (ceil(M/128), ceil(2N/256), slices), 128 threads; nk = ceil(K/64) K blocks per part;
+// zr1 = n3 / 2 for even n3 (the second real slice), else -1.
+__global__ void __launch_bounds__(kThreads, 1) cgemm_bf16x3_kernel(
+    const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+    const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+    float2* __restrict__ C, int M, int N, int64_t sC, int nk, int zr1, uint32_t* err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* done = empty + kStages;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = blockIdx.x, nt = blockIdx.y, z = blockIdx.z;
+    const int nkb = (z == 0 || z == zr1) ? nk : 2 * nk;
+    if (*reinterpret_cast<volatile uint32_t*>(err) != 0u) return;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % kStages, j = kb / kStages;
+            if (j > 0 && !mbar_wait(&empty[s], (j - 1) & 1)) {
+                atomicOr(err, 2u);
+                break;
+            }
+            unsigned char* st = smem + s * kStageBytes;
+            mbar_expect_tx(&full[s], kStageBytes);
+            const int part = kb >= nk ? 1 : 0;
+            const int k0 = (kb - part * nk) * 64;
+            const int m0 = mt * kBM;
+            tma_load_4d(st, &mAh, &full[s], m0, k0, part, z);
+            tma_load_4d(st + kHalfA, &mAh, &full[s], m0 + 64, k0, part, z);
+            tma_load_4d(st + kTileA, &mAl, &full[s], m0, k0, part, z);
+            tma_load_4d(st + kTileA + kHalfA, &mAl, &full[s], m0 + 64, k0, part, z);
+            tma_load_4d(st + 2 * kTileA, &mBh, &full[s], k0, nt * kBN, part, z);
+            tma_load_4d(st + 2 * kTileA + kTileB, &mBl, &full[s], k0, nt * kBN, part, z);
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % kStages, j = kb / kStages;
+            if (!mbar_wait(&full[s], j & 1)) {
+                atomicOr(err, 2u);
+                break;
+            }
+            fence_after_sync();
+            unsigned char* st = smem + s * kStageBytes;
+            const uint64_t ah = sw128_mn_desc(st), al = sw128_mn_desc(st + kTileA);
+            const uint64_t bh = sw128_desc(st + 2 * kTileA), bl = sw128_desc(st + 2 * kTileA + kTileB);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t aadv = (uint64_t)(kk * 16 * kRowBytes) >> 4;  // 16 k rows
+                const uint64_t badv = (uint64_t)(kk * 32) >> 4;              // 16 k elements
+                umma_bf16_mn(tmem, ah + aadv, bh + badv, (kb | kk) != 0);
+                umma_bf16_mn(tmem, ah + aadv, bl + badv, 1u);
+                umma_bf16_mn(tmem, al + aadv, bh + badv, 1u);
+            }
+            umma_commit(&empty[s]);
+        }
+        umma_commit(done);
+    }
+    __syncwarp();
+
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0));
+    fence_after_sync();
+    if (ok) {
+        const int row = mt * kBM + warp * 32 + lane;
+        float2* Cz = C + sC * z;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kBN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (row < M) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int n = nt * (kBN / 2) + c0 / 2 + q;
+                    if (n < N) Cz[row + (int64_t)M * n] = make_float2(v[2 * q], v[2 * q + 1]);
+                }
+            }
+        }
+    } else if (lane == 0) {
+        atomicOr(err, 4u);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+// Fills the planes of one operand from its complex spectrum X (P tubes x nslices).
+__global__ void __launch_bounds__(256) planes_from_spectrum_kernel(const float2* __restrict__ X,
+                                                                   FftJob J, int nslices) {
+    const int64_t total = J.P * nslices;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int z = (int)(i / J.P);
+        const int64_t p = i - (int64_t)z * J.P;
+        store_plane_value(J, plane_cursor(J, p), z, __ldg(X + i));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Host side: tensor maps and launches.
 // ---------------------------------------------------------------------------------------
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -414,7 +580,84 @@ cudaError_t run_tc(const float2* Ab, const float2* Bb, float2* Cb, int M, int N,
     return cudaGetLastError();
 }
 
+// 4-D map over [slices][parts][rows][cols] of bf16 with row pitch `pitch` elements and a
+// box of 64 columns (128 bytes) x box_rows rows; elements beyond cols or rows read as zero.
+bool make_map4(CUtensorMap* map, void* base, int64_t cols, int64_t rows, int64_t pitch,
+               int64_t slices, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)rows, 2, (cuuint64_t)slices};
+    cuuint64_t strides[3] = {(cuuint64_t)(pitch * 2), (cuuint64_t)(pitch * 2 * rows),
+                             (cuuint64_t)(pitch * 2 * rows * 2)};
+    cuuint32_t box[4] = {64, (cuuint32_t)box_rows, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 }  // namespace
+
+int64_t bf16_plane_pitch(int rows) { return ((int64_t)rows + 7) / 8 * 8; }
+
+int64_t bf16_left_plane_elems(int M, int K, int nslices) {
+    return bf16_plane_pitch(M) * 2 * (int64_t)K * nslices;
+}
+
+int64_t bf16_right_plane_elems(int N, int K, int nslices) {
+    return bf16_plane_pitch(K) * 2 * (2 * (int64_t)N) * nslices;
+}
+
+cudaError_t bf16_planes_from_spectrum(const float2* A, const float2* B, int M, int N, int K,
+                                      int nslices, void* planes, cudaStream_t s) {
+    uint16_t* base = static_cast<uint16_t*>(planes);
+    const int64_t la = bf16_left_plane_elems(M, K, nslices), lb = bf16_right_plane_elems(N, K, nslices);
+    FftJob ja{}, jb{};
+    ja.P = (int64_t)M * K;
+    ja.plane_kind = PLANE_LEFT;
+    ja.plane_rows = M;
+    ja.plane_pitch = bf16_plane_pitch(M);
+    ja.plane_hi = base;
+    ja.plane_lo = base + la;
+    jb.P = (int64_t)K * N;
+    jb.plane_kind = PLANE_RIGHT;
+    jb.plane_rows = K;
+    jb.plane_pitch = bf16_plane_pitch(K);
+    jb.plane_hi = base + 2 * la;
+    jb.plane_lo = base + 2 * la + lb;
+    int sms = 0, dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = 8 * sms;
+    planes_from_spectrum_kernel<<<grid, 256, 0, s>>>(A, ja, nslices);
+    planes_from_spectrum_kernel<<<grid, 256, 0, s>>>(B, jb, nslices);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cgemm_bf16x3(const void* planes, float2* C, int M, int N, int K, int nslices,
+                                int n3, uint32_t* err, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0 || nslices <= 0) return cudaSuccess;
+    uint16_t* base = static_cast<uint16_t*>(const_cast<void*>(planes));
+    const int64_t la = bf16_left_plane_elems(M, K, nslices), lb = bf16_right_plane_elems(N, K, nslices);
+    const int64_t pa = bf16_plane_pitch(M), pb = bf16_plane_pitch(K);
+    CUtensorMap mah, mal, mbh, mbl;
+    if (!make_map4(&mah, base, M, K, pa, nslices, 64) ||
+        !make_map4(&mal, base + la, M, K, pa, nslices, 64) ||
+        !make_map4(&mbh, base + 2 * la, K, 2 * (int64_t)N, pb, nslices, kBN) ||
+        !make_map4(&mbl, base + 2 * la + lb, K, 2 * (int64_t)N, pb, nslices, kBN))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(cgemm_bf16x3_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int nk = (K + 63) / 64;
+    const int zr1 = (n3 % 2 == 0) ? n3 / 2 : -1;
+    const int mtiles = (M + kBM - 1) / kBM, ntiles = (int)((2 * (int64_t)N + kBN - 1) / kBN);
+    cgemm_bf16x3_kernel<<<dim3(mtiles, ntiles, nslices), kThreads, kSmemBytes, s>>>(
+        mah, mal, mbh, mbl, C, M, N, (int64_t)M * N, nk, zr1, err);
+    return cudaGetLastError();
+}
 
 int64_t cgemm_tc_plane_bytes(int M, int N, int K, int nslices, int precision) {
     const bool tf32 = precision == TP_PREC_3XTF32;

@@ -28,7 +28,28 @@ struct FftJob {
     int64_t P = 0;             // tubes (n1*n2)
     int32_t n3 = 0;
     int32_t tile_begin = 0;    // first CTA of this job in the launch
+    // Forward DFT only, power-of-two n3 <= 64: with plane_kind != 0 the spectrum is written,
+    // instead of to X, as the BF16 hi/lo operand planes of the tensor-core slice GEMM
+    // (PLANE_LEFT / PLANE_RIGHT below; plane_rows = M or K, plane_pitch = the row pitch).
+    uint16_t* plane_hi = nullptr;
+    uint16_t* plane_lo = nullptr;
+    int64_t plane_pitch = 0;
+    int32_t plane_kind = 0;
+    int32_t plane_rows = 0;
 };
+
+// BF16x3 operand planes of the tensor-core slice GEMM C_z = A_z B_z (A_z M x K, B_z K x N,
+// complex), each value x stored as hi = bf16(x) and lo = bf16(x - hi) in two planes of the
+// same layout.  Rows have `pitch` elements (a multiple of 8, so that every row starts on a
+// 16-byte boundary); nothing beyond M or K is ever read, the GEMM's tensor maps zero-fill.
+//   PLANE_LEFT  (A, MN-major):  Re A_z(m, k) at ((2z + 0) K + k) pitch + m,
+//                               Im A_z(m, k) at ((2z + 1) K + k) pitch + m.
+//   PLANE_RIGHT (B, K-major, the rows of the real form [Br -Bi; Bi Br] interleaved so that
+//                output columns 2n and 2n+1 are Re and Im of C(:, n)):
+//                               part 0, rows 2n / 2n+1:  Re B_z(k, n) / Im B_z(k, n),
+//                               part 1, rows 2n / 2n+1: -Im B_z(k, n) / Re B_z(k, n),
+//                               at ((2z + part) 2N + row) pitch + k.
+enum : int32_t { PLANE_NONE = 0, PLANE_LEFT = 1, PLANE_RIGHT = 2 };
 
 // Fills the per-device twiddle table on first use; returns cudaSuccess or the error.
 cudaError_t ensure_twiddles();
@@ -37,11 +58,17 @@ cudaError_t ensure_twiddles();
 // the common n3 of all jobs of the launch, or 0 when they differ.  On the small-n3 path
 // (fft_small_path) a launch holds jobs of one register class (fft_small_class), given as
 // small_cls (-1: the class of uniform_n3).
+// `planes`: the jobs write BF16x3 operand planes (plane_kind != 0); the launch must then
+// satisfy fft_writes_planes(uniform_n3).
 cudaError_t launch_rfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
-                        int uniform_n3, bool vec_ok, cudaStream_t s, int small_cls = -1);
+                        int uniform_n3, bool vec_ok, cudaStream_t s, int small_cls = -1,
+                        bool planes = false);
 // Inverse DFT from the half spectrum with the conjugate mirror implied, scaled by 1/n3.
 cudaError_t launch_irfft(const FftJob* d_jobs, int njobs, int total_tiles, int max_n3,
                          int uniform_n3, bool vec_ok, cudaStream_t s, int small_cls = -1);
+// True when a forward DFT of tubes of length n3 (all of one length) can write the BF16x3
+// operand planes itself (FftJob::plane_kind).
+bool fft_writes_planes(int n3);
 // True when launches over jobs with these lengths use the per-length kernels for n3 <= 64.
 bool fft_small_path(int max_n3, int uniform_n3);
 // Register class (0, 1, 2) of the per-length kernel of n3 <= 64.
@@ -61,6 +88,18 @@ int64_t cgemm_tc_plane_bytes(int M, int N, int K, int nslices, int precision);
 cudaError_t launch_cgemm_tc(const float2* A, const float2* B, float2* C, int M, int N, int K,
                             int nslices, int precision, void* planes, uint32_t* err,
                             cudaStream_t s);
+// BF16x3 path on the operand planes above.  `planes` holds, in order, A's hi and lo planes
+// (bf16_left_plane_elems each) and B's hi and lo planes (bf16_right_plane_elems each).
+// bf16_planes_from_spectrum fills them from complex spectra A (M x K x nslices) and B
+// (K x N x nslices) when the forward DFT has not written them itself.  n3 marks the real
+// slices (0 and n3 / 2), whose second K half is zero and is skipped.
+int64_t bf16_plane_pitch(int rows);
+int64_t bf16_left_plane_elems(int M, int K, int nslices);
+int64_t bf16_right_plane_elems(int N, int K, int nslices);
+cudaError_t bf16_planes_from_spectrum(const float2* A, const float2* B, int M, int N, int K,
+                                      int nslices, void* planes, cudaStream_t s);
+cudaError_t launch_cgemm_bf16x3(const void* planes, float2* C, int M, int N, int K, int nslices,
+                                int n3, uint32_t* err, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Slice SVDs (tp_svd.cu)

@@ -64,16 +64,15 @@ __global__ void noalloc_jobs_kernel(FftJob* fft, SvdJob* svd, const float* Y, fl
     const int h = free_slices(n3);
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) {
-        fft[0].x = Y;
-        fft[0].X = spec;
-        fft[0].P = P;
-        fft[0].n3 = n3;
-        fft[0].tile_begin = 0;
-        fft[1].x = X;
-        fft[1].X = spec;
-        fft[1].P = P;
-        fft[1].n3 = n3;
-        fft[1].tile_begin = 0;
+        FftJob f;  // every field from its default (the array keeps the previous call's bytes)
+        f.x = Y;
+        f.X = spec;
+        f.P = P;
+        f.n3 = n3;
+        f.tile_begin = 0;
+        fft[0] = f;
+        f.x = X;
+        fft[1] = f;
     }
     if (k < h) {
         SvdJob j;

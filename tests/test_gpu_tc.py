@@ -24,8 +24,11 @@ def tp():
     return _tp
 
 
+# power-of-two n3 <= 64 (the forward DFT writes the BF16 operand planes itself) and other n3
+# (the planes are filled from the complex spectrum); M, K and N tails of every size
 SHAPES = [(128, 64, 128, 1), (1, 1, 1, 1), (200, 100, 150, 3), (64, 4, 64, 16),
-          (129, 65, 257, 2), (300, 200, 130, 5), (37, 129, 45, 17), (256, 512, 256, 8)]
+          (129, 65, 257, 2), (300, 200, 130, 5), (37, 129, 45, 17), (256, 512, 256, 8),
+          (100, 70, 90, 4), (130, 33, 70, 64), (7, 9, 3, 32)]
 
 
 @pytest.mark.parametrize("precision", ["bf16x3", "3xtf32"])
