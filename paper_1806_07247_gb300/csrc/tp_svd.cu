@@ -304,24 +304,40 @@ __global__ void __launch_bounds__(MAXE2 >= 8 ? 512 : 1024, 1)
     const float tol = prm.tol > 0.f ? prm.tol : 8.f * kEps;
     const float tol2 = tol * tol;
     const int N = n + (n & 1);
-    int sweeps = 0;
+    // Unchanged pairs are not revisited: every pair meets once per sweep, in the same round,
+    // so a pair whose two columns were not rotated since its previous visit (N - 1 rounds
+    // earlier) still passes the test it passed then, on the same data; skipping it gives the
+    // same result bit for bit.  last[c] is the round of column c's last rotation (-1: never;
+    // the `perm` array, unused until the epilogue).
+    int* last = perm;
+    for (int c = tid; c < n; c += T) last[c] = -1;
+    int sweeps = 0, round = 0;
     bool converged = n < 2;
     while (!converged && sweeps < prm.max_sweeps) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
-        for (int r = 0; r < N - 1; ++r) {
+        for (int r = 0; r < N - 1; ++r, ++round) {
             for (int base = 0; base < N / 2; base += slots) {  // uniform over the block
                 const int pi = base + slot;
                 int a = 0, b = 0;
                 if (pi == 0) { a = N - 1; b = r; }
                 else { a = (r + pi) % (N - 1); b = (r - pi + N - 1) % (N - 1); }
-                const bool active = pi < N / 2 && a < n && b < n;
+                bool active = pi < N / 2 && a < n && b < n;
                 const int p = active ? min(a, b) : 0, q = active ? max(a, b) : 0;
+                if (active && sweeps > 0) {
+                    const int prev = round - (N - 1);
+                    active = last[p] >= prev || last[q] >= prev;
+                }
+                if (!__any_sync(0xffffffffu, active)) continue;  // the warp's pairs all skip
                 bool did = jacobi_pair<LP, MAXE2, MODE == SVD_FULL>(
                     G + (size_t)p * ld, G + (size_t)q * ld, e2, sub, lane, tol2, active,
                     MODE == SVD_FULL ? VG + (size_t)p * n : nullptr,
                     MODE == SVD_FULL ? VG + (size_t)q * n : nullptr, n, prm.fp64_rotation != 0);
-                if (did && sub == 0) s_rot = 1;
+                if (did && sub == 0) {
+                    s_rot = 1;
+                    last[p] = round;
+                    last[q] = round;
+                }
             }
             __syncthreads();
         }
