@@ -17,8 +17,8 @@ The JSON line also carries:
   e2e           the same metric through tp_prox_tnn_batched_host: page-locked host inputs
                 copied in and outputs copied back inside the timed region, consecutive steps
                 on two alternating streams so copies overlap kernels;
-  tprod         t-product TFLOP/s on A 2048x1024x64 times B 1024x1024x64 in FP32,
-                BF16x3 and 3xTF32 slice-GEMM arithmetic;
+  tprod         t-product TFLOP/s on A 2048x1024x64 times B 1024x1024x64 (--gemm-shape) in
+                FP32, BF16x3 and 3xTF32 slice-GEMM arithmetic;
   tran          the conjugate transpose of that A, GB/s against the HBM copy peak;
   trpca         the synthetic TRPCA-style loop: 50 ADMM iterations on a 240x320x100 tensor
                 (tubal rank 10, unit RMS, 10% of entries corrupted by U[-5, 5]), each one
@@ -30,9 +30,10 @@ The JSON line also carries:
   plain.autotuned  the plain path again after tp_autotune_jacobi chose the Jacobi CTA shape
                 by timing its candidates on this batch (the shape stays set for the learned
                 step, whose fallback slices use it; the other legs run at the default);
-  stream        a bounded sample of the mixed call stream (prox_tnn and tprod calls on
-                tensors up to 512x512x256): every call on its own in FP32 with Jacobi, against
-                windows of calls as replayed learned batched plans plus BF16x3 tprod;
+  stream        the first 500 calls (--stream-calls) of the mixed call stream (prox_tnn and
+                tprod calls on tensors up to 512x512x256): every call on its own in FP32 with
+                Jacobi, against windows of calls as replayed learned batched plans plus BF16x3
+                tprod;
   cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
 
 `--impl reference` times the FP64 oracle itself (host cores) on the same workload.
@@ -116,7 +117,11 @@ def parse():
     p.add_argument("--no-trpca", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-stream", action="store_true")
-    p.add_argument("--stream-calls", type=int, default=48)
+    # the first 500 calls of the seeded stream: an unbiased sample of the 2000-call stream
+    # (same generator and distributions) whose plain pass (~12 s) keeps the run within minutes
+    p.add_argument("--stream-calls", type=int, default=500)
+    p.add_argument("--gemm-shape", default="2048,1024,1024,64",
+                   help="n1,n2,l,n3 of the tprod leg (A n1 x n2 x n3 times B n2 x l x n3)")
     p.add_argument("--stream-window", type=int, default=16)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--train-batches", type=int, default=4,
@@ -782,24 +787,24 @@ def sampled_rel_err(C, oracle):
 
 
 def tprod_leg(args, tp, synth, device):
-    """t-product of A 2048x1024x64 and B 1024x1024x64 (one rank) in the three slice-GEMM
-    arithmetics. Useful flops = (2 #real + 8 #complex slices) n1 n2 l; the split forms run
-    3x that on the tensor pipe."""
+    """t-product of A n1 x n2 x n3 and B n2 x l x n3 (--gemm-shape, default 2048x1024x64 and
+    1024x1024x64; one rank) in the three slice-GEMM arithmetics. Useful flops =
+    (2 #real + 8 #complex slices) n1 n2 l; the split forms run 3x that on the tensor pipe."""
     import torch
-    g = synth.gemm(0)
+    n1, n2, l, n3 = (int(v) for v in args.gemm_shape.split(","))
+    g = synth.gemm(0, n1, n2, l, n3)
     A, B = tp.to_device(g["A"], device), tp.to_device(g["B"], device)
     try:
         oracle = tprod_oracle_sample(g["A"], g["B"], args.cpu_seconds / 3)
     except Exception as e:  # a host-side baseline; the GPU legs below stand without it
         oracle = {"error": repr(e)}
     del g
-    n1, n2, l, n3 = 2048, 1024, 1024, 64
     C = tp.empty(n1, l, n3, device)
     h = n3 // 2 + 1
     nreal = 2 if n3 % 2 == 0 else 1
     flops = (2.0 * nreal + 8.0 * (h - nreal)) * n1 * n2 * l
     steps = max(3, min(args.steps, 10))
-    out = {"workload": "A 2048x1024x64 * B 1024x1024x64, N(0,1)", "flops": flops}
+    out = {"workload": f"A {n1}x{n2}x{n3} * B {n2}x{l}x{n3}, N(0,1)", "flops": flops}
     for prec in ("fp32", "bf16x3", "3xtf32"):
         for _ in range(2):
             tp.tprod(A, B, out=C, opts=tp.options(precision=prec, sync=False))
@@ -855,7 +860,7 @@ def tprod_leg(args, tp, synth, device):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
     nb = 8.0 * n1 * n2 * n3
-    out["tran"] = {"workload": "tran of A 2048x1024x64 (FP32, 512 MiB, larger than L2)",
+    out["tran"] = {"workload": f"tran of A {n1}x{n2}x{n3} (FP32, {nb / 2 / 2**20:.0f} MiB)",
                    "ms_per_call": ms, "bytes": nb,
                    "roofline": {"bound": "hbm", "achieved": nb / (ms / 1e3) / 1e9,
                                 "peak": HBM_PEAK_GBS, "unit": "GB/s",
@@ -1110,7 +1115,7 @@ def stream_leg(args, tp, synth, device):
             for i in tps:
                 tp.tprod(data[i]["A"], data[i]["B"], out=data[i]["Cc"], opts=o_tc)
 
-    reps = 2
+    reps = 1 if len(calls) >= 200 else 2
     out = {"workload": f"first {len(calls)} calls of the seeded mixed stream (prox_tnn or tprod "
                        "by a fair coin; n1,n2~U{16..512}, n3~U{4..256}, l~U{16..512}, tubal rank "
                        "r~U{4..40} + N(0,0.02^2) noise, tau = 2x noise level)",

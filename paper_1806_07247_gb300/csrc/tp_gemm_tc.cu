@@ -23,6 +23,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "tp_internal.cuh"
@@ -351,8 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1) cgemm_tc_kernel(
 // zero-fill the M, N and K tails, so the planes carry no padding.  One K block is 64
 // elements (128 bytes); the K loop runs over part 0 (Re A against the rows [Br; Bi]) and then
 // part 1 (Im A against [-Bi; Br]).  On the real slices (0 and n3 / 2) Im A is zero and the
-// loop stops after part 0.  The CTA's roles, the ring and the bounded waits are those of
-// cgemm_tc_kernel above.
+// loop stops after part 0.  The kernel is persistent, with two accumulators (below).
 // ---------------------------------------------------------------------------------------
 constexpr int kHalfA = 64 * kRowBytes;  // 64 k rows of one 64-element half of M: 8 KB
 
@@ -387,22 +387,36 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// Grid (ceil(M/128), ceil(2N/256), slices), 128 threads; nk = ceil(K/64) K blocks per part;
-// zr1 = n3 / 2 for even n3 (the second real slice), else -1.
-__global__ void __launch_bounds__(kThreads, 1) cgemm_bf16x3_kernel(
+constexpr int kPThreads = 256;         // 8 warps: TMA, MMA, two idle, four for the epilogue
+constexpr uint32_t kPTmemCols = 512;   // two 256-column accumulators
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent: min(tiles, SMs) CTAs, CTA b taking tiles b, b + gridDim.x, ... of the
+// (m tile, n tile, slice) grid, m tile fastest.  Lane 0 of warp 0 streams the K blocks of all
+// its tiles through the two-stage ring; lane 0 of warp 1 issues the MMAs of tile i into
+// accumulator i % 2 (TMEM columns 256 (i % 2) ..), once the epilogue has drained the tile
+// two before; warps 4..7 (TMEM lanes 32 (w - 4) ..) drain each finished accumulator to C and
+// release it.  So the epilogue of one tile overlaps the main loop of the next.  nk =
+// ceil(K/64) K blocks per part; zr1 = n3 / 2 for even n3 (the second real slice), else -1.
+// Every wait is bounded: a role that times out records an error bit and stops, and the
+// roles waiting on it time out in turn.
+__global__ void __launch_bounds__(kPThreads, 1) cgemm_bf16x3_kernel(
     const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
     const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-    float2* __restrict__ C, int M, int N, int64_t sC, int nk, int zr1, uint32_t* err) {
+    float2* __restrict__ C, int M, int N, int64_t sC, int nk, int zr1, int mtiles, int ntiles,
+    int tiles, uint32_t* err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
     uint64_t* empty = full + kStages;
-    uint64_t* done = empty + kStages;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* accf = empty + kStages;  // accumulator b filled (MMA commit)
+    uint64_t* acce = accf + 2;         // accumulator b drained (four epilogue warps)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mt = blockIdx.x, nt = blockIdx.y, z = blockIdx.z;
-    const int nkb = (z == 0 || z == zr1) ? nk : 2 * nk;
     if (*reinterpret_cast<volatile uint32_t*>(err) != 0u) return;
 
     if (threadIdx.x == 0) {
@@ -410,89 +424,125 @@ __global__ void __launch_bounds__(kThreads, 1) cgemm_bf16x3_kernel(
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tslot)),
-                     "r"(kTmemCols)
+                     "r"(kPTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tslot;
+    auto slice_of = [&](int t) { return t / (mtiles * ntiles); };
 
     if (warp == 0 && lane == 0) {
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % kStages, j = kb / kStages;
-            if (j > 0 && !mbar_wait(&empty[s], (j - 1) & 1)) {
-                atomicOr(err, 2u);
-                break;
+        int g = 0;  // K blocks issued by this CTA so far (ring position)
+        bool bad = false;
+        for (int t = blockIdx.x; t < tiles && !bad; t += gridDim.x) {
+            const int mt = t % mtiles, nt = (t / mtiles) % ntiles, z = slice_of(t);
+            const int nkb = (z == 0 || z == zr1) ? nk : 2 * nk;
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int s = g % kStages, j = g / kStages;
+                if (j > 0 && !mbar_wait(&empty[s], (j - 1) & 1)) {
+                    atomicOr(err, 2u);
+                    bad = true;
+                    break;
+                }
+                unsigned char* st = smem + s * kStageBytes;
+                mbar_expect_tx(&full[s], kStageBytes);
+                const int part = kb >= nk ? 1 : 0;
+                const int k0 = (kb - part * nk) * 64;
+                const int m0 = mt * kBM;
+                tma_load_4d(st, &mAh, &full[s], m0, k0, part, z);
+                tma_load_4d(st + kHalfA, &mAh, &full[s], m0 + 64, k0, part, z);
+                tma_load_4d(st + kTileA, &mAl, &full[s], m0, k0, part, z);
+                tma_load_4d(st + kTileA + kHalfA, &mAl, &full[s], m0 + 64, k0, part, z);
+                tma_load_4d(st + 2 * kTileA, &mBh, &full[s], k0, nt * kBN, part, z);
+                tma_load_4d(st + 2 * kTileA + kTileB, &mBl, &full[s], k0, nt * kBN, part, z);
             }
-            unsigned char* st = smem + s * kStageBytes;
-            mbar_expect_tx(&full[s], kStageBytes);
-            const int part = kb >= nk ? 1 : 0;
-            const int k0 = (kb - part * nk) * 64;
-            const int m0 = mt * kBM;
-            tma_load_4d(st, &mAh, &full[s], m0, k0, part, z);
-            tma_load_4d(st + kHalfA, &mAh, &full[s], m0 + 64, k0, part, z);
-            tma_load_4d(st + kTileA, &mAl, &full[s], m0, k0, part, z);
-            tma_load_4d(st + kTileA + kHalfA, &mAl, &full[s], m0 + 64, k0, part, z);
-            tma_load_4d(st + 2 * kTileA, &mBh, &full[s], k0, nt * kBN, part, z);
-            tma_load_4d(st + 2 * kTileA + kTileB, &mBl, &full[s], k0, nt * kBN, part, z);
         }
     } else if (warp == 1 && lane == 0) {
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % kStages, j = kb / kStages;
-            if (!mbar_wait(&full[s], j & 1)) {
+        int g = 0, i = 0;
+        bool bad = false;
+        for (int t = blockIdx.x; t < tiles && !bad; t += gridDim.x, ++i) {
+            const int z = slice_of(t);
+            const int nkb = (z == 0 || z == zr1) ? nk : 2 * nk;
+            const int b = i & 1;
+            if (i >= 2 && !mbar_wait(&acce[b], ((i >> 1) - 1) & 1)) {
                 atomicOr(err, 2u);
                 break;
             }
             fence_after_sync();
-            unsigned char* st = smem + s * kStageBytes;
-            const uint64_t ah = sw128_mn_desc(st), al = sw128_mn_desc(st + kTileA);
-            const uint64_t bh = sw128_desc(st + 2 * kTileA), bl = sw128_desc(st + 2 * kTileA + kTileB);
+            const uint32_t acc = tmem + (uint32_t)(b * kBN);
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int s = g % kStages, j = g / kStages;
+                if (!mbar_wait(&full[s], j & 1)) {
+                    atomicOr(err, 2u);
+                    bad = true;
+                    break;
+                }
+                fence_after_sync();
+                unsigned char* st = smem + s * kStageBytes;
+                const uint64_t ah = sw128_mn_desc(st), al = sw128_mn_desc(st + kTileA);
+                const uint64_t bh = sw128_desc(st + 2 * kTileA), bl = sw128_desc(st + 2 * kTileA + kTileB);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t aadv = (uint64_t)(kk * 16 * kRowBytes) >> 4;  // 16 k rows
-                const uint64_t badv = (uint64_t)(kk * 32) >> 4;              // 16 k elements
-                umma_bf16_mn(tmem, ah + aadv, bh + badv, (kb | kk) != 0);
-                umma_bf16_mn(tmem, ah + aadv, bl + badv, 1u);
-                umma_bf16_mn(tmem, al + aadv, bh + badv, 1u);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t aadv = (uint64_t)(kk * 16 * kRowBytes) >> 4;  // 16 k rows
+                    const uint64_t badv = (uint64_t)(kk * 32) >> 4;              // 16 k elements
+                    umma_bf16_mn(acc, ah + aadv, bh + badv, (kb | kk) != 0);
+                    umma_bf16_mn(acc, ah + aadv, bl + badv, 1u);
+                    umma_bf16_mn(acc, al + aadv, bh + badv, 1u);
+                }
+                umma_commit(&empty[s]);
             }
-            umma_commit(&empty[s]);
+            if (bad) break;
+            umma_commit(&accf[b]);
         }
-        umma_commit(done);
-    }
-    __syncwarp();
-
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0));
-    fence_after_sync();
-    if (ok) {
-        const int row = mt * kBM + warp * 32 + lane;
-        float2* Cz = C + sC * z;
+    } else if (warp >= 4) {
+        const int q = warp - 4;  // TMEM lanes 32 q .. 32 q + 31 = rows of the tile
+        int i = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+            const int mt = t % mtiles, nt = (t / mtiles) % ntiles, z = slice_of(t);
+            const int b = i & 1;
+            // tcgen05.ld is warp-collective: the whole warp proceeds only if every lane saw it
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[b], (i >> 1) & 1));
+            if (!ok) {
+                if (lane == 0) atomicOr(err, 4u);
+                break;
+            }
+            fence_after_sync();
+            const int row = mt * kBM + q * 32 + lane;
+            float2* Cz = C + sC * z;
 #pragma unroll 1
-        for (int c0 = 0; c0 < kBN; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (row < M) {
+            for (int c0 = 0; c0 < kBN; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kBN + c0), v);
+                if (row < M) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int n = nt * (kBN / 2) + c0 / 2 + q;
-                    if (n < N) Cz[row + (int64_t)M * n] = make_float2(v[2 * q], v[2 * q + 1]);
+                    for (int k = 0; k < 8; ++k) {
+                        const int n = nt * (kBN / 2) + c0 / 2 + k;
+                        if (n < N) Cz[row + (int64_t)M * n] = make_float2(v[2 * k], v[2 * k + 1]);
+                    }
                 }
             }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[b]);
         }
-    } else if (lane == 0) {
-        atomicOr(err, 4u);
     }
+    __syncwarp();
     fence_before_sync();
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols)
+                     "r"(kPTmemCols)
                      : "memory");
     }
 }
@@ -654,8 +704,15 @@ cudaError_t launch_cgemm_bf16x3(const void* planes, float2* C, int M, int N, int
     const int nk = (K + 63) / 64;
     const int zr1 = (n3 % 2 == 0) ? n3 / 2 : -1;
     const int mtiles = (M + kBM - 1) / kBM, ntiles = (int)((2 * (int64_t)N + kBN - 1) / kBN);
-    cgemm_bf16x3_kernel<<<dim3(mtiles, ntiles, nslices), kThreads, kSmemBytes, s>>>(
-        mah, mal, mbh, mbl, C, M, N, (int64_t)M * N, nk, zr1, err);
+    const int64_t tiles = (int64_t)mtiles * ntiles * nslices;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(tiles, sms);
+    cgemm_bf16x3_kernel<<<grid, kPThreads, kSmemBytes, s>>>(
+        mah, mal, mbh, mbl, C, M, N, (int64_t)M * N, nk, zr1, mtiles, ntiles, (int)tiles, err);
     return cudaGetLastError();
 }
 
