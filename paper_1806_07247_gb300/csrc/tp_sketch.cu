@@ -607,7 +607,11 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     const int q_retry = RETRY ? P.power_iters + P.extra_power[job] : 0;
 #define TP_SKETCH_Q (RETRY ? q_retry : P.power_iters)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool global_bufs = WIDE && P.gscratch != nullptr;  // the last class and retries
+    // tall buffers in the global scratch only when the launch has one and they do not fit the
+    // launch's shared memory (the retry launches have both: the slices that fit keep the
+    // faster shared-memory buffers)
+    const bool global_bufs = WIDE && P.gscratch != nullptr &&
+                             sketch_smem_need(n1, n2, l) > (size_t)P.smem_bytes;
     if (l <= 0 || l >= min(n1, n2) || l > (WIDE ? kLMax : kNarrowL) ||
         (global_bufs ? (sketch_small_need(n1, n2, l) > (size_t)P.smem_bytes ||
                         (int64_t)3 * nm * l > P.gstride)
