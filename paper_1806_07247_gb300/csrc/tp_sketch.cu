@@ -607,11 +607,12 @@ __device__ void sketch_one(const SvdJob* __restrict__ jobs, int job, const Sketc
     const int q_retry = RETRY ? P.power_iters + P.extra_power[job] : 0;
 #define TP_SKETCH_Q (RETRY ? q_retry : P.power_iters)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // tall buffers in the global scratch only when the launch has one and they do not fit the
-    // launch's shared memory (the retry launches have both: the slices that fit keep the
-    // faster shared-memory buffers)
+    // tall buffers in the global scratch when the launch has one: always in the global class
+    // (its shared memory holds only the small arrays), and in a retry round only for the
+    // slices that do not fit the round's shared memory (the others keep the faster
+    // shared-memory buffers)
     const bool global_bufs = WIDE && P.gscratch != nullptr &&
-                             sketch_smem_need(n1, n2, l) > (size_t)P.smem_bytes;
+                             (!RETRY || sketch_smem_need(n1, n2, l) > (size_t)P.smem_bytes);
     if (l <= 0 || l >= min(n1, n2) || l > (WIDE ? kLMax : kNarrowL) ||
         (global_bufs ? (sketch_small_need(n1, n2, l) > (size_t)P.smem_bytes ||
                         (int64_t)3 * nm * l > P.gstride)
@@ -925,7 +926,21 @@ __global__ void __launch_bounds__(kTS, 4) sketch_svt_kernel(const SvdJob* __rest
         const int item = sh.item;
         if (item >= *P.queue_len) break;
         const int job = P.order[item];
-        if (job >= 0 && job < P.njobs) sketch_one<RETRY, WIDE>(jobs, job, P, smem4, sh);
+        if (job >= 0 && job < P.njobs) {
+            // a retry round holds slices of every width: those within the narrow limit whose
+            // buffers fit the round's shared memory take the leaner narrow code (block-uniform:
+            // every thread reads the same slice)
+            if constexpr (RETRY && WIDE) {
+                const int l = P.ell[job];
+                if (l <= kNarrowL &&
+                    sketch_smem_need(jobs[job].n1, jobs[job].n2, l) <= (size_t)P.smem_bytes)
+                    sketch_one<RETRY, false>(jobs, job, P, smem4, sh);
+                else
+                    sketch_one<RETRY, WIDE>(jobs, job, P, smem4, sh);
+            } else {
+                sketch_one<RETRY, WIDE>(jobs, job, P, smem4, sh);
+            }
+        }
         __syncthreads();  // the CTA is done with this slice's shared state
     }
 }
