@@ -218,9 +218,9 @@ class Clocks:
 # ----------------------------------------------------------------------------- workload
 # DRAM traffic of the sketch stage (dram__bytes_read.sum + dram__bytes_write.sum over the four
 # class launches of one call) per byte of half spectrum, from an ncu capture of the 160-tensor
-# batch of the same workload: 278.2 MB for 178.9 MB of spectrum.  The traffic of a batch is
+# batch of the same workload: 274.9 MB for 178.9 MB of spectrum.  The traffic of a batch is
 # taken in proportion to its half-spectrum bytes.
-SKETCH_DRAM_PER_SPEC_BYTE = 278.2 / 178.9
+SKETCH_DRAM_PER_SPEC_BYTE = 274.9 / 178.9
 
 
 def svd_launch_groups(shapes, shape=None):
