@@ -264,6 +264,40 @@ tp_status finish(uint32_t* d_status, const Opts& o, cudaStream_t s) {
     return (h & 1u) ? TP_ERR_NOT_CONVERGED : TP_OK;
 }
 
+// Events of one call, destroyed when it returns (the driver releases them once
+// the recorded work completes).
+struct CallEvents {
+    std::vector<cudaEvent_t> ev;
+    tp_status create(size_t n) {
+        ev.assign(n, nullptr);
+        for (auto& e : ev) TP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        return TP_OK;
+    }
+    ~CallEvents() {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+// Per-device streams on which the launch groups of one SVD batch after the first run beside it
+// (created once, never destroyed).
+constexpr int kGroupStreams = 3;
+std::mutex g_group_mutex;
+cudaStream_t g_group_streams[128][kGroupStreams] = {};
+
+tp_status group_streams(cudaStream_t* out) {
+    int dev = 0;
+    TP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return TP_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_group_mutex);
+    for (int i = 0; i < kGroupStreams; ++i) {
+        if (!g_group_streams[dev][i])
+            TP_CUDA(cudaStreamCreateWithFlags(&g_group_streams[dev][i], cudaStreamNonBlocking));
+        out[i] = g_group_streams[dev][i];
+    }
+    return TP_OK;
+}
+
 // Group per-slice SVD jobs by kernel instantiation and launch each group.
 struct SvdBatch {
     struct Item {
@@ -310,6 +344,7 @@ struct SvdBatch {
         p.sweeps_out = o.sweeps_out;
         p.status = d_status;
         p.fp64_rotation = o.jacobi_fp64;
+        std::vector<SvdLaunch> launches;
         size_t i = 0;
         while (i < items.size()) {
             size_t j = i;
@@ -327,8 +362,30 @@ struct SvdBatch {
             L.in_smem = items[i].cfg.in_smem;
             L.smem_bytes = smem;
             L.threads = threads;
-            TP_CUDA(launch_svd(L, p, s));
+            launches.push_back(L);
             i = j;
+        }
+        // One group, or the learned method's fallback (its groups hold only the few slices the
+        // sketch path rejected): in order on the caller's stream.  Otherwise the first group on
+        // the caller's stream and the others on group streams that fork from it and join back,
+        // so that one group's tail overlaps the others.  (The group streams are shared by all
+        // calls on a device, so concurrent callers would also wait on each other's groups.)
+        if (launches.size() == 1 || o.method == TP_METHOD_LEARNED) {
+            for (const SvdLaunch& L : launches) TP_CUDA(launch_svd(L, p, s));
+            return TP_OK;
+        }
+        cudaStream_t gs[kGroupStreams];
+        TP_TRY(group_streams(gs));
+        const int nside = (int)std::min<size_t>(launches.size() - 1, kGroupStreams);
+        CallEvents ev;
+        TP_TRY(ev.create(1 + (size_t)nside));
+        TP_CUDA(cudaEventRecord(ev.ev[0], s));
+        for (int k = 0; k < nside; ++k) TP_CUDA(cudaStreamWaitEvent(gs[k], ev.ev[0], 0));
+        for (size_t g = 0; g < launches.size(); ++g)
+            TP_CUDA(launch_svd(launches[g], p, g == 0 ? s : gs[(g - 1) % nside]));
+        for (int k = 0; k < nside; ++k) {
+            TP_CUDA(cudaEventRecord(ev.ev[1 + k], gs[k]));
+            TP_CUDA(cudaStreamWaitEvent(s, ev.ev[1 + k], 0));
         }
         return TP_OK;
     }
@@ -761,20 +818,6 @@ tp_status side_streams(SideStreams* out) {
     return TP_OK;
 }
 
-// Events of one host-buffer call, destroyed when it returns (the driver releases them once
-// the recorded work completes).
-struct CallEvents {
-    std::vector<cudaEvent_t> ev;
-    tp_status create(size_t n) {
-        ev.assign(n, nullptr);
-        for (auto& e : ev) TP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        return TP_OK;
-    }
-    ~CallEvents() {
-        for (auto e : ev)
-            if (e) cudaEventDestroy(e);
-    }
-};
 
 // Copies [first, last) of a chunk between host and device, one cudaMemcpyAsync per run of
 // tensors that are contiguous on both sides.
