@@ -120,6 +120,8 @@ def parse():
     # the first 500 calls of the seeded stream: an unbiased sample of the 2000-call stream
     # (same generator and distributions) whose plain pass (~12 s) keeps the run within minutes
     p.add_argument("--stream-calls", type=int, default=500)
+    p.add_argument("--host-parts", type=int, default=2, choices=[1, 2],
+                   help="tp_options.host_parts of the e2e leg's calls")
     p.add_argument("--gemm-shape", default="2048,1024,1024,64",
                    help="n1,n2,l,n3 of the tprod leg (A n1 x n2 x n3 times B n2 x l x n3)")
     p.add_argument("--stream-window", type=int, default=16)
@@ -545,7 +547,9 @@ def run_tp(args):
     sk_tflops_survey = sketch_model_flops(shapes, learned["widths"], survey=True) / \
         (st["sketch_svt"] / 1e3) / 1e12
     fb = learned["flags"]
-    groups = svd_launch_groups([(a, b) for a, b, _ in shapes], shape)
+    # the learned method's fallback launches are never split by CTA size
+    lshape = dict(shape, split_launches=0) if shape else shape
+    groups = svd_launch_groups([(a, b) for a, b, _ in shapes], lshape)
     dominant = "sketch_svt" if st["sketch_svt"] >= st["jacobi_svt"] else "jacobi_svt"
     if dominant == "sketch_svt":
         roof = {"kernel": "sketch_svt_kernel (randomized range finder + small Jacobi SVD + SVT)",
@@ -693,10 +697,11 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
             h.copy_(Y.cpu())
         sets.append((hin, hout, tp.make_descs(hin, hout, taus)))
     streams = [torch.cuda.Stream(device), torch.cuda.Stream(device)]
-    # one part per call: with consecutive calls on two streams, each call's copies already
-    # overlap the neighbouring calls' kernels, and a second part would only add its own launch
-    # tails (measured side by side: 7.57 ms per step with one part, 9.0-9.3 ms with two)
-    opts = tp.options(sync=False, method="learned", host_parts=1)
+    # --host-parts: two parts (the library default) by default.  One part is faster on average
+    # with calls on two streams (7.6 against 8.9-9.3 ms per step side by side in one process),
+    # but across fresh processes of the whole bench it ranged from 0.65M to 1.22M slices/s,
+    # against 1.04-1.06M for two parts.
+    opts = tp.options(sync=False, method="learned", host_parts=args.host_parts)
 
     def step(i):
         hin, hout, d = sets[i % 2]
@@ -725,7 +730,7 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
     nb = sum(4 * Y.numel() for Y in Ys)
     return {"value": job_throughput(sum_over_ranks(slices, device), args.steps, ms), "unit": UNIT,
             "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
-            "api": "tp_prox_tnn_batched_host (host_parts=1) on two alternating streams "
+            "api": f"tp_prox_tnn_batched_host (host_parts={args.host_parts}) on two alternating streams "
                    "(page-locked host tensors; each step's copies overlap the neighbouring "
                    "steps' kernels)"}
 

@@ -494,7 +494,10 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
     int64_t slices = 0;
     std::vector<SvdConfig> cfg(count);
     std::vector<int64_t> work(count, 0);
-    const JacobiShape shape = jacobi_shape_current();
+    JacobiShape shape = jacobi_shape_current();
+    // the learned method's Jacobi launches hold only the slices the sketch path rejects: one
+    // launch per instantiation, never split by CTA size (splitting would only add launches)
+    if (o.method == TP_METHOD_LEARNED) shape.split = 0;
     int64_t nfft = 0;
     int max_n1 = 1, max_n2 = 1;
     for (int64_t t = 0; t < count; ++t) {
