@@ -120,7 +120,7 @@ def parse():
     # the first 500 calls of the seeded stream: an unbiased sample of the 2000-call stream
     # (same generator and distributions) whose plain pass (~12 s) keeps the run within minutes
     p.add_argument("--stream-calls", type=int, default=500)
-    p.add_argument("--host-parts", type=int, default=2, choices=[1, 2],
+    p.add_argument("--host-parts", type=int, default=1, choices=[1, 2],
                    help="tp_options.host_parts of the e2e leg's calls")
     p.add_argument("--gemm-shape", default="2048,1024,1024,64",
                    help="n1,n2,l,n3 of the tprod leg (A n1 x n2 x n3 times B n2 x l x n3)")
@@ -697,10 +697,9 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
             h.copy_(Y.cpu())
         sets.append((hin, hout, tp.make_descs(hin, hout, taus)))
     streams = [torch.cuda.Stream(device), torch.cuda.Stream(device)]
-    # --host-parts: two parts (the library default) by default.  One part is faster on average
-    # with calls on two streams (7.6 against 8.9-9.3 ms per step side by side in one process),
-    # but across fresh processes of the whole bench it ranged from 0.65M to 1.22M slices/s,
-    # against 1.04-1.06M for two parts.
+    # --host-parts (default 1): with consecutive calls on two streams, each call's copies
+    # already overlap the neighbouring calls' kernels, and a second part only adds its own
+    # launch tails (7.6 against 8.9-9.3 ms per step measured side by side)
     opts = tp.options(sync=False, method="learned", host_parts=args.host_parts)
 
     def step(i):
@@ -708,7 +707,9 @@ def e2e_leg(args, tp, Ys, Xs, taus, descs, slices, world, barrier, device):
         tp.prox_tnn_batched_host(hin, taus, outs=hout, opts=opts, descs=d,
                                  stream=streams[i % 2])
 
-    for i in range(max(2, args.warmup)):
+    # at least 8 warm-up steps: the first calls on two streams grow the stream-ordered pool and
+    # the library's page-locked staging
+    for i in range(max(8, args.warmup)):
         step(i)
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
