@@ -664,7 +664,18 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             sp.resid_tol = 1e-5f;
             return sp;
         };
+        // the class launches are independent (each takes its own queue): class 0 on the
+        // caller's stream and the others on group streams forked from it, so that one class's
+        // tail overlaps the next classes; the retry rounds wait for all of them
+        cudaStream_t cls_streams[kGroupStreams];
+        TP_TRY(group_streams(cls_streams));
+        CallEvents cls_ev;
+        TP_TRY(cls_ev.create(1 + kGroupStreams));
+        TP_CUDA(cudaEventRecord(cls_ev.ev[0], s));
+        for (int k = 0; k < kGroupStreams; ++k)
+            TP_CUDA(cudaStreamWaitEvent(cls_streams[k], cls_ev.ev[0], 0));
         for (int c = 0; c < caps.n; ++c) {
+            const cudaStream_t cst = c == 0 ? s : cls_streams[(c - 1) % kGroupStreams];
             const bool global_class = c == caps.n - 1;
             // the global-scratch class: its shared part, one CTA per SM (one scratch slot each);
             // empty unless some slice can need it (then a one-CTA launch finds its queue empty)
@@ -683,7 +694,11 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
                 sp.gstride = g_stride;
                 grid = g_stride > 0 ? std::min<int64_t>(slices, sms_ws) : 1;
             }
-            TP_CUDA(launch_sketch_svt(d_nat, (int)grid, smem, sp, s));
+            TP_CUDA(launch_sketch_svt(d_nat, (int)grid, smem, sp, cst));
+        }
+        for (int k = 0; k < kGroupStreams; ++k) {
+            TP_CUDA(cudaEventRecord(cls_ev.ev[1 + k], cls_streams[k]));
+            TP_CUDA(cudaStreamWaitEvent(s, cls_ev.ev[1 + k], 0));
         }
         const int retry_per_sm = sketch_blocks_per_sm(retry_smem);
         if (retry_per_sm <= 0) return TP_ERR_CUDA;
