@@ -664,18 +664,24 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             sp.resid_tol = 1e-5f;
             return sp;
         };
-        // the class launches are independent (each takes its own queue): class 0 on the
-        // caller's stream and the others on group streams forked from it, so that one class's
-        // tail overlaps the next classes; the retry rounds wait for all of them
-        cudaStream_t cls_streams[kGroupStreams];
-        TP_TRY(group_streams(cls_streams));
+        // the class launches are independent (each takes its own queue).  With many slices
+        // (several per resident CTA of every SM) class 0 runs on the caller's stream and the
+        // others on group streams forked from it, so that one class's tail overlaps the next
+        // classes; the retry rounds wait for all of them.  A call of few, large slices keeps
+        // them in order: there concurrent classes only compete for the same SMs.
+        const bool fork_classes = slices >= (int64_t)16 * sms;
+        cudaStream_t cls_streams[kGroupStreams] = {};
         CallEvents cls_ev;
-        TP_TRY(cls_ev.create(1 + kGroupStreams));
-        TP_CUDA(cudaEventRecord(cls_ev.ev[0], s));
-        for (int k = 0; k < kGroupStreams; ++k)
-            TP_CUDA(cudaStreamWaitEvent(cls_streams[k], cls_ev.ev[0], 0));
+        if (fork_classes) {
+            TP_TRY(group_streams(cls_streams));
+            TP_TRY(cls_ev.create(1 + kGroupStreams));
+            TP_CUDA(cudaEventRecord(cls_ev.ev[0], s));
+            for (int k = 0; k < kGroupStreams; ++k)
+                TP_CUDA(cudaStreamWaitEvent(cls_streams[k], cls_ev.ev[0], 0));
+        }
         for (int c = 0; c < caps.n; ++c) {
-            const cudaStream_t cst = c == 0 ? s : cls_streams[(c - 1) % kGroupStreams];
+            const cudaStream_t cst =
+                (c == 0 || !fork_classes) ? s : cls_streams[(c - 1) % kGroupStreams];
             const bool global_class = c == caps.n - 1;
             // the global-scratch class: its shared part, one CTA per SM (one scratch slot each);
             // empty unless some slice can need it (then a one-CTA launch finds its queue empty)
@@ -696,7 +702,7 @@ tp_status prox_batched(const tp_tensor_desc* d, int64_t count, const Opts& o, cu
             }
             TP_CUDA(launch_sketch_svt(d_nat, (int)grid, smem, sp, cst));
         }
-        for (int k = 0; k < kGroupStreams; ++k) {
+        for (int k = 0; fork_classes && k < kGroupStreams; ++k) {
             TP_CUDA(cudaEventRecord(cls_ev.ev[1 + k], cls_streams[k]));
             TP_CUDA(cudaStreamWaitEvent(s, cls_ev.ev[1 + k], 0));
         }
