@@ -143,3 +143,31 @@ def test_peaks_come_from_the_measured_file_or_the_recorded_values(tmp_path):
     assert miss["source"].startswith("recorded") and miss["hbm_gbs"] == 6685.5
     # FP32 ALU peak: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
     assert abs(152 * 128 * 2 * 2.070e9 / 1e12 - 80.54784) < 1e-9
+
+
+def test_learned_launch_count_ignores_split_launches():
+    # the learned method's fallback groups are planned without splitting by CTA size, so the
+    # bench counts them under the chosen shape with split_launches = 0 (measured: 240
+    # launches over 10 steps under an autotuned shape that splits the plain path's launches)
+    shapes = _batch_shapes()
+    n3s = [s.n3 for s in synth.batched_specs(512, 0)]
+    tuned = {"target_lane_pairs": 7, "max_warps": 32, "split_launches": 1}
+    learned = dict(tuned, split_launches=0)
+    assert bench.svd_launch_groups(shapes, tuned) >= bench.svd_launch_groups(shapes, learned)
+    per_call = bench.LEARNED_FIXED_LAUNCHES + 2 * bench.dft_launches(n3s) + \
+        bench.svd_launch_groups(shapes, learned)
+    assert per_call * 10 == 240
+
+
+def test_bench_options_parse():
+    old = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        a = bench.parse()
+        assert a.host_parts == 1 and a.stream_calls == 500
+        assert tuple(int(v) for v in a.gemm_shape.split(",")) == (2048, 1024, 1024, 64)
+        sys.argv = ["bench.py", "--host-parts", "2", "--gemm-shape", "1024,1024,512,32"]
+        a = bench.parse()
+        assert a.host_parts == 2 and a.gemm_shape == "1024,1024,512,32"
+    finally:
+        sys.argv = old
