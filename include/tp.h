@@ -326,6 +326,11 @@ tp_status tp_proposer_set(const float* host_params);
  *     4 pairs, the kernel's register limit);
  *   split_launches: 1 launches slices whose CTA sizes differ separately; 0 (default) launches
  *     all slices of one kernel instantiation together at the largest CTA size among them.
+ *     With TP_METHOD_LEARNED the Jacobi launches (only the slices the sketch path rejects)
+ *     are never split.
+ * With several launches, the Jacobi method runs the first on `stream` and the others on
+ * library streams forked from it and joined back before the call's next step (the library
+ * creates these streams once per device; concurrent calls on one device share them).
  * The current device's shape applies to the Jacobi launches of tp_prox_tnn, tp_prox_tnn_batched,
  * tp_prox_tnn_batched_host, plans created while it is set, tp_proposer_train, tp_tnn, tp_tsn
  * and tp_tubalrank; tp_tsvd and tp_prox_tnn_noalloc always use the default. Results under
