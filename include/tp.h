@@ -129,7 +129,9 @@ typedef struct tp_options {
  *   as wide (at least 4 columns more, at most 48) if the rank was underestimated; every other
  *   failed slice is recomputed by the Jacobi path. Widths up to 48; slices whose sketch
  *   buffers exceed shared memory keep them in a global scratch area of the call. Error target
- *   1e-4 relative (Frobenius) against the exact prox.
+ *   1e-4 relative (Frobenius) against the exact prox. A call of at least 16 slices per SM runs
+ *   its sketch size classes on library streams forked from `stream` and joined back (shared
+ *   by the calls on a device, like those of the Jacobi launch groups).
  */
 #define TP_METHOD_JACOBI 0
 #define TP_METHOD_LEARNED 1
