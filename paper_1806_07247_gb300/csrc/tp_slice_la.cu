@@ -212,6 +212,150 @@ __global__ void __launch_bounds__(512, 1) tinv_kernel(const LaJob* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------------------
+// Register-resident slice inverse for n <= 32 RM.  Lane l of warp w holds rows l + 32 m
+// (m < RM) of columns w + W c (c < CW) in registers for the whole elimination, so a step reads
+// and writes no matrix element in memory.  The rows are not exchanged: step k takes as pivot
+// the largest |a_ik| among the rows not yet used (physical row p_k), scales row p_k and reduces
+// every other row, as the kernel above does after its exchange.  Regarding the matrix as the
+// map y = A x, each such step swaps the roles of x_k and y_(p_k), so after n steps the element
+// at (p_k, j) is element (k, p_j) of the inverse; the final store applies that permutation.
+// One barrier per step: the warp that owns column k chooses the pivot and publishes the
+// column (double-buffered), and each warp takes row p_k of its own columns from lane p_k mod 32
+// by shuffles.
+// ---------------------------------------------------------------------------------------
+template <int RM, int W, int CW>
+__global__ void __launch_bounds__(32 * W) tinv_reg_kernel(const LaJob* __restrict__ jobs,
+                                                          uint32_t* status) {
+    static_assert(32 * RM == W * CW, "the register tile is square");
+    constexpr int NC = 32 * RM;
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ float2 colk[2][NC];
+    __shared__ int pivot[2];
+    __shared__ int perm[NC], iperm[NC];
+    __shared__ float red[W];
+    const LaJob J = jobs[blockIdx.x];
+    const int n = J.n1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    float2 M[RM][CW];
+    float amax2 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+#pragma unroll
+        for (int m = 0; m < RM; ++m) {
+            const int i = lane + 32 * m, j = warp + W * c;
+            M[m][c] = (i < n && j < n) ? J.A[i + (size_t)n * j] : make_float2(0.0f, 0.0f);
+            amax2 = fmaxf(amax2, abs2(M[m][c]));
+        }
+    for (int o = 16; o; o >>= 1) amax2 = fmaxf(amax2, __shfl_xor_sync(kFull, amax2, o));
+    if (lane == 0) red[warp] = amax2;
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < W; ++w) amax2 = fmaxf(amax2, red[w]);
+    // the singularity threshold of the kernel above
+    const float thr = (float)n * kEps;
+    const float thr2 = thr * thr * amax2;
+    uint32_t avail = 0;  // bit m: row lane + 32 m can still be a pivot
+#pragma unroll
+    for (int m = 0; m < RM; ++m)
+        if (lane + 32 * m < n) avail |= 1u << m;
+
+    bool singular = false;
+    for (int k = 0; k < n; ++k) {
+        const int b = k & 1;
+        const int wk = k % W, ck = k / W;
+        if (warp == wk) {  // owner of column k: publish it and choose the pivot
+            float pv = -1.0f;
+            int p = 0x7fffffff;
+#pragma unroll
+            for (int c = 0; c < CW; ++c)
+                if (c == ck) {
+#pragma unroll
+                    for (int m = 0; m < RM; ++m) {
+                        colk[b][lane + 32 * m] = M[m][c];
+                        if ((avail >> m) & 1u) argmax_step(pv, p, abs2(M[m][c]), lane + 32 * m);
+                    }
+                }
+            for (int o = 16; o; o >>= 1)
+                argmax_step(pv, p, __shfl_xor_sync(kFull, pv, o), __shfl_xor_sync(kFull, p, o));
+            if (lane == 0) pivot[b] = pv > thr2 ? p : -1;  // also catches NaN and Inf
+        }
+        __syncthreads();
+        const int p = pivot[b];
+        if (p < 0) {
+            singular = true;
+            break;
+        }
+        if (threadIdx.x == 0) perm[k] = p;
+        const float2 inv = crcp(colk[b][p]);
+        const int lp = p & 31, mp = p >> 5;
+        // the scaled pivot row on this warp's columns; 1 / pivot in column k
+        float2 r[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) r[c] = M[0][c];
+#pragma unroll
+        for (int m = 1; m < RM; ++m)
+            if (m == mp) {
+#pragma unroll
+                for (int c = 0; c < CW; ++c) r[c] = M[m][c];
+            }
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+            const float2 x = make_float2(__shfl_sync(kFull, r[c].x, lp), __shfl_sync(kFull, r[c].y, lp));
+            r[c] = cmul(x, inv);
+        }
+        if (warp == wk) {  // column k: a_ik <- 0 before the update, so it ends at -f_i / pivot
+#pragma unroll
+            for (int c = 0; c < CW; ++c)
+                if (c == ck) {
+                    r[c] = inv;
+#pragma unroll
+                    for (int m = 0; m < RM; ++m) M[m][c] = make_float2(0.0f, 0.0f);
+                }
+        }
+#pragma unroll
+        for (int m = 0; m < RM; ++m) {
+            const float2 f = colk[b][lane + 32 * m];
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+                const float2 a = M[m][c];
+                M[m][c] = make_float2(fmaf(-f.x, r[c].x, fmaf(f.y, r[c].y, a.x)),
+                                      fmaf(-f.x, r[c].y, fmaf(-f.y, r[c].x, a.y)));
+            }
+        }
+        if (lane == lp) {  // the pivot row itself becomes the scaled row
+#pragma unroll
+            for (int m = 0; m < RM; ++m)
+                if (m == mp) {
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) M[m][c] = r[c];
+                }
+            avail &= ~(1u << mp);
+        }
+    }
+    if (singular) {
+        const float qnan = __int_as_float(0x7fc00000);
+        for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) J.R[e] = make_float2(qnan, qnan);
+        if (threadIdx.x == 0 && status) atomicOr(status, 2u);
+        return;
+    }
+    __syncthreads();  // perm complete
+    for (int t = threadIdx.x; t < n; t += blockDim.x) iperm[perm[t]] = t;
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+        const int j = warp + W * c;
+        if (j >= n) continue;
+        const size_t col = (size_t)n * perm[j];
+#pragma unroll
+        for (int m = 0; m < RM; ++m) {
+            const int i = lane + 32 * m;
+            if (i < n) J.R[iperm[i] + col] = M[m][c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Slice QR.  Shared memory: [A n1*n2, Q n1*qcols if in_smem][vhead nref][dph m]
 // [vscale nref floats][reduction 32 floats].
 // ---------------------------------------------------------------------------------------
@@ -332,6 +476,199 @@ __global__ void __launch_bounds__(512) tqr_kernel(const LaJob* __restrict__ jobs
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Register-resident slice QR for n1 <= 32 RM and n2, qcols <= 16 CW, 16 warps (the launcher
+// takes it for 32 x 128, 64 x 64 and 128 x 64 tiles, which keep the tile in registers).  The layout of
+// tinv_reg_kernel: lane l of warp w holds rows l + 32 m of columns w + 16 c, first of the
+// slice and then of Q.  Step k: the warp that owns column k forms reflector k from its
+// registers (a warp sum for the norm) and publishes it to shared memory, where every reflector
+// stays; after one barrier each warp applies it to its own columns j > k (a warp sum per
+// column for w = v^H a_j).  Q = H_0 ... H_(nref-1) I(:, 0:qcols) is then formed column by
+// column with no barrier at all, each warp applying the stored reflectors to its own columns
+// of the identity, last reflector first.  Shared memory: [V max(nref, 1) x 32 RM]
+// [diagonal phases 32 RM][scales max(nref, 1) floats].
+// ---------------------------------------------------------------------------------------
+constexpr int kQrWarps = 16;
+
+template <int RM, int CW>
+__global__ void __launch_bounds__(32 * kQrWarps) tqr_reg_kernel(const LaJob* __restrict__ jobs) {
+    constexpr int W = kQrWarps, NR = 32 * RM;
+    constexpr unsigned kFull = 0xffffffffu;
+    extern __shared__ float4 la_smem[];
+    const LaJob J = jobs[blockIdx.x];
+    const int n1 = J.n1, n2 = J.n2, qc = J.qcols, rr = J.rrows;
+    const int m = min(n1, n2), nref = min(n1 - 1, n2);
+    float2* V = reinterpret_cast<float2*>(la_smem);
+    float2* dph = V + (size_t)max(nref, 1) * NR;
+    float* vscale = reinterpret_cast<float*>(dph + NR);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    float2 M[RM][CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+#pragma unroll
+        for (int mm = 0; mm < RM; ++mm) {
+            const int i = lane + 32 * mm, j = warp + W * c;
+            M[mm][c] = (i < n1 && j < n2) ? J.A[i + (size_t)n1 * j] : make_float2(0.0f, 0.0f);
+        }
+
+    for (int k = 0; k < nref; ++k) {
+        const int wk = k % W, ck = k / W;
+        float2* vk = V + (size_t)k * NR;
+        if (warp == wk) {  // owner of column k: reflector k
+            float2 x[RM];
+#pragma unroll
+            for (int mm = 0; mm < RM; ++mm) x[mm] = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int c = 0; c < CW; ++c)
+                if (c == ck) {
+#pragma unroll
+                    for (int mm = 0; mm < RM; ++mm) x[mm] = M[mm][c];
+                }
+            float s = 0.0f;
+            float2 a = x[0];
+#pragma unroll
+            for (int mm = 0; mm < RM; ++mm) {
+                if (lane + 32 * mm > k) s += abs2(x[mm]);
+                if (mm == (k >> 5)) a = x[mm];
+            }
+            s = warp_sum(s);
+            a = make_float2(__shfl_sync(kFull, a.x, k & 31), __shfl_sync(kFull, a.y, k & 31));
+            float scale = 0.0f;  // s == 0: nothing below the diagonal, no reflector
+            if (s != 0.0f) {
+                const float absa = sqrtf(abs2(a));
+                const float nrm = sqrtf(fmaf(absa, absa, s));
+                const float2 ph = absa > 0.0f ? make_float2(a.x / absa, a.y / absa) : make_float2(1.0f, 0.0f);
+                scale = 1.0f / (nrm * (nrm + absa));  // H = I - scale v v^H
+                const float2 v0 = make_float2(ph.x * (absa + nrm), ph.y * (absa + nrm));
+#pragma unroll
+                for (int mm = 0; mm < RM; ++mm) {
+                    const int i = lane + 32 * mm;
+                    vk[i] = i > k ? x[mm] : (i == k ? v0 : make_float2(0.0f, 0.0f));
+                }
+                if (lane == (k & 31)) {  // the diagonal becomes beta = -phase(a) ||x||
+#pragma unroll
+                    for (int c = 0; c < CW; ++c)
+                        if (c == ck) {
+#pragma unroll
+                            for (int mm = 0; mm < RM; ++mm)
+                                if (mm == (k >> 5)) M[mm][c] = make_float2(-ph.x * nrm, -ph.y * nrm);
+                        }
+                }
+            }
+            if (lane == 0) vscale[k] = scale;
+        }
+        __syncthreads();
+        const float scale = vscale[k];
+        if (scale == 0.0f) continue;
+        float2 v[RM];
+#pragma unroll
+        for (int mm = 0; mm < RM; ++mm) v[mm] = vk[lane + 32 * mm];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+            const int j = warp + W * c;
+            if (j <= k || j >= n2) continue;
+            float2 w = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int mm = 0; mm < RM; ++mm) {
+                const float2 t = cjmul(v[mm], M[mm][c]);
+                w.x += t.x;
+                w.y += t.y;
+            }
+            w.x = warp_sum(w.x) * scale;
+            w.y = warp_sum(w.y) * scale;
+#pragma unroll
+            for (int mm = 0; mm < RM; ++mm) {
+                const float2 t = cmul(v[mm], w);
+                M[mm][c] = make_float2(M[mm][c].x - t.x, M[mm][c].y - t.y);
+            }
+        }
+    }
+
+    // phases of the diagonal of R, then R with row i rotated by conj(phase_i)
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+        const int j = warp + W * c;
+#pragma unroll
+        for (int mm = 0; mm < RM; ++mm)
+            if (j < m && lane + 32 * mm == j) {
+                const float2 d = M[mm][c];
+                const float ad = sqrtf(abs2(d));
+                dph[j] = ad > 0.0f ? make_float2(d.x / ad, d.y / ad) : make_float2(1.0f, 0.0f);
+            }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+        const int j = warp + W * c;
+        if (j >= n2) continue;
+#pragma unroll
+        for (int mm = 0; mm < RM; ++mm) {
+            const int i = lane + 32 * mm;
+            if (i >= rr) continue;
+            float2 r = make_float2(0.0f, 0.0f);
+            if (i < m && i <= j) {
+                const float2 x = M[mm][c];
+                r = (i == j) ? make_float2(sqrtf(abs2(x)), 0.0f) : cjmul(dph[i], x);
+            }
+            J.R[i + (size_t)rr * j] = r;
+        }
+    }
+
+    // Q: the reflectors, last first, on this warp's columns of the identity; H_k leaves
+    // column j < k unchanged
+    float2 Q[RM][CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+#pragma unroll
+        for (int mm = 0; mm < RM; ++mm)
+            Q[mm][c] = make_float2(lane + 32 * mm == warp + W * c ? 1.0f : 0.0f, 0.0f);
+    for (int k = nref - 1; k >= 0; --k) {
+        const float scale = vscale[k];
+        if (scale == 0.0f) continue;
+        const float2* vk = V + (size_t)k * NR;
+        float2 v[RM];
+#pragma unroll
+        for (int mm = 0; mm < RM; ++mm) v[mm] = vk[lane + 32 * mm];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+            const int j = warp + W * c;
+            if (j < k || j >= qc) continue;
+            float2 w = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int mm = 0; mm < RM; ++mm) {
+                const float2 t = cjmul(v[mm], Q[mm][c]);
+                w.x += t.x;
+                w.y += t.y;
+            }
+            w.x = warp_sum(w.x) * scale;
+            w.y = warp_sum(w.y) * scale;
+#pragma unroll
+            for (int mm = 0; mm < RM; ++mm) {
+                const float2 t = cmul(v[mm], w);
+                Q[mm][c] = make_float2(Q[mm][c].x - t.x, Q[mm][c].y - t.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+        const int j = warp + W * c;
+        if (j >= qc) continue;
+        const float2 ph = j < m ? dph[j] : make_float2(1.0f, 0.0f);
+#pragma unroll
+        for (int mm = 0; mm < RM; ++mm) {
+            const int i = lane + 32 * mm;
+            if (i < n1) J.Q[i + (size_t)n1 * j] = cmul(Q[mm][c], ph);
+        }
+    }
+}
+
+size_t tqr_reg_smem_bytes(int n1, int n2) {
+    const size_t nr = n1 <= 32 ? 32 : (n1 <= 64 ? 64 : 128);
+    const size_t nref = (size_t)std::max(std::min(n1 - 1, n2), 1);
+    return align16(sizeof(float2) * (nref * nr + nr) + sizeof(float) * nref);
+}
+
 int la_threads(int n1, int n2) { return max(n1, n2) > 64 ? 512 : 256; }
 
 cudaError_t set_smem(const void* fn, size_t bytes) {
@@ -354,6 +691,12 @@ size_t tqr_smem_bytes(int n1, int n2, int qcols, bool in_smem) {
 
 cudaError_t launch_tinv(const LaJob* d_jobs, int njobs, int n, uint32_t* status, cudaStream_t s) {
     if (njobs <= 0) return cudaSuccess;
+    if (n <= 128) {  // register-resident: 32 x 32, 64 x 64 or 128 x 128 tile
+        if (n <= 32) tinv_reg_kernel<1, 8, 4><<<njobs, 256, 0, s>>>(d_jobs, status);
+        else if (n <= 64) tinv_reg_kernel<2, 8, 8><<<njobs, 256, 0, s>>>(d_jobs, status);
+        else tinv_reg_kernel<4, 16, 8><<<njobs, 512, 0, s>>>(d_jobs, status);
+        return cudaGetLastError();
+    }
     const bool in_smem = tinv_smem_bytes(n, true) <= kLaSmemLimit;
     const size_t smem = tinv_smem_bytes(n, in_smem);
     const int rows = (n + 31) / 32;
@@ -363,10 +706,7 @@ cudaError_t launch_tinv(const LaJob* d_jobs, int njobs, int n, uint32_t* status,
         if (e != cudaSuccess) return e;                                                        \
         tinv_kernel<R><<<njobs, la_threads(n, n), smem, s>>>(d_jobs, in_smem ? 1 : 0, status); \
     } while (0)
-    if (rows <= 1) TP_TINV_LAUNCH(1);
-    else if (rows <= 2) TP_TINV_LAUNCH(2);
-    else if (rows <= 4) TP_TINV_LAUNCH(4);
-    else if (rows <= 8) TP_TINV_LAUNCH(8);
+    if (rows <= 8) TP_TINV_LAUNCH(8);  // n > 128 here
     else TP_TINV_LAUNCH(16);
 #undef TP_TINV_LAUNCH
     return cudaGetLastError();
@@ -374,6 +714,33 @@ cudaError_t launch_tinv(const LaJob* d_jobs, int njobs, int n, uint32_t* status,
 
 cudaError_t launch_tqr(const LaJob* d_jobs, int njobs, int n1, int n2, int qcols, cudaStream_t s) {
     if (njobs <= 0) return cudaSuccess;
+    const int cols = std::max(n2, qcols);
+    // register-resident where the tile fits the registers: 32 x 128, 64 x 64 or 128 x 64
+    if ((n1 <= 32 && cols <= 128) || (n1 <= 128 && cols <= 64)) {
+        const size_t smem = tqr_reg_smem_bytes(n1, n2);
+#define TP_TQR_REG(RM, CW)                                                                   \
+    do {                                                                                     \
+        cudaError_t e = set_smem(reinterpret_cast<const void*>(tqr_reg_kernel<RM, CW>), smem); \
+        if (e != cudaSuccess) return e;                                                      \
+        tqr_reg_kernel<RM, CW><<<njobs, 32 * kQrWarps, smem, s>>>(d_jobs);                   \
+    } while (0)
+#define TP_TQR_REG_COLS(RM)                     \
+    do {                                        \
+        if (cols <= 32) TP_TQR_REG(RM, 2);      \
+        else TP_TQR_REG(RM, 4);                 \
+    } while (0)
+        if (n1 <= 32) {
+            if (cols <= 64) TP_TQR_REG_COLS(1);
+            else TP_TQR_REG(1, 8);
+        } else if (n1 <= 64) {
+            TP_TQR_REG_COLS(2);
+        } else {
+            TP_TQR_REG_COLS(4);
+        }
+#undef TP_TQR_REG_COLS
+#undef TP_TQR_REG
+        return cudaGetLastError();
+    }
     const bool in_smem = tqr_smem_bytes(n1, n2, qcols, true) <= kLaSmemLimit;
     const size_t smem = tqr_smem_bytes(n1, n2, qcols, in_smem);
     cudaError_t e = set_smem(reinterpret_cast<const void*>(tqr_kernel), smem);

@@ -41,9 +41,11 @@ def _tprod_ref(A, B):
 
 
 # ----------------------------------------------------------------------------- tinv
+# n <= 128 holds the slice in registers (32-, 64- and 128-wide tiles, full and ragged);
 # n = 170 and 200 do not fit one CTA's shared memory and take the global-memory path
-@pytest.mark.parametrize("n,n3", [(1, 1), (3, 1), (2, 2), (8, 4), (17, 7), (33, 6), (64, 16),
-                                  (100, 5), (160, 3), (170, 3), (200, 4)])
+@pytest.mark.parametrize("n,n3", [(1, 1), (3, 1), (2, 2), (8, 4), (17, 7), (32, 3), (33, 6),
+                                  (64, 16), (65, 2), (100, 5), (127, 3), (128, 6), (160, 3),
+                                  (170, 3), (200, 4)])
 def test_tinv_parity(tp, n, n3):
     A = synth.shifted_square(n, n3, seed=n + n3)
     B = tp.to_numpy(tp.tinv(tp.to_device(A)))
@@ -97,9 +99,10 @@ def test_tinv_shape_and_empty(tp):
 QR_CASES = [
     ("gauss", 1, 1, 1), ("gauss", 5, 3, 1), ("gauss", 1, 4, 3), ("gauss", 6, 1, 2),
     ("gauss", 40, 20, 7), ("gauss", 64, 16, 8), ("gauss", 150, 60, 9),
-    ("square", 3, 3, 4), ("square", 64, 64, 16), ("square", 120, 120, 5),
+    ("square", 3, 3, 4), ("square", 33, 33, 2), ("square", 64, 64, 16), ("square", 120, 120, 5),
+    ("gauss", 100, 50, 3), ("gauss", 128, 64, 6),  # register tiles 128 x 64 (economy Q)
     ("gauss", 240, 100, 4),  # global-memory path (A and Q exceed shared memory)
-    ("wide", 12, 30, 6),
+    ("wide", 12, 30, 6), ("wide", 30, 100, 3),  # the second: the 32 x 128 register tile
 ]
 
 
