@@ -219,10 +219,111 @@ __global__ void __launch_bounds__(512, 1) tinv_kernel(const LaJob* __restrict__ 
 // every other row, as the kernel above does after its exchange.  Regarding the matrix as the
 // map y = A x, each such step swaps the roles of x_k and y_(p_k), so after n steps the element
 // at (p_k, j) is element (k, p_j) of the inverse; the final store applies that permutation.
-// One barrier per step: the warp that owns column k chooses the pivot and publishes the
-// column (double-buffered), and each warp takes row p_k of its own columns from lane p_k mod 32
-// by shuffles.
+//
+// One barrier per step.  The warp that owns column k + 1 updates that column first, publishes
+// it (double-buffered) with its pivot row and 1 / pivot, and only then updates its other
+// columns, so the pivot search overlaps the other warps' updates.  Each warp takes row p_k of
+// its own columns from lane p_k mod 32 by shuffles.  With g_i = a_ik / pivot the update is
+// a_ij -= g_i a_(p_k) j on every row; column k is zeroed first and row p_k enters with
+// a = 0 and g = -1 / pivot, which leaves -g_i in column k and the scaled pivot row in row p_k.
 // ---------------------------------------------------------------------------------------
+// p ? a : b through a PTX select the optimiser cannot see into: a chain of these over a
+// register array stays a chain of selects instead of becoming an indexed access to a copy of
+// the array in local memory.
+__device__ __forceinline__ float sel(bool p, float a, float b) {
+    float r;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\tselp.f32 %0, %1, %2, q;\n\t}"
+        : "=f"(r) : "f"(a), "f"(b), "r"((unsigned)p));
+    return r;
+}
+__device__ __forceinline__ float2 sel(bool p, float2 a, float2 b) {
+    return make_float2(sel(p, a.x, b.x), sel(p, a.y, b.y));
+}
+
+// Row MI of the register tile (a compile-time index, chosen by a switch on the uniform row):
+// its values on this warp's columns from lane lp, and its reset for the pivot row.
+template <int MI, int RM, int CW>
+__device__ __forceinline__ void row_from_lane(const float2 (&M)[RM][CW], float2 (&x)[CW], int lp) {
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+        x[c] = make_float2(__shfl_sync(0xffffffffu, M[MI][c].x, lp), __shfl_sync(0xffffffffu, M[MI][c].y, lp));
+}
+template <int MI, int RM, int CW>
+__device__ __forceinline__ void pivot_row_reset(float2 (&M)[RM][CW], float2 (&g)[RM], float2 inv) {
+#pragma unroll
+    for (int c = 0; c < CW; ++c) M[MI][c] = make_float2(0.0f, 0.0f);
+    g[MI] = make_float2(-inv.x, -inv.y);
+}
+
+// Runs BODY(C) for the compile-time C in [0, 8) equal to the warp-uniform value v, so that the
+// register tile is indexed by constants only.
+#define TP_STATIC_SWITCH8(v, BODY)         \
+    switch (v) {                           \
+        case 0: BODY(0) break;             \
+        case 1: BODY(1) break;             \
+        case 2: BODY(2) break;             \
+        case 3: BODY(3) break;             \
+        case 4: BODY(4) break;             \
+        case 5: BODY(5) break;             \
+        case 6: BODY(6) break;             \
+        case 7: BODY(7) break;             \
+        default: break;                    \
+    }
+
+// Column CC of this warp: published to col_out with its pivot row among the available rows
+// (-1 when the pivot is at or below the threshold) and 1 / pivot.  The arg-max is two warp
+// reductions: the largest |a|^2 (its bit pattern, which orders non-negative floats; NaN counts
+// as 0) and then the smallest row holding it.  Warp-level.
+template <int CC, int RM, int CW>
+__device__ __forceinline__ void tinv_publish(const float2 (&M)[RM][CW], uint32_t avail, float thr2,
+                                             float2* col_out, int* pivot_out, float2* inv_out) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    unsigned best = 0u;
+    int bi = 0x7fffffff;
+#pragma unroll
+    for (int m = 0; m < RM; ++m) {
+        const float2 v = M[m][CC];
+        col_out[lane + 32 * m] = v;
+        const float a2 = abs2(v);
+        const unsigned bits = (((avail >> m) & 1u) && a2 == a2) ? __float_as_uint(a2) : 0u;
+        if (bits > best) {
+            best = bits;
+            bi = lane + 32 * m;
+        }
+    }
+    const unsigned mx = __reduce_max_sync(kFull, best);
+    const int p = (int)__reduce_min_sync(kFull, best == mx ? (unsigned)bi : 0xffffffffu);
+    const float pv = __uint_as_float(mx);
+    float2 a = M[0][CC];
+#pragma unroll
+    for (int m = 1; m < RM; ++m) a = sel(m == (p >> 5), M[m][CC], a);
+    a = make_float2(__shfl_sync(kFull, a.x, p & 31), __shfl_sync(kFull, a.y, p & 31));
+    if (lane == 0) {
+        const bool ok = pv > thr2;
+        *pivot_out = ok ? p : -1;
+        *inv_out = ok ? crcp(a) : make_float2(0.0f, 0.0f);
+    }
+}
+
+// a_ij -= g_i x_j on column c of the tile
+template <int RM, int CW>
+__device__ __forceinline__ void tinv_update(float2 (&M)[RM][CW], const float2 (&g)[RM], float2 xc, int c) {
+#pragma unroll
+    for (int m = 0; m < RM; ++m) {
+        const float2 a = M[m][c];
+        M[m][c] = make_float2(fmaf(-g[m].x, xc.x, fmaf(g[m].y, xc.y, a.x)),
+                              fmaf(-g[m].x, xc.y, fmaf(-g[m].y, xc.x, a.y)));
+    }
+}
+template <int CSKIP, int RM, int CW>
+__device__ __forceinline__ void tinv_update_all_but(float2 (&M)[RM][CW], const float2 (&g)[RM],
+                                                    const float2 (&x)[CW]) {
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+        if (c != CSKIP) tinv_update(M, g, x[c], c);
+}
+
 template <int RM, int W, int CW>
 __global__ void __launch_bounds__(32 * W) tinv_reg_kernel(const LaJob* __restrict__ jobs,
                                                           uint32_t* status) {
@@ -230,6 +331,7 @@ __global__ void __launch_bounds__(32 * W) tinv_reg_kernel(const LaJob* __restric
     constexpr int NC = 32 * RM;
     constexpr unsigned kFull = 0xffffffffu;
     __shared__ float2 colk[2][NC];
+    __shared__ float2 pinv[2];
     __shared__ int pivot[2];
     __shared__ int perm[NC], iperm[NC];
     __shared__ float red[W];
@@ -260,77 +362,55 @@ __global__ void __launch_bounds__(32 * W) tinv_reg_kernel(const LaJob* __restric
     for (int m = 0; m < RM; ++m)
         if (lane + 32 * m < n) avail |= 1u << m;
 
+    if (warp == 0) tinv_publish<0>(M, avail, thr2, colk[0], &pivot[0], &pinv[0]);
     bool singular = false;
     for (int k = 0; k < n; ++k) {
-        const int b = k & 1;
-        const int wk = k % W, ck = k / W;
-        if (warp == wk) {  // owner of column k: publish it and choose the pivot
-            float pv = -1.0f;
-            int p = 0x7fffffff;
-#pragma unroll
-            for (int c = 0; c < CW; ++c)
-                if (c == ck) {
-#pragma unroll
-                    for (int m = 0; m < RM; ++m) {
-                        colk[b][lane + 32 * m] = M[m][c];
-                        if ((avail >> m) & 1u) argmax_step(pv, p, abs2(M[m][c]), lane + 32 * m);
-                    }
-                }
-            for (int o = 16; o; o >>= 1)
-                argmax_step(pv, p, __shfl_xor_sync(kFull, pv, o), __shfl_xor_sync(kFull, p, o));
-            if (lane == 0) pivot[b] = pv > thr2 ? p : -1;  // also catches NaN and Inf
-        }
         __syncthreads();
+        const int b = k & 1;
         const int p = pivot[b];
         if (p < 0) {
             singular = true;
             break;
         }
         if (threadIdx.x == 0) perm[k] = p;
-        const float2 inv = crcp(colk[b][p]);
+        const float2 inv = pinv[b];
         const int lp = p & 31, mp = p >> 5;
-        // the scaled pivot row on this warp's columns; 1 / pivot in column k
-        float2 r[CW];
+        // row p of this warp's columns
+        float2 x[CW];
+#define TP_ROW(C) if constexpr (C < RM) row_from_lane<C>(M, x, lp);
+        TP_STATIC_SWITCH8(mp, TP_ROW)
+#undef TP_ROW
+        float2 g[RM];
 #pragma unroll
-        for (int c = 0; c < CW; ++c) r[c] = M[0][c];
-#pragma unroll
-        for (int m = 1; m < RM; ++m)
-            if (m == mp) {
-#pragma unroll
-                for (int c = 0; c < CW; ++c) r[c] = M[m][c];
-            }
-#pragma unroll
-        for (int c = 0; c < CW; ++c) {
-            const float2 x = make_float2(__shfl_sync(kFull, r[c].x, lp), __shfl_sync(kFull, r[c].y, lp));
-            r[c] = cmul(x, inv);
+        for (int m = 0; m < RM; ++m) g[m] = cmul(colk[b][lane + 32 * m], inv);
+        const int wk = k % W, ck = k / W;
+        if (warp == wk) {  // column k: zero, and a unit entry in row p
+#define TP_UNIT_COL(C)                                                 \
+    if constexpr (C < CW) {                                            \
+        x[C] = make_float2(1.0f, 0.0f);                                \
+        _Pragma("unroll") for (int m = 0; m < RM; ++m) M[m][C] = make_float2(0.0f, 0.0f); \
+    }
+            TP_STATIC_SWITCH8(ck, TP_UNIT_COL)
+#undef TP_UNIT_COL
         }
-        if (warp == wk) {  // column k: a_ik <- 0 before the update, so it ends at -f_i / pivot
-#pragma unroll
-            for (int c = 0; c < CW; ++c)
-                if (c == ck) {
-                    r[c] = inv;
-#pragma unroll
-                    for (int m = 0; m < RM; ++m) M[m][c] = make_float2(0.0f, 0.0f);
-                }
-        }
-#pragma unroll
-        for (int m = 0; m < RM; ++m) {
-            const float2 f = colk[b][lane + 32 * m];
-#pragma unroll
-            for (int c = 0; c < CW; ++c) {
-                const float2 a = M[m][c];
-                M[m][c] = make_float2(fmaf(-f.x, r[c].x, fmaf(f.y, r[c].y, a.x)),
-                                      fmaf(-f.x, r[c].y, fmaf(-f.y, r[c].x, a.y)));
-            }
-        }
-        if (lane == lp) {  // the pivot row itself becomes the scaled row
-#pragma unroll
-            for (int m = 0; m < RM; ++m)
-                if (m == mp) {
-#pragma unroll
-                    for (int c = 0; c < CW; ++c) M[m][c] = r[c];
-                }
+        if (lane == lp) {  // row p: a = 0, g = -1 / pivot
+#define TP_RESET(C) if constexpr (C < RM) pivot_row_reset<C>(M, g, inv);
+            TP_STATIC_SWITCH8(mp, TP_RESET)
+#undef TP_RESET
             avail &= ~(1u << mp);
+        }
+        if (k + 1 < n && warp == (k + 1) % W) {
+            // look-ahead: column k + 1 first, then its pivot, then the other columns
+#define TP_AHEAD(C)                                                                      \
+    if constexpr (C < CW) {                                                              \
+        tinv_update(M, g, x[C], C);                                                      \
+        tinv_publish<C>(M, avail, thr2, colk[b ^ 1], &pivot[b ^ 1], &pinv[b ^ 1]);       \
+        tinv_update_all_but<C>(M, g, x);                                                 \
+    }
+            TP_STATIC_SWITCH8((k + 1) / W, TP_AHEAD)
+#undef TP_AHEAD
+        } else {
+            tinv_update_all_but<-1>(M, g, x);
         }
     }
     if (singular) {
@@ -478,22 +558,154 @@ __global__ void __launch_bounds__(512) tqr_kernel(const LaJob* __restrict__ jobs
 
 // ---------------------------------------------------------------------------------------
 // Register-resident slice QR for n1 <= 32 RM and n2, qcols <= 16 CW, 16 warps (the launcher
-// takes it for 32 x 128, 64 x 64 and 128 x 64 tiles, which keep the tile in registers).  The layout of
-// tinv_reg_kernel: lane l of warp w holds rows l + 32 m of columns w + 16 c, first of the
-// slice and then of Q.  Step k: the warp that owns column k forms reflector k from its
-// registers (a warp sum for the norm) and publishes it to shared memory, where every reflector
-// stays; after one barrier each warp applies it to its own columns j > k (a warp sum per
-// column for w = v^H a_j).  Q = H_0 ... H_(nref-1) I(:, 0:qcols) is then formed column by
-// column with no barrier at all, each warp applying the stored reflectors to its own columns
-// of the identity, last reflector first.  Shared memory: [V max(nref, 1) x 32 RM]
-// [diagonal phases 32 RM][scales max(nref, 1) floats].
+// takes it for 32 x 128, 64 x 64 and 128 x 64 tiles, which keep the tile in registers).  The
+// layout of tinv_reg_kernel: lane l of warp w holds rows l + 32 m of columns w + 16 c, first
+// of the slice and then of Q.  Step k: reflector k is in shared memory, where every reflector
+// stays; after one barrier each warp applies it to its own columns j > k, the w = v^H a_j of
+// all its columns summed over the warp together (warp_sum_all).  The warp that owns column
+// k + 1 updates that column first, forms and publishes reflector k + 1 (a warp sum for the
+// norm) and applies reflector k to its other columns only in the next step, so that the next
+// reflector is ready when the others arrive.
+// Q = H_0 ... H_(nref-1) I(:, 0:qcols) is then formed with no barrier at all, each warp
+// applying the stored reflectors, last first, to its own columns of the identity.
+// Shared memory: [V max(nref, 1) x 32 RM][diagonal phases 32 RM][scales max(nref, 1) floats].
 // ---------------------------------------------------------------------------------------
 constexpr int kQrWarps = 16;
+
+// Sums each of the NV values of every lane over the warp; every lane receives all NV sums.
+// Recursive halving over the values padded to a power of two P (in each round a lane keeps one
+// half of its values, summed with its partner's copy of that half), plain butterflies for the
+// remaining lane bits, then a gather: about 2 P + 5 - log2 P shuffles instead of 5 NV.
+template <int NV>
+__device__ __forceinline__ void warp_sum_all(float (&v)[NV]) {
+    static_assert(NV >= 1 && NV <= 32, "up to 32 values");
+    constexpr unsigned kFull = 0xffffffffu;
+    constexpr int P = NV > 16 ? 32 : NV > 8 ? 16 : NV > 4 ? 8 : NV > 2 ? 4 : NV > 1 ? 2 : 1;
+    constexpr int R = P == 32 ? 5 : P == 16 ? 4 : P == 8 ? 3 : P == 4 ? 2 : P == 2 ? 1 : 0;
+    const int lane = threadIdx.x & 31;
+    float u[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) u[i] = i < NV ? v[i] : 0.0f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int o = 16 >> r, half = P >> (r + 1);
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? u[i] : u[i + half];
+            const float keep = upper ? u[i + half] : u[i];
+            u[i] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+    float s = u[0];
+#pragma unroll
+    for (int o = 16 >> R; o >= 1; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    // lane L now holds the sum of value sum_r [L & (16 >> r)] (P >> (r + 1))
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        int src = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (i & (P >> (r + 1))) src |= 16 >> r;
+        v[i] = __shfl_sync(kFull, s, src);
+    }
+}
+
+// Reflector kk of the QR from column CC of this warp, which is column kk: V_kk (zero above
+// row kk), its scale (0 when nothing lies below the diagonal: no reflector) and beta on the
+// diagonal.  Warp-level.
+template <int CC, int RM, int CW>
+__device__ __forceinline__ void qr_reflector(float2 (&M)[RM][CW], int kk, float2* vk, float* scale_out) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float2 x[RM];
+#pragma unroll
+    for (int mm = 0; mm < RM; ++mm) x[mm] = M[mm][CC];
+    float s = 0.0f;
+    float2 a = x[0];
+#pragma unroll
+    for (int mm = 0; mm < RM; ++mm) {
+        if (lane + 32 * mm > kk) s += abs2(x[mm]);
+        if (mm > 0) a = sel(mm == (kk >> 5), x[mm], a);
+    }
+    s = warp_sum(s);
+    a = make_float2(__shfl_sync(kFull, a.x, kk & 31), __shfl_sync(kFull, a.y, kk & 31));
+    float scale = 0.0f;
+    if (s != 0.0f) {
+        const float absa = sqrtf(abs2(a));
+        const float nrm = sqrtf(fmaf(absa, absa, s));
+        const float2 ph = absa > 0.0f ? make_float2(a.x / absa, a.y / absa) : make_float2(1.0f, 0.0f);
+        scale = 1.0f / (nrm * (nrm + absa));  // H = I - scale v v^H
+        const float2 v0 = make_float2(ph.x * (absa + nrm), ph.y * (absa + nrm));
+#pragma unroll
+        for (int mm = 0; mm < RM; ++mm) {
+            const int i = lane + 32 * mm;
+            vk[i] = i > kk ? x[mm] : (i == kk ? v0 : make_float2(0.0f, 0.0f));
+        }
+        const float2 beta = make_float2(-ph.x * nrm, -ph.y * nrm);  // the new diagonal
+#pragma unroll
+        for (int mm = 0; mm < RM; ++mm)
+            M[mm][CC] = sel(mm == (kk >> 5) && lane == (kk & 31), beta, M[mm][CC]);
+    }
+    if (lane == 0) *scale_out = scale;
+}
+
+// T <- (I - v v^H mask_c) T on the columns c >= CLO of the tile; mask_c = 0 leaves column c
+// as is.  Rows below 32 MLO are skipped, where v is zero.
+template <int CLO, int MLO, int RM, int CW>
+__device__ __forceinline__ void qr_apply(float2 (&T)[RM][CW], const float2 (&v)[RM], const float (&mask)[CW]) {
+    constexpr int NC = CW - CLO;
+    float w[2 * NC];
+#pragma unroll
+    for (int c = CLO; c < CW; ++c) {
+        float wr = 0.0f, wi = 0.0f;
+#pragma unroll
+        for (int mm = MLO; mm < RM; ++mm) {
+            wr = fmaf(v[mm].x, T[mm][c].x, fmaf(v[mm].y, T[mm][c].y, wr));
+            wi = fmaf(v[mm].x, T[mm][c].y, fmaf(-v[mm].y, T[mm][c].x, wi));
+        }
+        w[2 * (c - CLO)] = wr;
+        w[2 * (c - CLO) + 1] = wi;
+    }
+    warp_sum_all<2 * NC>(w);
+#pragma unroll
+    for (int c = CLO; c < CW; ++c) {
+        const float wx = w[2 * (c - CLO)] * mask[c], wy = w[2 * (c - CLO) + 1] * mask[c];
+#pragma unroll
+        for (int mm = MLO; mm < RM; ++mm) {
+            const float2 t = T[mm][c];
+            T[mm][c] = make_float2(fmaf(-v[mm].x, wx, fmaf(v[mm].y, wy, t.x)),
+                                   fmaf(-v[mm].x, wy, fmaf(-v[mm].y, wx, t.y)));
+        }
+    }
+}
+
+// Reflector k touches neither the columns c < k / 16 of any warp (done in the factorisation, or
+// left unchanged in Q) nor the rows below 32 (k / 32), where it is zero.
+#define TP_QR_APPLY(C)                                                                  \
+    if constexpr (C < CW) qr_apply<C, (C / 2 < RM ? C / 2 : RM - 1)>(T_, v, mask);
+
+// The same on column c alone, with its own warp sums.
+template <int RM, int CW>
+__device__ __forceinline__ void qr_apply_one(float2 (&T)[RM][CW], const float2 (&v)[RM], float scale, int c) {
+    float wr = 0.0f, wi = 0.0f;
+#pragma unroll
+    for (int mm = 0; mm < RM; ++mm) {
+        wr = fmaf(v[mm].x, T[mm][c].x, fmaf(v[mm].y, T[mm][c].y, wr));
+        wi = fmaf(v[mm].x, T[mm][c].y, fmaf(-v[mm].y, T[mm][c].x, wi));
+    }
+    const float wx = warp_sum(wr) * scale, wy = warp_sum(wi) * scale;
+#pragma unroll
+    for (int mm = 0; mm < RM; ++mm) {
+        const float2 t = T[mm][c];
+        T[mm][c] = make_float2(fmaf(-v[mm].x, wx, fmaf(v[mm].y, wy, t.x)),
+                               fmaf(-v[mm].x, wy, fmaf(-v[mm].y, wx, t.y)));
+    }
+}
 
 template <int RM, int CW>
 __global__ void __launch_bounds__(32 * kQrWarps) tqr_reg_kernel(const LaJob* __restrict__ jobs) {
     constexpr int W = kQrWarps, NR = 32 * RM;
-    constexpr unsigned kFull = 0xffffffffu;
     extern __shared__ float4 la_smem[];
     const LaJob J = jobs[blockIdx.x];
     const int n1 = J.n1, n2 = J.n2, qc = J.qcols, rr = J.rrows;
@@ -512,76 +724,63 @@ __global__ void __launch_bounds__(32 * kQrWarps) tqr_reg_kernel(const LaJob* __r
             M[mm][c] = (i < n1 && j < n2) ? J.A[i + (size_t)n1 * j] : make_float2(0.0f, 0.0f);
         }
 
+    if (nref > 0 && warp == 0) qr_reflector<0>(M, 0, V, &vscale[0]);
+    // The warp that forms reflector k + 1 in step k leaves reflector k on its other columns
+    // for step k + 1 (kd), so that its path to the barrier is the look-ahead alone.
+    int kd = -1;
     for (int k = 0; k < nref; ++k) {
-        const int wk = k % W, ck = k / W;
-        float2* vk = V + (size_t)k * NR;
-        if (warp == wk) {  // owner of column k: reflector k
-            float2 x[RM];
-#pragma unroll
-            for (int mm = 0; mm < RM; ++mm) x[mm] = make_float2(0.0f, 0.0f);
-#pragma unroll
-            for (int c = 0; c < CW; ++c)
-                if (c == ck) {
-#pragma unroll
-                    for (int mm = 0; mm < RM; ++mm) x[mm] = M[mm][c];
-                }
-            float s = 0.0f;
-            float2 a = x[0];
-#pragma unroll
-            for (int mm = 0; mm < RM; ++mm) {
-                if (lane + 32 * mm > k) s += abs2(x[mm]);
-                if (mm == (k >> 5)) a = x[mm];
-            }
-            s = warp_sum(s);
-            a = make_float2(__shfl_sync(kFull, a.x, k & 31), __shfl_sync(kFull, a.y, k & 31));
-            float scale = 0.0f;  // s == 0: nothing below the diagonal, no reflector
-            if (s != 0.0f) {
-                const float absa = sqrtf(abs2(a));
-                const float nrm = sqrtf(fmaf(absa, absa, s));
-                const float2 ph = absa > 0.0f ? make_float2(a.x / absa, a.y / absa) : make_float2(1.0f, 0.0f);
-                scale = 1.0f / (nrm * (nrm + absa));  // H = I - scale v v^H
-                const float2 v0 = make_float2(ph.x * (absa + nrm), ph.y * (absa + nrm));
-#pragma unroll
-                for (int mm = 0; mm < RM; ++mm) {
-                    const int i = lane + 32 * mm;
-                    vk[i] = i > k ? x[mm] : (i == k ? v0 : make_float2(0.0f, 0.0f));
-                }
-                if (lane == (k & 31)) {  // the diagonal becomes beta = -phase(a) ||x||
-#pragma unroll
-                    for (int c = 0; c < CW; ++c)
-                        if (c == ck) {
-#pragma unroll
-                            for (int mm = 0; mm < RM; ++mm)
-                                if (mm == (k >> 5)) M[mm][c] = make_float2(-ph.x * nrm, -ph.y * nrm);
-                        }
-                }
-            }
-            if (lane == 0) vscale[k] = scale;
-        }
         __syncthreads();
+        if (kd >= 0) {  // the deferred reflector first: columns j > kd except kd + 1
+            const float sd = vscale[kd];
+            if (sd != 0.0f) {
+                float2 v[RM];
+#pragma unroll
+                for (int mm = 0; mm < RM; ++mm) v[mm] = V[(size_t)kd * NR + lane + 32 * mm];
+                float mask[CW];
+                bool any = false;
+#pragma unroll
+                for (int c = 0; c < CW; ++c) {
+                    const int j = warp + W * c;
+                    const bool on = j > kd + 1 && j < n2;
+                    mask[c] = on ? sd : 0.0f;
+                    any |= on;
+                }
+                if (any) {
+                    auto& T_ = M;
+                    TP_STATIC_SWITCH8(kd >> 4, TP_QR_APPLY)
+                }
+            }
+            kd = -1;
+        }
         const float scale = vscale[k];
-        if (scale == 0.0f) continue;
         float2 v[RM];
 #pragma unroll
-        for (int mm = 0; mm < RM; ++mm) v[mm] = vk[lane + 32 * mm];
+        for (int mm = 0; mm < RM; ++mm)
+            v[mm] = scale != 0.0f ? V[(size_t)k * NR + lane + 32 * mm] : make_float2(0.0f, 0.0f);
+        if (k + 1 < nref && warp == (k + 1) % W) {  // look-ahead: column k + 1, reflector k + 1
+#define TP_AHEAD(C)                                                             \
+    if constexpr (C < CW) {                                                     \
+        if (scale != 0.0f) qr_apply_one(M, v, scale, C);                        \
+        qr_reflector<C>(M, k + 1, V + (size_t)(k + 1) * NR, &vscale[k + 1]);    \
+    }
+            TP_STATIC_SWITCH8((k + 1) / W, TP_AHEAD)
+#undef TP_AHEAD
+            kd = k;
+            continue;
+        }
+        if (scale == 0.0f) continue;
+        float mask[CW];
+        bool any = false;
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
             const int j = warp + W * c;
-            if (j <= k || j >= n2) continue;
-            float2 w = make_float2(0.0f, 0.0f);
-#pragma unroll
-            for (int mm = 0; mm < RM; ++mm) {
-                const float2 t = cjmul(v[mm], M[mm][c]);
-                w.x += t.x;
-                w.y += t.y;
-            }
-            w.x = warp_sum(w.x) * scale;
-            w.y = warp_sum(w.y) * scale;
-#pragma unroll
-            for (int mm = 0; mm < RM; ++mm) {
-                const float2 t = cmul(v[mm], w);
-                M[mm][c] = make_float2(M[mm][c].x - t.x, M[mm][c].y - t.y);
-            }
+            const bool on = j > k && j < n2;
+            mask[c] = on ? scale : 0.0f;
+            any |= on;
+        }
+        if (any) {
+            auto& T_ = M;
+            TP_STATIC_SWITCH8(k >> 4, TP_QR_APPLY)
         }
     }
 
@@ -625,30 +824,18 @@ __global__ void __launch_bounds__(32 * kQrWarps) tqr_reg_kernel(const LaJob* __r
             Q[mm][c] = make_float2(lane + 32 * mm == warp + W * c ? 1.0f : 0.0f, 0.0f);
     for (int k = nref - 1; k >= 0; --k) {
         const float scale = vscale[k];
-        if (scale == 0.0f) continue;
-        const float2* vk = V + (size_t)k * NR;
+        if (scale == 0.0f || warp + W * (CW - 1) < k) continue;
         float2 v[RM];
 #pragma unroll
-        for (int mm = 0; mm < RM; ++mm) v[mm] = vk[lane + 32 * mm];
+        for (int mm = 0; mm < RM; ++mm) v[mm] = V[(size_t)k * NR + lane + 32 * mm];
+        float mask[CW];
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
             const int j = warp + W * c;
-            if (j < k || j >= qc) continue;
-            float2 w = make_float2(0.0f, 0.0f);
-#pragma unroll
-            for (int mm = 0; mm < RM; ++mm) {
-                const float2 t = cjmul(v[mm], Q[mm][c]);
-                w.x += t.x;
-                w.y += t.y;
-            }
-            w.x = warp_sum(w.x) * scale;
-            w.y = warp_sum(w.y) * scale;
-#pragma unroll
-            for (int mm = 0; mm < RM; ++mm) {
-                const float2 t = cmul(v[mm], w);
-                Q[mm][c] = make_float2(Q[mm][c].x - t.x, Q[mm][c].y - t.y);
-            }
+            mask[c] = (j >= k && j < qc) ? scale : 0.0f;
         }
+        auto& T_ = Q;
+        TP_STATIC_SWITCH8(k >> 4, TP_QR_APPLY)
     }
 #pragma unroll
     for (int c = 0; c < CW; ++c) {
