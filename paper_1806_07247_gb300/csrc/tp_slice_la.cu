@@ -613,29 +613,36 @@ __device__ __forceinline__ void warp_sum_all(float (&v)[NV]) {
 
 // Reflector kk of the QR from column CC of this warp, which is column kk: V_kk (zero above
 // row kk), its scale (0 when nothing lies below the diagonal: no reflector) and beta on the
-// diagonal.  Warp-level.
+// diagonal.  have_hint: s_hint and a_hint already hold the squared norm below the diagonal and
+// the diagonal element (qr_apply_one), else they are summed here.  Warp-level.
 template <int CC, int RM, int CW>
-__device__ __forceinline__ void qr_reflector(float2 (&M)[RM][CW], int kk, float2* vk, float* scale_out) {
+__device__ __forceinline__ void qr_reflector(float2 (&M)[RM][CW], int kk, float2* vk, float* scale_out,
+                                             bool have_hint, float s_hint, float2 a_hint) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     float2 x[RM];
 #pragma unroll
     for (int mm = 0; mm < RM; ++mm) x[mm] = M[mm][CC];
-    float s = 0.0f;
-    float2 a = x[0];
+    float s = s_hint;
+    float2 a = a_hint;
+    if (!have_hint) {
+        s = 0.0f;
+        a = x[0];
 #pragma unroll
-    for (int mm = 0; mm < RM; ++mm) {
-        if (lane + 32 * mm > kk) s += abs2(x[mm]);
-        if (mm > 0) a = sel(mm == (kk >> 5), x[mm], a);
+        for (int mm = 0; mm < RM; ++mm) {
+            if (lane + 32 * mm > kk) s += abs2(x[mm]);
+            if (mm > 0) a = sel(mm == (kk >> 5), x[mm], a);
+        }
+        s = warp_sum(s);
+        a = make_float2(__shfl_sync(kFull, a.x, kk & 31), __shfl_sync(kFull, a.y, kk & 31));
     }
-    s = warp_sum(s);
-    a = make_float2(__shfl_sync(kFull, a.x, kk & 31), __shfl_sync(kFull, a.y, kk & 31));
     float scale = 0.0f;
     if (s != 0.0f) {
         const float absa = sqrtf(abs2(a));
         const float nrm = sqrtf(fmaf(absa, absa, s));
-        const float2 ph = absa > 0.0f ? make_float2(a.x / absa, a.y / absa) : make_float2(1.0f, 0.0f);
-        scale = 1.0f / (nrm * (nrm + absa));  // H = I - scale v v^H
+        const float ra = __frcp_rn(absa);
+        const float2 ph = absa > 0.0f ? make_float2(a.x * ra, a.y * ra) : make_float2(1.0f, 0.0f);
+        scale = __frcp_rn(nrm * (nrm + absa));  // H = I - scale v v^H
         const float2 v0 = make_float2(ph.x * (absa + nrm), ph.y * (absa + nrm));
 #pragma unroll
         for (int mm = 0; mm < RM; ++mm) {
@@ -685,22 +692,46 @@ __device__ __forceinline__ void qr_apply(float2 (&T)[RM][CW], const float2 (&v)[
 #define TP_QR_APPLY(C)                                                                  \
     if constexpr (C < CW) qr_apply<C, (C / 2 < RM ? C / 2 : RM - 1)>(T_, v, mask);
 
-// The same on column c alone, with its own warp sums.
+// Reflector k (scale != 0) on column c alone, which is column k + 1, with its own warp sums.
+// The same sums give the squared norm t of rows >= k, which the unitary reflector keeps, so the
+// squared norm below the next diagonal is t - |y_k|^2 - |y_(k+1)|^2 with y the updated column
+// (y_(k+1) is returned in a).  Returns whether that difference kept at least a quarter of t,
+// i.e. lost at most two bits to cancellation; otherwise the caller sums it again.
 template <int RM, int CW>
-__device__ __forceinline__ void qr_apply_one(float2 (&T)[RM][CW], const float2 (&v)[RM], float scale, int c) {
-    float wr = 0.0f, wi = 0.0f;
+__device__ __forceinline__ bool qr_apply_one(float2 (&T)[RM][CW], const float2 (&v)[RM], float scale,
+                                             int c, int k, float& s, float2& a) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float wr = 0.0f, wi = 0.0f, t = 0.0f;
 #pragma unroll
     for (int mm = 0; mm < RM; ++mm) {
         wr = fmaf(v[mm].x, T[mm][c].x, fmaf(v[mm].y, T[mm][c].y, wr));
         wi = fmaf(v[mm].x, T[mm][c].y, fmaf(-v[mm].y, T[mm][c].x, wi));
+        if (lane + 32 * mm >= k) t += abs2(T[mm][c]);
     }
-    const float wx = warp_sum(wr) * scale, wy = warp_sum(wi) * scale;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        wr += __shfl_xor_sync(kFull, wr, o);
+        wi += __shfl_xor_sync(kFull, wi, o);
+        t += __shfl_xor_sync(kFull, t, o);
+    }
+    const float wx = wr * scale, wy = wi * scale;
 #pragma unroll
     for (int mm = 0; mm < RM; ++mm) {
-        const float2 t = T[mm][c];
-        T[mm][c] = make_float2(fmaf(-v[mm].x, wx, fmaf(v[mm].y, wy, t.x)),
-                               fmaf(-v[mm].x, wy, fmaf(-v[mm].y, wx, t.y)));
+        const float2 u = T[mm][c];
+        T[mm][c] = make_float2(fmaf(-v[mm].x, wx, fmaf(v[mm].y, wy, u.x)),
+                               fmaf(-v[mm].x, wy, fmaf(-v[mm].y, wx, u.y)));
     }
+    float2 yk = T[0][c], yk1 = T[0][c];
+#pragma unroll
+    for (int mm = 1; mm < RM; ++mm) {
+        yk = sel(mm == (k >> 5), T[mm][c], yk);
+        yk1 = sel(mm == ((k + 1) >> 5), T[mm][c], yk1);
+    }
+    yk = make_float2(__shfl_sync(kFull, yk.x, k & 31), __shfl_sync(kFull, yk.y, k & 31));
+    a = make_float2(__shfl_sync(kFull, yk1.x, (k + 1) & 31), __shfl_sync(kFull, yk1.y, (k + 1) & 31));
+    s = t - abs2(yk) - abs2(a);
+    return s >= 0.25f * t;
 }
 
 template <int RM, int CW>
@@ -724,7 +755,7 @@ __global__ void __launch_bounds__(32 * kQrWarps) tqr_reg_kernel(const LaJob* __r
             M[mm][c] = (i < n1 && j < n2) ? J.A[i + (size_t)n1 * j] : make_float2(0.0f, 0.0f);
         }
 
-    if (nref > 0 && warp == 0) qr_reflector<0>(M, 0, V, &vscale[0]);
+    if (nref > 0 && warp == 0) qr_reflector<0>(M, 0, V, &vscale[0], false, 0.0f, make_float2(0.0f, 0.0f));
     // The warp that forms reflector k + 1 in step k leaves reflector k on its other columns
     // for step k + 1 (kd), so that its path to the barrier is the look-ahead alone.
     int kd = -1;
@@ -758,10 +789,12 @@ __global__ void __launch_bounds__(32 * kQrWarps) tqr_reg_kernel(const LaJob* __r
         for (int mm = 0; mm < RM; ++mm)
             v[mm] = scale != 0.0f ? V[(size_t)k * NR + lane + 32 * mm] : make_float2(0.0f, 0.0f);
         if (k + 1 < nref && warp == (k + 1) % W) {  // look-ahead: column k + 1, reflector k + 1
-#define TP_AHEAD(C)                                                             \
-    if constexpr (C < CW) {                                                     \
-        if (scale != 0.0f) qr_apply_one(M, v, scale, C);                        \
-        qr_reflector<C>(M, k + 1, V + (size_t)(k + 1) * NR, &vscale[k + 1]);    \
+#define TP_AHEAD(C)                                                                   \
+    if constexpr (C < CW) {                                                           \
+        float sh = 0.0f;                                                              \
+        float2 ah = make_float2(0.0f, 0.0f);                                          \
+        const bool hint = scale != 0.0f && qr_apply_one(M, v, scale, C, k, sh, ah);   \
+        qr_reflector<C>(M, k + 1, V + (size_t)(k + 1) * NR, &vscale[k + 1], hint, sh, ah); \
     }
             TP_STATIC_SWITCH8((k + 1) / W, TP_AHEAD)
 #undef TP_AHEAD
