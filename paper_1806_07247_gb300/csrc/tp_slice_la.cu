@@ -15,8 +15,11 @@
 //              the factors unique for slices of full rank.  The real slices (Eq. 8) stay real:
 //              every reflector of a real column is real.
 //
-// The whole slice (and Q) sits in shared memory when it fits; larger slices are worked on in
-// place in global memory (the spectrum buffer), one CTA each, L2-resident.
+// Slices up to 128 wide are factorised in registers (tinv_reg_kernel, tqr_reg_kernel: one
+// barrier per pivot or reflector, the pivot search or next reflector formed ahead by the warp
+// that owns the next column).  For wider slices the whole slice (and Q) sits in shared memory
+// when it fits (tinv_kernel, tqr_kernel); larger ones are worked on in place in global memory
+// (the spectrum buffer), one CTA each, L2-resident.
 #include <algorithm>
 
 #include "tp_internal.cuh"
