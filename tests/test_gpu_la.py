@@ -100,9 +100,10 @@ QR_CASES = [
     ("gauss", 1, 1, 1), ("gauss", 5, 3, 1), ("gauss", 1, 4, 3), ("gauss", 6, 1, 2),
     ("gauss", 40, 20, 7), ("gauss", 64, 16, 8), ("gauss", 150, 60, 9),
     ("square", 3, 3, 4), ("square", 33, 33, 2), ("square", 64, 64, 16), ("square", 120, 120, 5),
-    ("gauss", 100, 50, 3), ("gauss", 128, 64, 6),  # register tiles 128 x 64 (economy Q)
+    ("gauss", 100, 20, 3), ("gauss", 100, 50, 3), ("gauss", 128, 64, 6),  # register tiles
+                                                     # 128 x 32 and 128 x 64 (economy Q)
     ("gauss", 240, 100, 4),  # global-memory path (A and Q exceed shared memory)
-    ("wide", 12, 30, 6), ("wide", 30, 100, 3),  # the second: the 32 x 128 register tile
+    ("wide", 12, 30, 6), ("wide", 12, 50, 3), ("wide", 30, 100, 3),  # 32 x 32, 64, 128 tiles
 ]
 
 
