@@ -392,21 +392,21 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
-def sketch_model_flops(shapes, widths, counts=None, survey=False):
+def sketch_model_flops(shapes, widths, counts=None, one_product=False):
     """Flop counts of the sketch SVT stage over the slices it sketched (width l > 0).
 
-    survey=False, the work the kernel does for one slice of width l: five passes of an
+    one_product=False, the work the kernel does for one slice of width l: five passes of an
     n1 x n2 by n2 x l complex product (range finder, one power iteration, B, residual check),
     four n1 x n2 complex mat-vecs (norm estimate) and the W update; 8 flops per complex MAC:
     8 n1 n2 (6 l + 4).
-    survey=True, the scope table's count of randomized SVD work, 8 m n (k + p) flops per
+    one_product=True, the usual count of randomized SVD work, 8 m n (k + p) flops per
     sketched slice with k + p = l (one n1 x n2 by n2 x l complex product)."""
     total, idx = 0.0, 0
     for n1, n2, n3 in shapes:
         for _ in range(n3 // 2 + 1):
             l = int(widths[idx])
             if l > 0:
-                total += 8.0 * n1 * n2 * (l if survey else (5 * l + 4 + l))
+                total += 8.0 * n1 * n2 * (l if one_product else (5 * l + 4 + l))
             idx += 1
     return total
 
@@ -544,7 +544,7 @@ def run_tp(args):
     st = learned["stages"]
     sk_flops = sketch_model_flops(shapes, learned["widths"])
     sk_tflops = sk_flops / (st["sketch_svt"] / 1e3) / 1e12
-    sk_tflops_survey = sketch_model_flops(shapes, learned["widths"], survey=True) / \
+    sk_tflops_one = sketch_model_flops(shapes, learned["widths"], one_product=True) / \
         (st["sketch_svt"] / 1e3) / 1e12
     fb = learned["flags"]
     # the learned method's fallback launches are never split by CTA size
@@ -553,10 +553,10 @@ def run_tp(args):
     dominant = "sketch_svt" if st["sketch_svt"] >= st["jacobi_svt"] else "jacobi_svt"
     if dominant == "sketch_svt":
         roof = {"kernel": "sketch_svt_kernel (randomized range finder + small Jacobi SVD + SVT)",
-                "bound": "alu", "achieved": sk_tflops_survey, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": sk_tflops_survey / FP32_PEAK_TFLOPS,
-                "count": "scope table: 8*n1*n2*l flops per sketched slice (l = k + p, the sketch "
-                         "width)",
+                "bound": "alu", "achieved": sk_tflops_one, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": sk_tflops_one / FP32_PEAK_TFLOPS,
+                "count": "randomized SVD work: 8*n1*n2*l flops per sketched slice (l = k + p, "
+                         "the sketch width)",
                 "work_model": {"achieved": sk_tflops, "frac": sk_tflops / FP32_PEAK_TFLOPS,
                                "count": "work done per sketched slice 8*n1*n2*(6*l+4) flops: five "
                                         "width-l products, four mat-vecs, the W update"},
