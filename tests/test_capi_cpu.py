@@ -91,6 +91,24 @@ def test_limits_and_bad_options_rejected(L):
     assert L.tp_tran(None, None, 2, 2, 2, None) == tp.TP_ERR_INVALID_ARG
 
 
+def test_factorisation_argument_checks_before_any_cuda_call(L):
+    """tinv (Def. 2.4) needs square frontal slices; both factorisations reject slices above the
+    SVD size limit and null pointers of non-empty tensors, and return at once on empty ones."""
+    from paper_1806_07247_gb300 import tp
+    assert L.tp_tinv(None, None, 3, 4, 2, None, None) == tp.TP_ERR_SHAPE
+    big = tp.MAX_SVD_DIM + 1
+    assert L.tp_tinv(None, None, big, big, 2, None, None) == tp.TP_ERR_UNSUPPORTED
+    assert L.tp_tinv(None, None, 0, 0, 2, None, None) == tp.TP_OK
+    assert L.tp_tinv(None, None, 4, 4, 0, None, None) == tp.TP_OK
+    assert L.tp_tinv(None, None, 4, 4, 2, None, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_tinv(None, None, -1, -1, 2, None, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_tqr(None, None, None, big, 4, 2, None, None) == tp.TP_ERR_UNSUPPORTED
+    assert L.tp_tqr(None, None, None, 4, big, 2, None, None) == tp.TP_ERR_UNSUPPORTED
+    assert L.tp_tqr(None, None, None, 0, 4, 2, None, None) == tp.TP_OK
+    assert L.tp_tqr(None, None, None, 4, 3, 2, None, None) == tp.TP_ERR_INVALID_ARG
+    assert L.tp_tqr(None, None, None, 4, -3, 2, None, None) == tp.TP_ERR_INVALID_ARG
+
+
 def test_jacobi_shape_and_autotune_argument_checks(L):
     from paper_1806_07247_gb300 import tp
     # every field out of range is rejected before the device is touched
